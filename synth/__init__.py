@@ -1,0 +1,289 @@
+"""Seeded synthetic inputs for the RT subcycle: meshes, gas, radiation, sources.
+
+This module holds no arithmetic of the RT method itself.  It produces the
+static mesh (cells and faces) and the initial state that the oracle and the
+CUDA path both consume:
+
+* periodic Cartesian grids (one face per cell pair, exact geometry);
+* periodic Voronoi meshes of jittered cubic lattices (``voronoi.cpp``, built
+  on first use with g++), standing in for AREPO's moving-mesh tessellation
+  (Sec. 2.1) held static over the RT subcycles (Sec. 2.3);
+* lognormal and exp(Gaussian random field) density fields, density peaks;
+* point sources binned onto cells, and the travelling-wave initial condition
+  of the photon-transport test (Sec. 4.2.1).
+
+Units: geometry in a length unit of the caller's choice (``unit_length_cm``
+converts it), number densities in cm^-3, photon rates in photons/s.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+__all__ = [
+    "Mesh", "cartesian_mesh", "voronoi_mesh", "jittered_lattice",
+    "lognormal_density", "grf_density", "density_peaks", "locate_cells",
+    "KPC_CM", "MPC_CM", "C_LIGHT", "helium_ratio", "SPECTRAL_SPLIT_E4",
+]
+
+KPC_CM = 3.0856775814913673e21
+MPC_CM = 1e3 * KPC_CM
+C_LIGHT = 2.99792458e10          # cm/s
+MYR_S = 3.15576e13               # s
+# Photon-rate split over the HI / HeI / HeII bins used by the coupled HII-region
+# test of Sec. 4.2.2 (1e50, 5e48, 3e48 photons/s), applied to every source.
+SPECTRAL_SPLIT_E4 = np.array([1e50, 5e48, 3e48]) / (1e50 + 5e48 + 3e48)
+
+
+def helium_ratio(Y: float) -> float:
+    """n_He / n_H for helium mass fraction Y (He nucleus mass = 4 m_H)."""
+    return Y / (4.0 * (1.0 - Y))
+
+
+@dataclasses.dataclass
+class Mesh:
+    """Static mesh in structure-of-arrays form.
+
+    Cells: ``volume``, centroid ``cx, cy, cz``.  Faces: ``left, right`` (int32
+    cell ids), ``area``, unit normal ``nx, ny, nz`` pointing from left to
+    right, centroid ``fx, fy, fz``.  ``box`` is the periodic box length
+    (0 = not periodic).  ``gen`` holds the generating points where there are any.
+    """
+    volume: np.ndarray
+    cx: np.ndarray
+    cy: np.ndarray
+    cz: np.ndarray
+    left: np.ndarray
+    right: np.ndarray
+    area: np.ndarray
+    nx: np.ndarray
+    ny: np.ndarray
+    nz: np.ndarray
+    fx: np.ndarray
+    fy: np.ndarray
+    fz: np.ndarray
+    box: float
+    gen: np.ndarray | None = None
+    lattice_n: int = 0
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.volume.shape[0])
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.left.shape[0])
+
+    @property
+    def faces_per_cell(self) -> float:
+        return self.n_faces / max(self.n_cells, 1)
+
+    def centroids(self) -> np.ndarray:
+        return np.stack([self.cx, self.cy, self.cz], axis=1)
+
+
+# ----------------------------------------------------------------------------
+# Cartesian grid
+# ----------------------------------------------------------------------------
+
+def cartesian_mesh(n: int, L: float) -> Mesh:
+    """Periodic n^3 grid of side L.  Cell (i,j,k) has id i + n(j + n k); its
+    faces towards +x, +y, +z come in that order, so face 3c+a joins cell c
+    (left) to its +a neighbour (right)."""
+    h = L / n
+    idx = np.arange(n ** 3, dtype=np.int64)
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+    cx, cy, cz = (i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h
+    nbr = [((i + 1) % n) + n * (j + n * k), i + n * (((j + 1) % n) + n * k), i + n * (j + n * ((k + 1) % n))]
+    left = np.repeat(idx, 3).astype(np.int32)
+    right = np.stack(nbr, axis=1).reshape(-1).astype(np.int32)
+    F = 3 * n ** 3
+    nx = np.tile(np.array([1.0, 0.0, 0.0]), n ** 3)
+    ny = np.tile(np.array([0.0, 1.0, 0.0]), n ** 3)
+    nz = np.tile(np.array([0.0, 0.0, 1.0]), n ** 3)
+    fx = np.repeat(cx, 3) + 0.5 * h * nx
+    fy = np.repeat(cy, 3) + 0.5 * h * ny
+    fz = np.repeat(cz, 3) + 0.5 * h * nz
+    fx, fy, fz = np.mod(fx, L), np.mod(fy, L), np.mod(fz, L)
+    return Mesh(volume=np.full(n ** 3, h ** 3), cx=cx, cy=cy, cz=cz, left=left, right=right,
+                area=np.full(F, h * h), nx=nx, ny=ny, nz=nz, fx=fx, fy=fy, fz=fz, box=float(L),
+                gen=np.stack([cx, cy, cz], axis=1), lattice_n=n)
+
+
+# ----------------------------------------------------------------------------
+# Voronoi mesh of a jittered lattice
+# ----------------------------------------------------------------------------
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+_LIB_LOCK = threading.Lock()
+
+
+def _lib_path() -> str:
+    return os.path.join(_HERE, "_voronoi.so")
+
+
+def build_voronoi_lib(force: bool = False) -> str:
+    """Compile voronoi.cpp into _voronoi.so (g++, OpenMP).  Returns the path."""
+    src = os.path.join(_HERE, "voronoi.cpp")
+    out = _lib_path()
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp])
+        os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _LIB
+    with _LIB_LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build_voronoi_lib())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            lib.vor_build.restype = ctypes.c_void_p
+            lib.vor_build.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp, ctypes.c_int,
+                                      ctypes.c_char_p, ctypes.c_int]
+            lib.vor_num_faces.restype = ctypes.c_int64
+            lib.vor_num_faces.argtypes = [ctypes.c_void_p]
+            lib.vor_num_asym.restype = ctypes.c_int64
+            lib.vor_num_asym.argtypes = [ctypes.c_void_p]
+            lib.vor_fetch.restype = None
+            lib.vor_fetch.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, ip, ip, dp, dp, dp, dp, dp, dp, dp]
+            lib.vor_free.restype = None
+            lib.vor_free.argtypes = [ctypes.c_void_p]
+            _LIB = lib
+    return _LIB
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def jittered_lattice(n: int, L: float, jitter: float, seed: int) -> np.ndarray:
+    """n^3 generators: lattice-cell centres (i+1/2)h plus an offset drawn
+    uniformly from [-jitter*h, +jitter*h] per axis (numpy PCG64, ``seed``).
+    Point p = i + n(j + n k) stays inside lattice cell (i,j,k) for jitter < 1/2."""
+    if not 0 <= jitter < 0.5:
+        raise ValueError("jitter must lie in [0, 0.5)")
+    h = L / n
+    rng = np.random.default_rng(seed)
+    idx = np.arange(n ** 3, dtype=np.int64)
+    base = np.stack([idx % n, (idx // n) % n, idx // (n * n)], axis=1).astype(np.float64) + 0.5
+    off = rng.uniform(-jitter, jitter, size=(n ** 3, 3))
+    return (base + off) * h
+
+
+def voronoi_mesh(n: int, L: float, jitter: float = 0.3, seed: int = 1, nthreads: int = 0) -> Mesh:
+    """Periodic Voronoi mesh of an n^3 jittered lattice in a box of side L."""
+    if jitter <= 0:
+        raise ValueError("use cartesian_mesh for an unjittered lattice (degenerate Voronoi vertices)")
+    pts = np.ascontiguousarray(jittered_lattice(n, L, jitter, seed))
+    px, py, pz = (np.ascontiguousarray(pts[:, a]) for a in range(3))
+    lib = _load()
+    err = ctypes.create_string_buffer(256)
+    h = lib.vor_build(n, L, _dptr(px), _dptr(py), _dptr(pz), int(nthreads), err, 256)
+    if not h:
+        raise RuntimeError(err.value.decode())
+    try:
+        C, F = n ** 3, lib.vor_num_faces(h)
+        arr = {k: np.empty(C) for k in ("volume", "cx", "cy", "cz")}
+        left, right = np.empty(F, np.int32), np.empty(F, np.int32)
+        farr = {k: np.empty(F) for k in ("area", "nx", "ny", "nz", "fx", "fy", "fz")}
+        lib.vor_fetch(h, _dptr(arr["volume"]), _dptr(arr["cx"]), _dptr(arr["cy"]), _dptr(arr["cz"]),
+                      _iptr(left), _iptr(right), _dptr(farr["area"]), _dptr(farr["nx"]), _dptr(farr["ny"]),
+                      _dptr(farr["nz"]), _dptr(farr["fx"]), _dptr(farr["fy"]), _dptr(farr["fz"]))
+    finally:
+        lib.vor_free(h)
+    return Mesh(left=left, right=right, box=float(L), gen=pts, lattice_n=n, **arr, **farr)
+
+
+# ----------------------------------------------------------------------------
+# Density fields and sources
+# ----------------------------------------------------------------------------
+
+def lognormal_density(n_cells: int, median: float, sigma_ln: float, seed: int) -> np.ndarray:
+    """i.i.d. lognormal n_H per cell: median * exp(sigma_ln * z), z ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    return median * np.exp(sigma_ln * rng.standard_normal(n_cells))
+
+
+def grf_field(ng: int, slope: float, seed: int) -> np.ndarray:
+    """Zero-mean, unit-variance Gaussian random field on a periodic ng^3 grid
+    with power spectrum P(k) ~ k^slope (k=0 mode removed)."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((ng, ng, ng))
+    wk = np.fft.rfftn(white)
+    kx = np.fft.fftfreq(ng)[:, None, None]
+    ky = np.fft.fftfreq(ng)[None, :, None]
+    kz = np.fft.rfftfreq(ng)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    amp = np.zeros_like(k2)
+    nz = k2 > 0
+    amp[nz] = k2[nz] ** (slope / 4.0)   # sqrt(P) = k^(slope/2)
+    g = np.fft.irfftn(wk * amp, s=(ng, ng, ng), axes=(0, 1, 2))
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def grf_density(points: np.ndarray, L: float, ng: int, sigma: float, mean: float, seed: int,
+                slope: float = -2.0):
+    """exp(sigma * g) of a unit-variance GRF g (P(k) ~ k^slope) on an ng^3 grid,
+    sampled at ``points`` by nearest grid node and scaled so that the mean over
+    the grid is ``mean``.  Returns (n_H at points, grid field)."""
+    g = grf_field(ng, slope, seed)
+    rho = np.exp(sigma * g)
+    rho *= mean / rho.mean()
+    ijk = np.floor(points / L * ng).astype(np.int64) % ng
+    # grid axis order (x, y, z)
+    return rho[ijk[:, 0], ijk[:, 1], ijk[:, 2]], rho
+
+
+def density_peaks(rho: np.ndarray, count: int) -> np.ndarray:
+    """Grid indices (m, 3) of the ``count`` highest strict local maxima over the
+    26 periodic neighbours, in decreasing order of density."""
+    is_max = np.ones(rho.shape, dtype=bool)
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                if dx == dy == dz == 0:
+                    continue
+                is_max &= rho > np.roll(rho, (dx, dy, dz), axis=(0, 1, 2))
+    cand = np.argwhere(is_max)
+    vals = rho[is_max]
+    order = np.argsort(-vals, kind="stable")[:count]
+    return cand[order]
+
+
+def locate_cells(mesh: Mesh, pos: np.ndarray) -> np.ndarray:
+    """Cell whose generator is nearest (periodic) to each position; for a
+    Voronoi mesh that is the cell containing it.  Uses the lattice: a point
+    in lattice cell c is nearest to a generator within +-2 lattice cells."""
+    n, L = mesh.lattice_n, mesh.box
+    if mesh.gen is None or n == 0:
+        raise ValueError("mesh has no lattice generators")
+    h = L / n
+    base = np.floor(pos / h).astype(np.int64)
+    best = np.full(len(pos), -1, dtype=np.int64)
+    bestd = np.full(len(pos), np.inf)
+    for dk in range(-2, 3):
+        for dj in range(-2, 3):
+            for di in range(-2, 3):
+                c = (base + np.array([di, dj, dk])) % n
+                q = c[:, 0] + n * (c[:, 1] + n * c[:, 2])
+                d = mesh.gen[q] - pos
+                d -= L * np.round(d / L)
+                d2 = (d * d).sum(axis=1)
+                better = d2 < bestd
+                best[better], bestd[better] = q[better], d2[better]
+    return best

@@ -1,0 +1,106 @@
+"""Input generators: mesh invariants and a brute-force cross-check of the
+Voronoi builder against Qhull (scipy.spatial) on a small periodic mesh."""
+import numpy as np
+import pytest
+
+import synth
+
+
+def _closure(mesh):
+    an = np.stack([mesh.area * mesh.nx, mesh.area * mesh.ny, mesh.area * mesh.nz], 1)
+    clo = np.zeros((mesh.n_cells, 3))
+    np.add.at(clo, mesh.left, an)
+    np.add.at(clo, mesh.right, -an)
+    return clo
+
+
+@pytest.mark.parametrize("n,jit", [(6, 0.3), (12, 0.3), (10, 0.1)])
+def test_voronoi_invariants(n, jit):
+    L = 3.0
+    m = synth.voronoi_mesh(n, L, jit, seed=n)
+    h = L / n
+    assert m.n_cells == n ** 3
+    assert abs(m.volume.sum() / L ** 3 - 1) < 1e-12
+    assert np.all(m.volume > 0) and np.all(m.area > 0)
+    np.testing.assert_allclose(np.sqrt(m.nx ** 2 + m.ny ** 2 + m.nz ** 2), 1, rtol=1e-14)
+    # closed cells: sum_f A n = 0
+    assert np.abs(_closure(m)).max() < 1e-12 * h * h
+    # each cell pair at most once, no self faces, both ids in range
+    assert np.all(m.left < m.right)
+    pairs = m.left.astype(np.int64) * m.n_cells + m.right
+    assert len(np.unique(pairs)) == m.n_faces
+    # normal points from left generator to right generator (periodic image)
+    g = m.gen
+    d = g[m.right] - g[m.left]
+    d -= L * np.round(d / L)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    np.testing.assert_allclose(np.stack([m.nx, m.ny, m.nz], 1), d, atol=1e-12)
+    # face centroid lies on the bisector plane of the two generators
+    fc = np.stack([m.fx, m.fy, m.fz], 1)
+    mid = g[m.left] + 0.5 * (g[m.right] - g[m.left] - L * np.round((g[m.right] - g[m.left]) / L))
+    off = fc - mid
+    off -= L * np.round(off / L)
+    assert np.abs((off * d).sum(1)).max() < 1e-10 * h
+    assert 7.0 < m.faces_per_cell < 8.5
+
+
+def test_voronoi_matches_qhull():
+    """Volumes and neighbour pairs equal those of scipy's Qhull tessellation
+    of the points plus their 26 periodic images."""
+    spatial = pytest.importorskip("scipy.spatial")
+    n, L = 6, 1.0
+    m = synth.voronoi_mesh(n, L, 0.3, seed=4)
+    pts = m.gen
+    shifts = np.array([(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)], float) * L
+    allp = np.concatenate([pts + s for s in shifts])
+    C = len(pts)
+    base = 13 * C  # shift (0,0,0) is index 13
+    vor = spatial.Voronoi(allp)
+    vols = np.empty(C)
+    for i in range(C):
+        reg = vor.regions[vor.point_region[base + i]]
+        assert -1 not in reg
+        vols[i] = spatial.ConvexHull(vor.vertices[reg]).volume
+    np.testing.assert_allclose(m.volume, vols, rtol=1e-9)
+    # neighbour pairs with a face of non-negligible area
+    qpairs = set()
+    for (a, b), rv in zip(vor.ridge_points, vor.ridge_vertices):
+        if a // C != 13 and b // C != 13:
+            continue
+        if -1 in rv:
+            continue
+        poly = vor.vertices[rv]
+        c0 = poly.mean(0)
+        area = 0.5 * np.linalg.norm(sum(np.cross(poly[k] - c0, poly[(k + 1) % len(poly)] - c0)
+                                        for k in range(len(poly))))
+        if area > 1e-8 * (L / n) ** 2:
+            i, j = sorted((a % C, b % C))
+            qpairs.add((i, j))
+    ours = {(int(i), int(j)) for i, j in zip(m.left, m.right)
+            if m.area[(m.left == i) & (m.right == j)][0] > 1e-8 * (L / n) ** 2}
+    assert ours == qpairs
+
+
+def test_cartesian_mesh():
+    m = synth.cartesian_mesh(4, 2.0)
+    assert m.n_cells == 64 and m.n_faces == 192
+    assert abs(m.volume.sum() - 8.0) < 1e-14
+    assert np.abs(_closure(m)).max() < 1e-15
+    assert m.faces_per_cell == 3.0
+
+
+def test_generators_seeded():
+    a = synth.lognormal_density(100, 1e-3, 1.0, 5)
+    b = synth.lognormal_density(100, 1e-3, 1.0, 5)
+    np.testing.assert_array_equal(a, b)
+    assert abs(np.median(synth.lognormal_density(100001, 1e-3, 1.0, 1)) / 1e-3 - 1) < 0.02
+    pts = synth.jittered_lattice(8, 1.0, 0.3, 2)
+    rho_pts, rho = synth.grf_density(pts, 1.0, 16, 1.5, 2e-4, 3)
+    assert abs(rho.mean() / 2e-4 - 1) < 1e-12 and rho_pts.shape == (512,)
+    peaks = synth.density_peaks(rho, 5)
+    assert len(peaks) == 5
+    vals = rho[tuple(peaks.T)]
+    assert np.all(np.diff(vals) <= 0)
+    m = synth.voronoi_mesh(8, 1.0, 0.3, seed=2)
+    probe = m.gen + 0.01
+    assert np.all(synth.locate_cells(m, probe) == np.arange(m.n_cells))
