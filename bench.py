@@ -1,0 +1,411 @@
+"""Benchmark of the M1 RT subcycle on GB300: RT cell-updates/s per subcycle
+(3 bins), mixed FP32/FP64 and FP64, with the HBM-roofline fraction of the
+dominant kernel, an end-to-end number through the C ABI with host buffers,
+and the FP64 CPU oracle timed on the host as a reported baseline.
+
+Workload (one step = one rt_step of 200 subcycles): periodic Voronoi mesh of a
+59^3 jittered lattice (205,379 cells, jitter 0.3 h, box 10 kpc), lognormal
+n_H (median 1e-3 cm^-3, sigma_ln 1), neutral H+He gas (Y = 0.24) at 1e4 K,
+16 sources with log10 Q ~ U(48, 51) split over the HI/HeI/HeII bins,
+c_red = 0.01 c, CFL 0.3, full chemistry.  The simulation runs on from step to
+step (warm-up steps included).  The working set is larger than the 129 MB L2.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1: one process per GPU (torchrun), independent replicas, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT cell-updates/s per subcycle (3 bins), FP64 vs mixed; % of HBM roofline"
+UNIT = "cell-updates/s"
+N_SUB = 200
+LATTICE = 59
+L_BOX = 10.0
+L2_BYTES = 129e6
+
+
+def workload(n=LATTICE, seed=1, n_src=16):
+    """Seeded inputs of the 2e5-cell Voronoi workload (see module doc)."""
+    import synth
+    mesh = synth.voronoi_mesh(n, L_BOX, 0.3, seed=seed)
+    C = mesh.n_cells
+    nH = synth.lognormal_density(C, 1e-3, 1.0, seed + 1)
+    x5 = np.zeros((5, C)); x5[0] = 1.0; x5[2] = 1.0
+    T = np.full(C, 1e4)
+    srng = np.random.default_rng(seed + 2)
+    cells = srng.choice(C, size=n_src, replace=False).astype(np.int64)
+    Q = np.outer(10 ** srng.uniform(48, 51, n_src), synth.SPECTRAL_SPLIT_E4)
+    cfg = dict(n_bins=3, c_red=0.01 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L_BOX, cfl=0.3, chem_mode=2,
+               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
+               max_substeps=10000, y_he=synth.helium_ratio(0.24), sigma=synth.GREY_SIGMA, eps=synth.GREY_EPS)
+    state = dict(nH=nH, x5=x5, T=T, N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q)
+    return mesh, cfg, state
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (compulsory traffic: each array the kernel
+# needs is read or written once; neighbour re-reads are not counted)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(kernel, C, F, B, w):
+    """w = bytes per word of the transport sweep (8 FP64, 4 mixed)."""
+    if kernel == "k_grad":
+        # prim 4wBC, M^-1 6wC, offsets 4C, CSR 8F, face ids 8F, w_f 3wF,
+        # x_f - s_L and x_f - s_R 6wF, gradients out 12wBC
+        return (16 * w * B + 6 * w + 4) * C + (16 + 9 * w) * F
+    if kernel == "k_flux":
+        # face ids 8F, (n, A) 4wF, x_f - s 6wF, prim + gradients of the
+        # cells 16wBC, fluxes out 4wBF
+        return (8 + 10 * w + 4 * w * B) * F + 16 * w * B * C
+    if kernel == "k_cell":
+        # offsets 4C, CSR 8F, fluxes 4wBF, V 8C, master radiation r/w 64BC,
+        # FP32 shadow out 16BC (mixed), source ids 4C, n_H 8C, abundances
+        # r/w 80C, T r/w 16C, substep counts 4C
+        shadow = 16 * B * C if w == 4 else 0
+        return 4 * C + 8 * F + 4 * w * B * F + 8 * C + 64 * B * C + shadow + 4 * C + 8 * C + 80 * C + 16 * C + 4 * C
+    raise KeyError(kernel)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for d in ("paper_2404_17630_gb300/csrc", "include"):
+        for name in sorted(os.listdir(os.path.join(ROOT, d))):
+            if name.endswith((".cu", ".cuh", ".h")):
+                with open(os.path.join(ROOT, d, name), "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = d.get(f"{precision}:{kernel}")
+    if not ent or ent.get("source_sha") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0])); mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def l2_flush(buf):
+    buf.add_(1.0)
+
+
+def run_gpu(precision, mesh, cfg, state, steps, warmup, rank, world, dev, dist, clocks=None):
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
+
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision=precision, **cfg), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dt = rt.max_dt() * N_SUB
+    flush = torch.empty(int(2 * L2_BYTES / 4), dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        rt.step(dt, N_SUB)
+    rt.sync()
+    l2_flush(flush)
+    n0 = rtb.rt_launch_count(rt.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ctx = clocks if clocks is not None else _Null()
+    with ctx:
+        ev0.record(stream)
+        for _ in range(steps):
+            rt.step(dt, N_SUB)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    rt.sync()
+    ms = ev0.elapsed_time(ev1)
+    launches = rtb.rt_launch_count(rt.ctx) - n0
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # per-kernel device times over the same number of steps (profiled pass)
+    rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, True)
+    for _ in range(steps):
+        rt.step(dt, N_SUB)
+    prof = rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, False)
+    rt.sync()
+    C, F, _ = rt.mesh_info()
+    return dict(ms=ms, C=C, F=F, launches=launches, prof=prof, rt=rt)
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def e2e_measure(precision, mesh, cfg, state, steps, dev):
+    """The same metric through the C ABI with host buffers: every step copies
+    the state in from pinned host memory, runs the 200 subcycles and copies
+    all fields back."""
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
+
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision=precision, **cfg), mesh, stream=stream)
+    rt.set_sources(state["cells"], state["Q"])
+    C, B = mesh.n_cells, 3
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    hN, hF = pin(state["N"]), pin(state["fr"] * cfg["c_red"])
+    hn, hx, hT = pin(state["nH"]), pin(state["x5"]), pin(state["T"])
+    oN, oF, ox, oT = (torch.empty(s, dtype=torch.float64).pin_memory() for s in ((B, C), (B, 3, C), (5, C), (C,)))
+    dt = rt.max_dt() * N_SUB
+    mask = rtb.RT_FIELD_N | rtb.RT_FIELD_F | rtb.RT_FIELD_X | rtb.RT_FIELD_T
+
+    def one():
+        rtb.rt_set_radiation(rt.ctx, hN, hF)
+        rtb.rt_set_gas(rt.ctx, hn, hx, hT)
+        rtb.rt_step(rt.ctx, dt, N_SUB)
+        rtb.rt_get_fields(rt.ctx, mask, [oN, oF, ox, oT])
+
+    one()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize(dev)
+    sec = time.perf_counter() - t0
+    h2d = (hN.numel() + hF.numel() + hn.numel() + hx.numel() + hT.numel()) * 8
+    d2h = (oN.numel() + oF.numel() + ox.numel() + oT.numel()) * 8
+    return dict(value=C * N_SUB * steps / sec, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                ms_per_step=1e3 * sec / steps)
+
+
+def roofline(res, precision, peaks, peak_kind):
+    C, F, B = res["C"], res["F"], 3
+    w = 4 if precision == "mixed" else 8
+    prof = res["prof"]
+    total = sum(v[0] for v in prof.values())
+    shares = {k: (v[0] / total if total else 0.0) for k, v in prof.items()}
+    top = max(prof, key=lambda k: prof[k][0])
+    ms, n = prof[top]
+    per_launch_s = ms / 1e3 / max(n, 1)
+    alg = algorithmic_bytes(top, C, F, B, w)
+    ach = alg / per_launch_s / 1e9
+    peak = float(peaks["hbm_gbs"])
+    kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": round(shares[k], 4),
+                "alg_bytes_per_launch": algorithmic_bytes(k, C, F, B, w),
+                "GBs": algorithmic_bytes(k, C, F, B, w) / (v[0] / 1e3 / max(v[1], 1)) / 1e9 if v[0] else None}
+            for k, v in prof.items()}
+    return {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "peak_source": f"hbm_gbs of {peak_kind}",
+            "traffic": ncu_traffic(top, precision), "alg_bytes_per_launch": alg}, kern
+
+
+def cpu_baseline(mesh, cfg, state, budget_s=12.0):
+    """The FP64 oracle as it stands, single thread, on the same workload:
+    subcycles of the full mesh until ~budget_s of CPU time."""
+    from tests._cases import make_oracle
+    o = make_oracle(mesh, cfg, state)
+    dt = o.max_dt()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(dt, 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 50:
+            break
+    sec = time.perf_counter() - t0
+    return {"value": mesh.n_cells * n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} subcycles of the full {mesh.n_cells}-cell workload from its initial state "
+                      f"({sec:.1f} s, FP64, single thread)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl")
+        dist = dist_
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    mesh, cfg, state = workload()
+    peaks, peak_kind = measured_peaks()
+    clocks = ClockSampler(local)
+    res = run_gpu("mixed", mesh, cfg, state, args.steps, args.warmup, rank, world, dev, dist, clocks)
+    cl = clocks.summary()
+    fp64 = None
+    if not args.no_fp64:
+        r64 = run_gpu("fp64", mesh, cfg, state, max(2, args.steps // 5), 1, rank, world, dev, dist)
+        fp64 = {"value": world * r64["C"] * N_SUB * max(2, args.steps // 5) / (r64["ms"] / 1e3),
+                "ms_per_step": r64["ms"] / max(2, args.steps // 5), "dtype": "f64"}
+        rf64, k64 = roofline(r64, "fp64", peaks, peak_kind)
+        fp64["roofline"] = rf64
+        fp64["kernels"] = k64
+    e2e = None if args.no_e2e else e2e_measure("mixed", mesh, cfg, state, max(2, args.steps // 2), dev)
+    if rank != 0:
+        return
+    C, F = res["C"], res["F"]
+    value = world * C * N_SUB * args.steps / (res["ms"] / 1e3)
+    rf, kern = roofline(res, "mixed", peaks, peak_kind)
+    cpu = None if args.no_cpu else cpu_baseline(mesh, cfg, state)
+    ws = (C * 3 * (32 + 16 + 48) + F * (64 + 48) + C * 200)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"voronoi {LATTICE}^3 jittered lattice ({C} cells, {F} faces, "
+                               f"{F / C:.3f} faces/cell), lognormal n_H, 16 sources, 3 bins, {N_SUB} subcycles/step",
+                   "cells": C, "faces": F, "n_sub": N_SUB, "precision": "mixed (FP32 sweep, FP64 update+chemistry)",
+                   "l2": f"working set ~{ws / 1e6:.0f} MB > L2 129 MB (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": rf, "kernels": kern,
+        "fp64": fp64,
+        "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "e2e": e2e, "cpu_baseline": cpu,
+        "gpu_launches": res["launches"], "clocks": cl,
+    }
+    print(json.dumps(out))
+
+
+def reference_arm(args, rank):
+    """The FP64 oracle timed on the host cores, on the same workload: each
+    step is a bounded sample (one subcycle of the full mesh)."""
+    if rank != 0:
+        return
+    mesh, cfg, state = workload()
+    from tests._cases import make_oracle
+    o = make_oracle(mesh, cfg, state)
+    dt = o.max_dt()
+    for _ in range(args.warmup):
+        o.step(dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(dt, 1)
+    sec = time.perf_counter() - t0
+    v = mesh.n_cells * args.steps / sec
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"voronoi {LATTICE}^3 jittered lattice ({mesh.n_cells} cells), one subcycle per step",
+                      "cells": mesh.n_cells, "n_sub": 1},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} timed subcycles after {args.warmup} warm-up subcycles"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

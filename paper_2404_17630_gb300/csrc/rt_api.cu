@@ -1,0 +1,716 @@
+// C ABI of the M1 RT subcycle (include/rt.h): context, mesh upload, state
+// transfer, the subcycle driver and the stage entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+#include "rt_kernels.cuh"
+
+using namespace m1rt;
+
+namespace {
+
+constexpr int kThreads = 256;
+inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct rt_ctx {
+  rt_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool mesh_ready = false;
+  int C = 0, F = 0, B = 0, max_deg = 0;
+  double min_dx_cm = 0;
+  // FP64 cell and face data
+  double *vol = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
+  int32_t *off = nullptr, *csr = nullptr;
+  int2* lr = nullptr;
+  d4 *nA64 = nullptr, *rL64 = nullptr, *rR64 = nullptr, *w64 = nullptr;
+  double* minv64 = nullptr;
+  // FP32 copies (mixed precision)
+  float4 *nA32 = nullptr, *rL32 = nullptr, *rR32 = nullptr, *w32 = nullptr;
+  float* minv32 = nullptr;
+  // state
+  d4* rad = nullptr;      // master [C][B]
+  float4* shadow = nullptr;    // FP32 sweep copy [C][B] (mixed)
+  double *nH = nullptr, *x5 = nullptr, *T = nullptr;
+  int32_t* src_idx = nullptr;
+  double* src_rate = nullptr;
+  int n_src_cells = 0, src_cap = 0;
+  int32_t* nsub = nullptr;
+  // work
+  void* G = nullptr;           // [C][B][12] in sweep precision
+  void* flux = nullptr;        // [F][B] 4-vectors in sweep precision
+  double* stage = nullptr;     // staging for caller arrays (max(4BC, 5C) doubles)
+  size_t stage_n = 0;
+  int* status = nullptr;
+  std::vector<void*> allocs;
+  // profiling: event pairs around launches, per kernel class
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;   // (class, index of start event)
+  double prof_ms[RT_KERNEL_COUNT] = {0, 0, 0};
+  int64_t prof_n[RT_KERNEL_COUNT] = {0, 0, 0};
+  int64_t launches = 0;
+};
+
+namespace {
+
+rt_status fail(rt_ctx* c, rt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_error = buf;
+  return st;
+}
+
+rt_status cuda_fail(rt_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, RT_OOM, "%s: out of device memory", what);
+  }
+  return fail(c, RT_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+template <class T> rt_status dalloc(rt_ctx* ctx, T** p, size_t n, const char* what) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  ctx->allocs.push_back(q);
+  *p = (T*)q;
+  return RT_OK;
+}
+
+void free_all(rt_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->mesh_ready = false;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n elements from caller memory (host or device) to device memory dst.
+rt_status copy_in(rt_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream), "copy in");
+  if (k == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(ctx->stream), "copy in");
+  return RT_OK;
+}
+
+rt_status copy_out(rt_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream), "copy out");
+  if (k == cudaMemcpyDeviceToHost) CK(cudaStreamSynchronize(ctx->stream), "copy out");
+  return RT_OK;
+}
+
+bool mixed(const rt_ctx* ctx) { return ctx->cfg.precision == RT_MIXED; }
+
+rt_status check_config(const rt_config* c) {
+  if (c->n_bins < 1 || c->n_bins > 3) return fail(nullptr, RT_INVALID_ARG, "n_bins must be 1..3");
+  if (c->precision != RT_FP64 && c->precision != RT_MIXED) return fail(nullptr, RT_INVALID_ARG, "bad precision");
+  if (!(c->c_red > 0) || !(c->unit_length_cm > 0) || !(c->cfl > 0) || c->box < 0)
+    return fail(nullptr, RT_INVALID_ARG, "c_red, unit_length_cm and cfl must be > 0, box >= 0");
+  if (c->chem_mode < 0 || c->chem_mode > 2) return fail(nullptr, RT_INVALID_ARG, "chem_mode must be 0..2");
+  if (c->order < 1 || c->order > 2) return fail(nullptr, RT_INVALID_ARG, "order must be 1 or 2");
+  if (c->chem_mode > 0 && (!(c->f_s > 0) || !(c->f_max > 0) || c->max_substeps < 1 || c->x_floor < 0))
+    return fail(nullptr, RT_INVALID_ARG, "bad substep parameters");
+  if (c->y_he < 0 || c->lim_eps < 0) return fail(nullptr, RT_INVALID_ARG, "y_he and lim_eps must be >= 0");
+  return RT_OK;
+}
+
+template <class R> Geo<R> geo(const rt_ctx* ctx);
+template <> Geo<double> geo<double>(const rt_ctx* c) {
+  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64};
+}
+template <> Geo<float> geo<float>(const rt_ctx* c) {
+  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32};
+}
+
+ChemParams chem_params(const rt_ctx* ctx) {
+  ChemParams P;
+  const rt_config& c = ctx->cfg;
+  P.B = c.n_bins;
+  P.mode = c.chem_mode;
+  P.flags = c.chem_flags;
+  P.c_red = c.c_red;
+  P.y_he = c.y_he;
+  P.f_s = c.f_s;
+  P.f_max = c.f_max;
+  P.x_floor = c.x_floor;
+  P.max_sub = c.max_substeps;
+  for (int b = 0; b < kMaxBins; ++b)
+    for (int s = 0; s < 3; ++s) {
+      P.sigma[b][s] = b < c.n_bins ? c.sigma[b][s] : 0.0;
+      P.eps[b][s] = b < c.n_bins ? c.eps[b][s] : 0.0;
+    }
+  return P;
+}
+
+CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
+  CellArgs a;
+  a.C = ctx->C; a.B = ctx->B; a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.rad = ctx->rad;
+  a.nH = ctx->nH; a.x5 = ctx->x5; a.T = ctx->T; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
+  a.nsub = ctx->nsub; a.status = ctx->status;
+  a.lam = ctx->cfg.c_red * dt / ctx->cfg.unit_length_cm;
+  a.dt = dt;
+  const double lu = ctx->cfg.unit_length_cm;
+  a.lu3 = lu * lu * lu;
+  a.do_gather = gather;
+  a.do_inject = inject && ctx->n_src_cells > 0;
+  a.do_chem = chem && ctx->cfg.chem_mode > 0;
+  return a;
+}
+
+// ---- kernel launches -------------------------------------------------------
+
+// Start/stop events around one launch of class k when profiling is on.
+struct ProfScope {
+  rt_ctx* c;
+  int k;
+  int idx = -1;
+  ProfScope(rt_ctx* ctx, int kind) : c(ctx), k(kind) {
+    c->launches++;
+    if (!c->profiling) return;
+    idx = (int)c->ev_used.size() * 2;
+    while ((int)c->ev_pool.size() < idx + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { idx = -1; return; }
+      c->ev_pool.push_back(e);
+    }
+    cudaEventRecord(c->ev_pool[idx], c->stream);
+  }
+  ~ProfScope() {
+    if (idx < 0) return;
+    cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+    c->ev_used.push_back({k, idx});
+  }
+};
+
+template <class R> const R4<R>* sweep_rad(rt_ctx* ctx);
+template <> const d4* sweep_rad<double>(rt_ctx* ctx) { return ctx->rad; }
+template <> const float4* sweep_rad<float>(rt_ctx* ctx) { return ctx->shadow; }
+
+template <class R> void launch_grad(rt_ctx* ctx) {
+  ProfScope ps(ctx, RT_KERNEL_GRAD);
+  const R e = (R)ctx->cfg.lim_eps;
+  k_grad<R><<<nblk((long long)ctx->C * ctx->B), kThreads, 0, ctx->stream>>>(
+      geo<R>(ctx), sweep_rad<R>(ctx), (R*)ctx->G, ctx->cfg.order, ctx->cfg.limiter, e * e);
+}
+
+template <class R> void launch_flux(rt_ctx* ctx) {
+  ProfScope ps(ctx, RT_KERNEL_FLUX);
+  k_flux<R><<<nblk((long long)ctx->F * ctx->B), kThreads, 0, ctx->stream>>>(geo<R>(ctx), sweep_rad<R>(ctx),
+                                                                            (const R*)ctx->G, (R4<R>*)ctx->flux);
+}
+
+void launch_cell(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
+  ProfScope ps(ctx, RT_KERNEL_CELL);
+  CellArgs a = cell_args(ctx, dt, gather, inject, chem);
+  ChemParams P = chem_params(ctx);
+  const int t = 128;
+  if (mixed(ctx))
+    k_cell<float, true><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, (const float4*)ctx->flux, ctx->shadow);
+  else
+    k_cell<double, false><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, (const d4*)ctx->flux, nullptr);
+}
+
+void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
+void launch_flux_any(rt_ctx* ctx) { mixed(ctx) ? launch_flux<float>(ctx) : launch_flux<double>(ctx); }
+
+void refresh_shadow(rt_ctx* ctx) {
+  if (!mixed(ctx)) return;
+  long long n = (long long)ctx->C * ctx->B;
+  k_shadow_rad<float><<<nblk(n), kThreads, 0, ctx->stream>>>((int)n, ctx->rad, ctx->shadow);
+}
+
+rt_status launched(rt_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return RT_OK;
+}
+
+rt_status need_mesh(rt_ctx* ctx) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  if (!ctx->mesh_ready) return fail(ctx, RT_NOT_READY, "rt_init_mesh has not succeeded");
+  return RT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
+  if (!out) return fail(nullptr, RT_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, RT_INVALID_ARG, "cfg is NULL");
+  rt_status st = check_config(cfg);
+  if (st) return st;
+  rt_ctx* ctx = new rt_ctx;
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->B = cfg->n_bins;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    cudaGetLastError();
+    return fail(nullptr, RT_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return RT_OK;
+}
+
+rt_status rt_set_stream(rt_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  ctx->stream = (cudaStream_t)stream;
+  return RT_OK;
+}
+
+rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  if (!cells || !faces) return fail(ctx, RT_INVALID_ARG, "cells or faces is NULL");
+  if (cells->n <= 0 || faces->n < 0 || cells->n > (1LL << 30) || faces->n > (1LL << 29))
+    return fail(ctx, RT_INVALID_ARG, "cell or face count out of range");
+  if (!cells->volume || !cells->cx || !cells->cy || !cells->cz || !faces->left || !faces->right || !faces->area ||
+      !faces->nx || !faces->ny || !faces->nz || !faces->fx || !faces->fy || !faces->fz)
+    return fail(ctx, RT_INVALID_ARG, "mesh array is NULL");
+  free_all(ctx);
+  const int C = (int)cells->n, F = (int)faces->n, B = ctx->B;
+  ctx->C = C;
+  ctx->F = F;
+  // host copies for validation and the CSR build (these are the only host
+  // passes over the mesh)
+  std::vector<int32_t> L(F), Rr(F);
+  std::vector<double> V(C);
+  const bool dev_l = F > 0 && is_device_ptr(faces->left);
+  if (F > 0) {
+    CK(cudaMemcpy(L.data(), faces->left, F * 4, dev_l ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "mesh");
+    CK(cudaMemcpy(Rr.data(), faces->right, F * 4,
+                  is_device_ptr(faces->right) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "mesh");
+  }
+  CK(cudaMemcpy(V.data(), cells->volume, (size_t)C * 8,
+                is_device_ptr(cells->volume) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "mesh");
+  std::vector<int32_t> off(C + 1, 0);
+  for (int f = 0; f < F; ++f) {
+    if (L[f] < 0 || L[f] >= C || Rr[f] < 0 || Rr[f] >= C || L[f] == Rr[f])
+      return fail(ctx, RT_BAD_MESH, "face %d joins cells %d and %d (C = %d)", f, L[f], Rr[f], C);
+    off[L[f] + 1]++;
+    off[Rr[f] + 1]++;
+  }
+  double minV = INFINITY;
+  for (int i = 0; i < C; ++i) {
+    if (!(V[i] > 0) || !std::isfinite(V[i])) return fail(ctx, RT_BAD_MESH, "cell %d has volume %g", i, V[i]);
+    minV = std::min(minV, V[i]);
+  }
+  int maxdeg = 0;
+  for (int i = 0; i < C; ++i) {
+    maxdeg = std::max(maxdeg, off[i + 1]);
+    off[i + 1] += off[i];
+  }
+  for (int i = 0; i < C; ++i) {
+    if (off[i + 1] == off[i]) return fail(ctx, RT_BAD_MESH, "cell %d has no faces", i);
+  }
+  std::vector<int32_t> csr(2 * (size_t)F);
+  {
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int f = 0; f < F; ++f) {     // ascending face index within each cell
+      csr[fill[L[f]]++] = f << 1;
+      csr[fill[Rr[f]]++] = (f << 1) | 1;
+    }
+  }
+  ctx->max_deg = maxdeg;
+  ctx->min_dx_cm = std::cbrt(minV) * ctx->cfg.unit_length_cm;
+
+  rt_status st;
+#define AL(p, n) if ((st = dalloc(ctx, &(p), (n), #p))) return st
+  AL(ctx->vol, C); AL(ctx->cx, C); AL(ctx->cy, C); AL(ctx->cz, C);
+  AL(ctx->off, C + 1); AL(ctx->csr, 2 * (size_t)F); AL(ctx->lr, F);
+  AL(ctx->nA64, F); AL(ctx->rL64, F); AL(ctx->rR64, F); AL(ctx->w64, F); AL(ctx->minv64, 6 * (size_t)C);
+  AL(ctx->rad, (size_t)C * B); AL(ctx->nH, C); AL(ctx->x5, 5 * (size_t)C); AL(ctx->T, C);
+  AL(ctx->src_idx, C); AL(ctx->nsub, C); AL(ctx->status, 1);
+  ctx->stage_n = std::max<size_t>(4 * (size_t)B * C, 7 * (size_t)F);
+  ctx->stage_n = std::max<size_t>(ctx->stage_n, 5 * (size_t)C);
+  AL(ctx->stage, ctx->stage_n);
+  const bool mx = mixed(ctx);
+  const size_t rs = mx ? 4 : 8;
+  {
+    void* p;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>((size_t)C * B * 12 * rs, 1));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "G");
+    ctx->allocs.push_back(p); ctx->G = p;
+    e = cudaMalloc(&p, std::max<size_t>((size_t)F * B * 4 * rs, 1));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "flux");
+    ctx->allocs.push_back(p); ctx->flux = p;
+  }
+  if (mx) {
+    AL(ctx->nA32, F); AL(ctx->rL32, F); AL(ctx->rR32, F); AL(ctx->w32, F); AL(ctx->minv32, 6 * (size_t)C);
+    AL(ctx->shadow, (size_t)C * B);
+  }
+#undef AL
+  if ((st = copy_in(ctx, ctx->vol, cells->volume, (size_t)C * 8))) return st;
+  if ((st = copy_in(ctx, ctx->cx, cells->cx, (size_t)C * 8))) return st;
+  if ((st = copy_in(ctx, ctx->cy, cells->cy, (size_t)C * 8))) return st;
+  if ((st = copy_in(ctx, ctx->cz, cells->cz, (size_t)C * 8))) return st;
+  CK(cudaMemcpyAsync(ctx->off, off.data(), (C + 1) * 4, cudaMemcpyHostToDevice, ctx->stream), "off");
+  CK(cudaMemcpyAsync(ctx->csr, csr.data(), 2 * (size_t)F * 4, cudaMemcpyHostToDevice, ctx->stream), "csr");
+  {
+    std::vector<int2> lr(F);
+    for (int f = 0; f < F; ++f) lr[f] = make_int2(L[f], Rr[f]);
+    CK(cudaMemcpyAsync(ctx->lr, lr.data(), (size_t)F * 8, cudaMemcpyHostToDevice, ctx->stream), "lr");
+    CK(cudaStreamSynchronize(ctx->stream), "mesh upload");
+  }
+  // face arrays through the staging buffer: area, n, x_f
+  double* sA = ctx->stage;
+  double *snx = sA + F, *sny = sA + 2 * (size_t)F, *snz = sA + 3 * (size_t)F;
+  double *sfx = sA + 4 * (size_t)F, *sfy = sA + 5 * (size_t)F, *sfz = sA + 6 * (size_t)F;
+  if (F > 0) {
+    if ((st = copy_in(ctx, sA, faces->area, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, snx, faces->nx, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, sny, faces->ny, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, snz, faces->nz, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, sfx, faces->fx, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, sfy, faces->fy, (size_t)F * 8))) return st;
+    if ((st = copy_in(ctx, sfz, faces->fz, (size_t)F * 8))) return st;
+    k_pack_nA<<<nblk(F), kThreads, 0, ctx->stream>>>(F, snx, sny, snz, sA, ctx->nA64);
+    k_geometry_faces<<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->cfg.box, ctx->lr, ctx->cx, ctx->cy, ctx->cz,
+                                                            sfx, sfy, sfz, sA, ctx->rL64, ctx->rR64, ctx->w64);
+  }
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  k_geometry_cells<<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->cfg.box, ctx->off, ctx->csr, ctx->lr, ctx->cx,
+                                                          ctx->cy, ctx->cz, sA, ctx->minv64, ctx->status);
+  if (mx && F > 0) {
+    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->nA64, ctx->nA32);
+    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->rL64, ctx->rL32);
+    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->rR64, ctx->rR32);
+    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->w64, ctx->w32);
+  }
+  if (mx) k_convert<float><<<nblk(6LL * C), kThreads, 0, ctx->stream>>>(6 * C, ctx->minv64, ctx->minv32);
+  if ((st = launched(ctx, "geometry kernels"))) return st;
+  int h_status = 0;
+  CK(cudaMemcpyAsync(&h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
+  CK(cudaStreamSynchronize(ctx->stream), "geometry");
+  if (h_status & kStSingular) return fail(ctx, RT_BAD_MESH, "singular least-squares matrix (degenerate cell)");
+  // default state: no radiation, neutral gas at 1e4 K, no sources
+  CK(cudaMemsetAsync(ctx->rad, 0, (size_t)C * B * sizeof(d4), ctx->stream), "state");
+  CK(cudaMemsetAsync(ctx->nH, 0, (size_t)C * 8, ctx->stream), "state");
+  CK(cudaMemsetAsync(ctx->nsub, 0, (size_t)C * 4, ctx->stream), "state");
+  CK(cudaMemsetAsync(ctx->src_idx, 0xff, (size_t)C * 4, ctx->stream), "state");
+  {
+    std::vector<double> x(5 * (size_t)C, 0.0), T(C, 1e4);
+    std::fill(x.begin(), x.begin() + C, 1.0);
+    std::fill(x.begin() + 2 * (size_t)C, x.begin() + 3 * (size_t)C, 1.0);
+    CK(cudaMemcpyAsync(ctx->x5, x.data(), x.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "state");
+    CK(cudaMemcpyAsync(ctx->T, T.data(), T.size() * 8, cudaMemcpyHostToDevice, ctx->stream), "state");
+    CK(cudaStreamSynchronize(ctx->stream), "state");
+  }
+  ctx->n_src_cells = 0;
+  refresh_shadow(ctx);
+  if ((st = launched(ctx, "state init"))) return st;
+  ctx->mesh_ready = true;
+  return RT_OK;
+}
+
+rt_status rt_set_gas(rt_ctx* ctx, const double* nH, const double* x5, const double* T) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!nH || !x5 || !T) return fail(ctx, RT_INVALID_ARG, "gas array is NULL");
+  const size_t C = ctx->C;
+  if ((st = copy_in(ctx, ctx->nH, nH, C * 8))) return st;
+  if ((st = copy_in(ctx, ctx->x5, x5, 5 * C * 8))) return st;
+  if ((st = copy_in(ctx, ctx->T, T, C * 8))) return st;
+  return RT_OK;
+}
+
+rt_status rt_set_radiation(rt_ctx* ctx, const double* N, const double* F) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!N) return fail(ctx, RT_INVALID_ARG, "N is NULL");
+  const size_t C = ctx->C, B = ctx->B;
+  double* sN = ctx->stage;
+  double* sF = ctx->stage + B * C;
+  if ((st = copy_in(ctx, sN, N, B * C * 8))) return st;
+  if (F && (st = copy_in(ctx, sF, F, 3 * B * C * 8))) return st;
+  k_pack_rad<<<nblk((long long)B * C), kThreads, 0, ctx->stream>>>((int)C, (int)B, 1.0 / ctx->cfg.c_red, sN,
+                                                                   F ? sF : nullptr, ctx->rad);
+  refresh_shadow(ctx);
+  return launched(ctx, "set radiation");
+}
+
+rt_status rt_set_sources(rt_ctx* ctx, int64_t n, const int64_t* cell, const double* Q) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (n < 0 || (n > 0 && (!cell || !Q))) return fail(ctx, RT_INVALID_ARG, "bad source arrays");
+  const int B = ctx->B;
+  std::vector<int64_t> hc(n);
+  std::vector<double> hq((size_t)n * B);
+  if (n > 0) {
+    CK(cudaMemcpy(hc.data(), cell, n * 8, is_device_ptr(cell) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+       "sources");
+    CK(cudaMemcpy(hq.data(), Q, n * B * 8, is_device_ptr(Q) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+       "sources");
+  }
+  // bin rates per cell, summed in source order
+  std::vector<int32_t> idx(ctx->C, -1);
+  std::vector<double> rate;
+  int m = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    if (hc[k] < 0 || hc[k] >= ctx->C) return fail(ctx, RT_INVALID_ARG, "source %lld in cell %lld out of range",
+                                                  (long long)k, (long long)hc[k]);
+    int32_t& s = idx[hc[k]];
+    if (s < 0) {
+      s = m++;
+      rate.resize((size_t)m * B, 0.0);
+    }
+    for (int b = 0; b < B; ++b) rate[(size_t)s * B + b] += hq[(size_t)k * B + b];
+  }
+  if (m > ctx->src_cap) {
+    double* p = nullptr;
+    if ((st = dalloc(ctx, &p, (size_t)m * B, "source rates"))) return st;
+    ctx->src_rate = p;
+    ctx->src_cap = m;
+  }
+  CK(cudaMemcpyAsync(ctx->src_idx, idx.data(), (size_t)ctx->C * 4, cudaMemcpyHostToDevice, ctx->stream),
+     "sources");
+  if (m > 0)
+    CK(cudaMemcpyAsync(ctx->src_rate, rate.data(), (size_t)m * B * 8, cudaMemcpyHostToDevice, ctx->stream),
+       "sources");
+  CK(cudaStreamSynchronize(ctx->stream), "sources");
+  ctx->n_src_cells = m;
+  return RT_OK;
+}
+
+rt_status rt_max_dt(rt_ctx* ctx, double* out) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!out) return fail(ctx, RT_INVALID_ARG, "out is NULL");
+  *out = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
+  return RT_OK;
+}
+
+rt_status rt_mesh_info(rt_ctx* ctx, int64_t* n_cells, int64_t* n_faces, int32_t* max_degree) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (n_cells) *n_cells = ctx->C;
+  if (n_faces) *n_faces = ctx->F;
+  if (max_degree) *max_degree = ctx->max_deg;
+  return RT_OK;
+}
+
+rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (n_sub < 1 || !(dt > 0) || !std::isfinite(dt)) return fail(ctx, RT_INVALID_ARG, "need dt > 0 and n_sub >= 1");
+  const double dts = dt / n_sub;
+  const double dmax = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
+  if (dts > dmax * (1.0 + 1e-12))
+    return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
+  // Subcycle s: sources + chemistry, gradients, fluxes, application.  The
+  // application of subcycle s is fused with the sources and chemistry of
+  // subcycle s+1 in one per-cell kernel.
+  for (int s = 0; s < n_sub; ++s) {
+    launch_cell(ctx, dts, s > 0, 1, 1);
+    launch_grad_any(ctx);
+    launch_flux_any(ctx);
+  }
+  launch_cell(ctx, dts, 1, 0, 0);
+  return launched(ctx, "rt_step");
+}
+
+rt_status rt_sync(rt_ctx* ctx) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
+  CK(cudaStreamSynchronize(ctx->stream), "rt_sync");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  if (h & kStNonFinite) return fail(ctx, RT_NONFINITE, "non-finite photon density");
+  if (h & kStChemSubsteps) return fail(ctx, RT_CHEM_SUBSTEPS, "a cell reached max_substeps");
+  return RT_OK;
+}
+
+rt_status rt_get_fields(rt_ctx* ctx, uint32_t mask, double* const* out) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!out && mask) return fail(ctx, RT_INVALID_ARG, "out is NULL");
+  const size_t C = ctx->C, B = ctx->B;
+  int k = 0;
+  if (mask & (RT_FIELD_N | RT_FIELD_F)) {
+    double* sN = ctx->stage;
+    double* sF = ctx->stage + B * C;
+    k_unpack_rad<<<nblk((long long)B * C), kThreads, 0, ctx->stream>>>((int)C, (int)B, ctx->cfg.c_red, ctx->rad,
+                                                                        sN, sF);
+    if ((st = launched(ctx, "get fields"))) return st;
+    if (mask & RT_FIELD_N) {
+      if (!out[k]) return fail(ctx, RT_INVALID_ARG, "output %d is NULL", k);
+      if ((st = copy_out(ctx, out[k++], sN, B * C * 8))) return st;
+    }
+    if (mask & RT_FIELD_F) {
+      if (!out[k]) return fail(ctx, RT_INVALID_ARG, "output %d is NULL", k);
+      if ((st = copy_out(ctx, out[k++], sF, 3 * B * C * 8))) return st;
+    }
+  }
+  if (mask & RT_FIELD_X) {
+    if (!out[k]) return fail(ctx, RT_INVALID_ARG, "output %d is NULL", k);
+    if ((st = copy_out(ctx, out[k++], ctx->x5, 5 * C * 8))) return st;
+  }
+  if (mask & RT_FIELD_T) {
+    if (!out[k]) return fail(ctx, RT_INVALID_ARG, "output %d is NULL", k);
+    if ((st = copy_out(ctx, out[k++], ctx->T, C * 8))) return st;
+  }
+  if (mask & RT_FIELD_NSUB) {
+    if (!out[k]) return fail(ctx, RT_INVALID_ARG, "output %d is NULL", k);
+    std::vector<int32_t> h(C);
+    CK(cudaMemcpyAsync(h.data(), ctx->nsub, C * 4, cudaMemcpyDeviceToHost, ctx->stream), "nsub");
+    CK(cudaStreamSynchronize(ctx->stream), "nsub");
+    std::vector<double> d(h.begin(), h.end());
+    if ((st = copy_in(ctx, ctx->stage, d.data(), C * 8))) return st;
+    if ((st = copy_out(ctx, out[k++], ctx->stage, C * 8))) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "get fields");
+  return RT_OK;
+}
+
+// ---- stage entry points -----------------------------------------------------
+
+rt_status rt_stage_gradients(rt_ctx* ctx, double* G) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  launch_grad_any(ctx);
+  if ((st = launched(ctx, "gradients"))) return st;
+  if (!G) return RT_OK;
+  const size_t n = (size_t)ctx->C * ctx->B * 12;
+  if (mixed(ctx)) {
+    // widen in a host buffer
+    std::vector<float> h(n);
+    CK(cudaMemcpyAsync(h.data(), ctx->G, n * 4, cudaMemcpyDeviceToHost, ctx->stream), "gradients");
+    CK(cudaStreamSynchronize(ctx->stream), "gradients");
+    std::vector<double> d(h.begin(), h.end());
+    if (is_device_ptr(G)) {
+      CK(cudaMemcpy(G, d.data(), n * 8, cudaMemcpyHostToDevice), "gradients");
+    } else {
+      std::memcpy(G, d.data(), n * 8);
+    }
+    return RT_OK;
+  }
+  return copy_out(ctx, G, ctx->G, n * 8);
+}
+
+rt_status rt_stage_fluxes(rt_ctx* ctx, const double* G, double* flux) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  const size_t nG = (size_t)ctx->C * ctx->B * 12, nF = (size_t)ctx->F * ctx->B * 4;
+  if (G) {
+    if (mixed(ctx)) {
+      std::vector<double> d(nG);
+      CK(cudaMemcpy(d.data(), G, nG * 8, is_device_ptr(G) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "G");
+      std::vector<float> h(d.begin(), d.end());
+      CK(cudaMemcpy(ctx->G, h.data(), nG * 4, cudaMemcpyHostToDevice), "G");
+    } else if ((st = copy_in(ctx, ctx->G, G, nG * 8))) {
+      return st;
+    }
+  } else {
+    launch_grad_any(ctx);
+  }
+  launch_flux_any(ctx);
+  if ((st = launched(ctx, "fluxes"))) return st;
+  if (!flux) return RT_OK;
+  if (mixed(ctx)) {
+    std::vector<float> h(nF);
+    CK(cudaMemcpyAsync(h.data(), ctx->flux, nF * 4, cudaMemcpyDeviceToHost, ctx->stream), "fluxes");
+    CK(cudaStreamSynchronize(ctx->stream), "fluxes");
+    std::vector<double> d(h.begin(), h.end());
+    if (is_device_ptr(flux)) CK(cudaMemcpy(flux, d.data(), nF * 8, cudaMemcpyHostToDevice), "fluxes");
+    else std::memcpy(flux, d.data(), nF * 8);
+    return RT_OK;
+  }
+  return copy_out(ctx, flux, ctx->flux, nF * 8);
+}
+
+rt_status rt_stage_transport(rt_ctx* ctx, double dt) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!(dt >= 0)) return fail(ctx, RT_INVALID_ARG, "dt must be >= 0");
+  launch_grad_any(ctx);
+  launch_flux_any(ctx);
+  launch_cell(ctx, dt, 1, 0, 0);
+  return launched(ctx, "transport");
+}
+
+rt_status rt_stage_chemistry(rt_ctx* ctx, double dt) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (!(dt >= 0)) return fail(ctx, RT_INVALID_ARG, "dt must be >= 0");
+  launch_cell(ctx, dt, 0, 1, 1);
+  return launched(ctx, "chemistry");
+}
+
+rt_status rt_profile_enable(rt_ctx* ctx, int on) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  ctx->profiling = on != 0;
+  return RT_OK;
+}
+
+rt_status rt_profile_read(rt_ctx* ctx, int n, double* ms, int64_t* launches, int reset) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  CK(cudaStreamSynchronize(ctx->stream), "profile");
+  for (auto& u : ctx->ev_used) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, ctx->ev_pool[u.second], ctx->ev_pool[u.second + 1]), "profile");
+    ctx->prof_ms[u.first] += t;
+    ctx->prof_n[u.first] += 1;
+  }
+  ctx->ev_used.clear();
+  for (int k = 0; k < n && k < RT_KERNEL_COUNT; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
+  if (reset)
+    for (int k = 0; k < RT_KERNEL_COUNT; ++k) { ctx->prof_ms[k] = 0; ctx->prof_n[k] = 0; }
+  return RT_OK;
+}
+
+rt_status rt_launch_count(rt_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return fail(ctx, RT_INVALID_ARG, "null argument");
+  *out = ctx->launches;
+  return RT_OK;
+}
+
+const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void rt_destroy(rt_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  free_all(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// Device thermochemistry of one cell over one subcycle (Sec. 2.3.1, 4.1.1).
+//
+// State and update arithmetic are FP64 in both precision modes.  With
+// FastRates the temperature-dependent rate coefficients (fits with exp/pow)
+// are evaluated in FP32 with hardware intrinsics, as Sec. 6.2 proposes for
+// the chemistry solver; the rate fits themselves carry percent-level
+// uncertainty, far above FP32 rounding.
+#pragma once
+#include "rt_common.cuh"
+
+namespace m1rt {
+
+struct ChemParams {
+  int B;
+  int mode;          // 1 isothermal, 2 thermal energy evolves
+  int flags;         // bit0 recombination, bit1 collisional ionisation, bit2 cooling, bit3 photoheating
+  double c_red;
+  double y_he;
+  double f_s, f_max, x_floor;
+  int max_sub;
+  double sigma[kMaxBins][3];
+  double eps[kMaxBins][3];
+};
+
+constexpr double kBoltzmann = 1.380649e-16;
+
+// Rate coefficients at temperature T (cm^3/s), cooling (erg cm^-3 s^-1).
+// Case-B recombination of HII and HeIII: Hui & Gnedin (1997); HeII case B
+// plus dielectronic; collisional ionisation and cooling: Katz, Weinberg &
+// Hernquist (1996).
+struct Rates {
+  double aHII, aHeII, aHeIII, bHI, bHeI, bHeII;
+};
+
+template <bool Fast> struct RateEval;
+
+template <> struct RateEval<false> {
+  __device__ static Rates eval(double T) {
+    Rates r;
+    double lH = 2.0 * 157807.0 / T;
+    r.aHII = 2.753e-14 * pow(lH, 1.5) / pow(1.0 + pow(lH / 2.740, 0.407), 2.242);
+    double lHe = 2.0 * 285335.0 / T;
+    r.aHeII = 1.26e-14 * pow(lHe, 0.750) +
+              1.9e-3 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
+    double lHe2 = 2.0 * 631515.0 / T;
+    r.aHeIII = 2.0 * 2.753e-14 * pow(lHe2, 1.5) / pow(1.0 + pow(lHe2 / 2.740, 0.407), 2.242);
+    double tf = 1.0 / (1.0 + sqrt(T / 1e5));
+    double sT = sqrt(T);
+    r.bHI = 5.85e-11 * sT * exp(-157809.1 / T) * tf;
+    r.bHeI = 2.38e-11 * sT * exp(-285335.4 / T) * tf;
+    r.bHeII = 5.68e-12 * sT * exp(-631515.0 / T) * tf;
+    return r;
+  }
+  __device__ static double cooling(double T, double ne, double nHI, double nHII, double nHeI, double nHeII,
+                                   double nHeIII) {
+    double sT = sqrt(T), tf = 1.0 / (1.0 + sqrt(T / 1e5));
+    double ce = 7.50e-19 * exp(-118348.0 / T) * tf * ne * nHI +
+                5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * tf * ne * nHeII;
+    double ci = 1.27e-21 * sT * exp(-157809.1 / T) * tf * ne * nHI +
+                9.38e-22 * sT * exp(-285335.4 / T) * tf * ne * nHeI +
+                4.95e-22 * sT * exp(-631515.0 / T) * tf * ne * nHeII;
+    double t3 = pow(T / 1e3, -0.2) / (1.0 + pow(T / 1e6, 0.7));
+    double rc = 8.70e-27 * sT * t3 * ne * nHII + 1.55e-26 * pow(T, 0.3647) * ne * nHeII +
+                3.48e-26 * sT * t3 * ne * nHeIII +
+                1.24e-13 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T)) * ne * nHeII;
+    double lg = log10(T);
+    double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+    double br = 1.42e-27 * gff * sT * (nHII + nHeII + 4.0 * nHeIII) * ne;
+    return ce + ci + rc + br;
+  }
+};
+
+// FP32 intrinsics: x^p = 2^(p log2 x), e^x = 2^(x log2 e).
+__device__ __forceinline__ float fpow(float x, float p) { return exp2f(p * __log2f(x)); }
+__device__ __forceinline__ float fexp(float x) { return exp2f(x * 1.4426950408889634f); }
+
+template <> struct RateEval<true> {
+  __device__ static Rates eval(double Td) {
+    float T = (float)Td;
+    float iT = __frcp_rn(T);
+    Rates r;
+    float lH = 315614.0f * iT;
+    r.aHII = 2.753e-14f * fpow(lH, 1.5f) / fpow(1.0f + fpow(lH * (1.0f / 2.740f), 0.407f), 2.242f);
+    float lHe = 570670.0f * iT;
+    r.aHeII = 1.26e-14f * fpow(lHe, 0.750f) +
+              1.9e-3f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    float lHe2 = 1263030.0f * iT;
+    r.aHeIII = 2.0f * 2.753e-14f * fpow(lHe2, 1.5f) / fpow(1.0f + fpow(lHe2 * (1.0f / 2.740f), 0.407f), 2.242f);
+    float sT = sqrtf(T);
+    float tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
+    r.bHI = 5.85e-11f * sT * fexp(-157809.1f * iT) * tf;
+    r.bHeI = 2.38e-11f * sT * fexp(-285335.4f * iT) * tf;
+    r.bHeII = 5.68e-12f * sT * fexp(-631515.0f * iT) * tf;
+    return r;
+  }
+  __device__ static double cooling(double Td, double ne, double nHI, double nHII, double nHeI, double nHeII,
+                                   double nHeIII) {
+    float T = (float)Td, iT = __frcp_rn(T);
+    float sT = sqrtf(T), tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
+    // coefficients in FP32 (erg cm^3 s^-1 scale fits FP32), densities in FP64
+    double c_ceH = 7.50e-19f * fexp(-118348.0f * iT) * tf;
+    double c_ceHe = 5.54e-17f * fpow(T, -0.397f) * fexp(-473638.0f * iT) * tf;
+    double c_ciH = 1.27e-21f * sT * fexp(-157809.1f * iT) * tf;
+    double c_ciHe = 9.38e-22f * sT * fexp(-285335.4f * iT) * tf;
+    double c_ciHe2 = 4.95e-22f * sT * fexp(-631515.0f * iT) * tf;
+    float t3 = fpow(T * 1e-3f, -0.2f) / (1.0f + fpow(T * 1e-6f, 0.7f));
+    double c_rH = 8.70e-27f * sT * t3;
+    double c_rHe = 1.55e-26f * fpow(T, 0.3647f);
+    double c_rHe2 = 3.48e-26f * sT * t3;
+    double c_di = 1.24e-13f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    float lg = __log10f(T);
+    double c_br = 1.42e-27f * (1.1f + 0.34f * fexp(-(5.5f - lg) * (5.5f - lg) * (1.0f / 3.0f))) * sT;
+    return ne * (c_ceH * nHI + c_ceHe * nHeII + c_ciH * nHI + c_ciHe * nHeI + c_ciHe2 * nHeII +
+                 c_rH * nHII + c_rHe * nHeII + c_rHe2 * nHeIII + c_di * nHeII +
+                 c_br * (nHII + nHeII + 4.0 * nHeIII));
+  }
+};
+
+// Per-cell state of the photochemistry step.
+struct CellState {
+  double N[kMaxBins];
+  double f[kMaxBins][3];   // reduced flux F / c_red
+  double xHI, xHII, yI, yII, yIII, T;
+};
+
+__device__ __forceinline__ double rel_change(double a, double b, double fl) {
+  double m = fabs(a) > fl ? fabs(a) : fl;
+  return fabs(b - a) / m;
+}
+
+// One semi-implicit photochemistry attempt over dt from s into t; returns the
+// largest relative change f of the substep rule.  Steps: radiation level
+// over the step (implicit in N, absorbers at the start); photoionisation
+// rates from it; backward Euler for H, then for He with the updated n_e;
+// photons removed = photoionisations credited (absorbers at the end), F scaled
+// alike; thermal energy explicit.
+template <bool Fast>
+__device__ double photochem_attempt(const ChemParams& P, double nH, double dt, const CellState& s, CellState& t) {
+  const int B = P.B;
+  const double c = P.c_red;
+  const double nHe = P.y_he * nH;
+  const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
+  const Rates r = RateEval<Fast>::eval(s.T);
+
+  double ns0 = nH * s.xHI, ns1 = nHe * s.yI, ns2 = nHe * s.yII;
+  double Nbar[kMaxBins];
+  double G0 = 0, G1 = 0, G2 = 0;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      double kap = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
+      Nbar[b] = s.N[b] / (1.0 + c * dt * kap);
+      G0 += c * P.sigma[b][0] * Nbar[b];
+      G1 += c * P.sigma[b][1] * Nbar[b];
+      G2 += c * P.sigma[b][2] * Nbar[b];
+    }
+  }
+  double ne0 = nH * s.xHII + nHe * (s.yII + 2.0 * s.yIII);
+  double aH = dt * (G0 + (coll ? r.bHI * ne0 : 0.0));
+  double bH = recomb ? dt * r.aHII * ne0 : 0.0;
+  double den = 1.0 + aH + bH;
+  t.xHI = (s.xHI * (1.0 + bH) + bH * s.xHII) / den;
+  t.xHII = (s.xHII * (1.0 + aH) + aH * s.xHI) / den;
+  double ne1 = nH * t.xHII + nHe * (s.yII + 2.0 * s.yIII);
+  double A = dt * (G1 + (coll ? r.bHeI * ne1 : 0.0));
+  double Bb = recomb ? dt * r.aHeII * ne1 : 0.0;
+  double Cc = dt * (G2 + (coll ? r.bHeII * ne1 : 0.0));
+  double D = recomb ? dt * r.aHeIII * ne1 : 0.0;
+  double opA = 1.0 + A, opD = 1.0 + D;
+  t.yII = (s.yII + A * s.yI / opA + D * s.yIII / opD) / (1.0 + Bb / opA + Cc / opD);
+  t.yI = (s.yI + Bb * t.yII) / opA;
+  t.yIII = (s.yIII + Cc * t.yII) / opD;
+
+  double m0 = nH * t.xHI, m1 = nHe * t.yI, m2 = nHe * t.yII;
+  double heat_e = 0.0;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      double i0 = c * dt * Nbar[b] * P.sigma[b][0] * m0;
+      double i1 = c * dt * Nbar[b] * P.sigma[b][1] * m1;
+      double i2 = c * dt * Nbar[b] * P.sigma[b][2] * m2;
+      heat_e += P.eps[b][0] * i0 + P.eps[b][1] * i1 + P.eps[b][2] * i2;
+      double N1 = s.N[b] - ((i0 + i1) + i2);
+      if (N1 < 0) N1 = 0;
+      double sc = s.N[b] > 0 ? N1 / s.N[b] : 0.0;
+      t.N[b] = N1;
+      t.f[b][0] = s.f[b][0] * sc;
+      t.f[b][1] = s.f[b][1] * sc;
+      t.f[b][2] = s.f[b][2] * sc;
+    }
+  }
+  double f = 0.0;
+  if (P.mode == 2) {
+    double ntot0 = nH * (1.0 + P.y_he) + ne0;
+    double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
+    double lam = cool ? RateEval<Fast>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
+                                                nHe * s.yIII)
+                      : 0.0;
+    double e1 = e0 + (heat ? heat_e : 0.0) - dt * lam;
+    double ne2 = nH * t.xHII + nHe * (t.yII + 2.0 * t.yIII);
+    double ntot1 = nH * (1.0 + P.y_he) + ne2;
+    t.T = e1 / (1.5 * kBoltzmann * ntot1);
+    f = rel_change(e0, e1, 0.0);
+  } else {
+    t.T = s.T;
+  }
+  f = fmax(f, rel_change(s.xHI, t.xHI, P.x_floor));
+  f = fmax(f, rel_change(s.xHII, t.xHII, P.x_floor));
+  if (P.y_he > 0) {
+    f = fmax(f, rel_change(s.yI, t.yI, P.x_floor));
+    f = fmax(f, rel_change(s.yII, t.yII, P.x_floor));
+    f = fmax(f, rel_change(s.yIII, t.yIII, P.x_floor));
+  }
+  return f;
+}
+
+// Adaptive substeps of Sec. 4.1.1 over dt_sub: first attempt = the whole
+// subcycle; reject if f > f_max and retry with dt f_s / f; after an accepted
+// attempt the next is dt min(f_s / f, 2), clipped to the remaining time.
+// Returns the number of attempts; sets *capped if max_sub was reached.
+template <bool Fast>
+__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {
+  double rem = dt_sub, dt = dt_sub;
+  int n = 0;
+  CellState t;
+  *capped = false;
+  while (rem > 0) {
+    if (n >= P.max_sub) { *capped = true; break; }
+    ++n;
+    double f = photochem_attempt<Fast>(P, nH, dt, s, t);
+    if (f > P.f_max) {
+      dt = dt * (P.f_s / f);
+      continue;
+    }
+    s = t;
+    rem = (dt == rem) ? 0.0 : rem - dt;
+    double grow = (f > 0) ? P.f_s / f : 2.0;
+    if (grow > 2.0) grow = 2.0;
+    dt = dt * grow;
+    if (dt > rem) dt = rem;
+  }
+  return n;
+}
+
+}  // namespace m1rt

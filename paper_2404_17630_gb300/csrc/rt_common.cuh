@@ -1,0 +1,56 @@
+// Shared device-side types and helpers of the M1 RT subcycle kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace m1rt {
+
+constexpr int kMaxBins = 3;
+
+// Status bits collected on the device (atomicOr) and read by rt_sync.
+constexpr int kStChemSubsteps = 1;
+constexpr int kStNonFinite = 2;
+constexpr int kStSingular = 4;
+
+// 32-byte aligned 4-vector of doubles (one 256-bit access).
+using d4 = double4_32a;
+__host__ __device__ __forceinline__ d4 make_d4(double x, double y, double z, double w) {
+  d4 v;
+  v.x = x; v.y = y; v.z = z; v.w = w;
+  return v;
+}
+
+// 4-wide vector of the sweep precision.
+template <class R> struct V4;
+template <> struct V4<double> { using T = d4; };
+template <> struct V4<float> { using T = float4; };
+template <class R> using R4 = typename V4<R>::T;
+
+template <class R> __device__ __forceinline__ R4<R> ld4(const R4<R>* p) { return __ldg(p); }
+template <> __device__ __forceinline__ d4 ld4<double>(const d4* p) { return *p; }
+
+template <class R> __device__ __forceinline__ R mk(double v) { return static_cast<R>(v); }
+
+__device__ __forceinline__ double rint_away(double x) { return round(x); }
+__device__ __forceinline__ float rint_away(float x) { return roundf(x); }
+
+// Periodic minimum image of a coordinate difference, d - L round(d / L),
+// evaluated without contraction so that it rounds like the plain expression.
+__device__ __forceinline__ double min_image(double d, double L) {
+  return L > 0.0 ? __dsub_rn(d, __dmul_rn(L, round(__ddiv_rn(d, L)))) : d;
+}
+
+// Mesh geometry in the sweep precision R, plus FP64 cell data.
+template <class R> struct Geo {
+  int C, F, B;
+  const int32_t* off;     // C+1 CSR offsets
+  const int32_t* csr;     // 2F entries: (face << 1) | side, side 1 = this cell is the right cell
+  const int2* lr;         // F: (left, right)
+  const R4<R>* nA;        // F: (n_x, n_y, n_z, A)
+  const R4<R>* rL;        // F: x_f - s_L (minimum image), w unused
+  const R4<R>* rR;        // F: x_f - s_R
+  const R4<R>* w;         // F: A d / |d|^2 with d = s_R - s_L
+  const R* minv;          // 6C: symmetric inverse of sum A n n^T (xx, xy, xz, yy, yz, zz)
+};
+
+}  // namespace m1rt

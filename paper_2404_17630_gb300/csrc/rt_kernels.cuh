@@ -1,0 +1,411 @@
+// Kernels of the M1 RT subcycle.
+//
+//   k_geometry_*   once per mesh (Sec. 2.3.2: the least-squares matrix depends
+//                  only on geometry and is inverted once)
+//   k_grad<R>      least-squares gradients + slope limiter, one thread per
+//                  (cell, bin)  (Sec. 2.3.2, 4.1.2)
+//   k_flux<R>      face reconstruction, M1 closure, Lax-Friedrichs flux, one
+//                  thread per (face, bin)  (Sec. 2.3.3, 4.1.3)
+//   k_cell<R,Fast> per cell: deterministic CSR gather of the stored face
+//                  fluxes with FP64 accumulation, source injection and
+//                  thermochemistry (Sec. 4.1.3, Eq. E, Sec. 4.1.1)
+//
+// R is the precision of the transport sweep (double, or float in the mixed
+// mode of Sec. 6.2); the master state, the gather sums, the volume divisions
+// and the chemistry are FP64 in both.
+#pragma once
+#include "rt_chem.cuh"
+
+namespace m1rt {
+
+// ---------------------------------------------------------------------------
+// geometry (FP64), once per mesh
+// ---------------------------------------------------------------------------
+
+// Per face: x_f - s_L, x_f - s_R (minimum image), d = s_R - s_L and
+// w = A d / |d|^2 (the face's weight in the right-hand side of the normal
+// equation, the same for both of its cells).
+__global__ void k_geometry_faces(int F, double box, const int2* __restrict__ lr, const double* __restrict__ cx,
+                                 const double* __restrict__ cy, const double* __restrict__ cz,
+                                 const double* __restrict__ fx, const double* __restrict__ fy,
+                                 const double* __restrict__ fz, const double* __restrict__ area,
+                                 d4* rL, d4* rR, d4* w) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  int2 c = lr[f];
+  double a0 = min_image(fx[f] - cx[c.x], box), a1 = min_image(fy[f] - cy[c.x], box),
+         a2 = min_image(fz[f] - cz[c.x], box);
+  double b0 = min_image(fx[f] - cx[c.y], box), b1 = min_image(fy[f] - cy[c.y], box),
+         b2 = min_image(fz[f] - cz[c.y], box);
+  double d0 = min_image(cx[c.y] - cx[c.x], box), d1 = min_image(cy[c.y] - cy[c.x], box),
+         d2 = min_image(cz[c.y] - cz[c.x], box);
+  double dd = d0 * d0 + d1 * d1 + d2 * d2;
+  double s = area[f] / dd;
+  rL[f] = make_d4(a0, a1, a2, 0.0);
+  rR[f] = make_d4(b0, b1, b2, 0.0);
+  w[f] = make_d4(s * d0, s * d1, s * d2, 0.0);
+}
+
+// Per cell: M = sum_f A n n^T with n = d / |d| towards the neighbour, and its
+// inverse (symmetric, 6 entries).  Flags a singular matrix.
+__global__ void k_geometry_cells(int C, double box, const int32_t* __restrict__ off,
+                                 const int32_t* __restrict__ csr, const int2* __restrict__ lr,
+                                 const double* __restrict__ cx, const double* __restrict__ cy,
+                                 const double* __restrict__ cz, const double* __restrict__ area,
+                                 double* minv, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C) return;
+  double m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
+  for (int k = off[i]; k < off[i + 1]; ++k) {
+    int e = csr[k], f = e >> 1;
+    int j = (e & 1) ? lr[f].x : lr[f].y;
+    double d0 = min_image(cx[j] - cx[i], box), d1 = min_image(cy[j] - cy[i], box),
+           d2 = min_image(cz[j] - cz[i], box);
+    double dl = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    double n0 = d0 / dl, n1 = d1 / dl, n2 = d2 / dl;
+    double A = area[f];
+    m00 += A * n0 * n0; m01 += A * n0 * n1; m02 += A * n0 * n2;
+    m11 += A * n1 * n1; m12 += A * n1 * n2; m22 += A * n2 * n2;
+  }
+  double c00 = m11 * m22 - m12 * m12, c01 = m12 * m02 - m01 * m22, c02 = m01 * m12 - m11 * m02;
+  double det = m00 * c00 + m01 * c01 + m02 * c02;
+  double* o = minv + 6 * i;
+  if (!(det != 0.0) || !isfinite(det)) {
+    atomicOr(status, kStSingular);
+    for (int q = 0; q < 6; ++q) o[q] = 0.0;
+    return;
+  }
+  o[0] = c00 / det;
+  o[1] = c01 / det;
+  o[2] = c02 / det;
+  o[3] = (m00 * m22 - m02 * m02) / det;
+  o[4] = (m02 * m01 - m00 * m12) / det;
+  o[5] = (m00 * m11 - m01 * m01) / det;
+}
+
+template <class R> __global__ void k_convert4(int n, const d4* __restrict__ in, R4<R>* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  d4 v = in[k];
+  R4<R> o;
+  o.x = (R)v.x; o.y = (R)v.y; o.z = (R)v.z; o.w = (R)v.w;
+  out[k] = o;
+}
+
+template <class R> __global__ void k_convert(int n, const double* __restrict__ in, R* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = (R)in[k];
+}
+
+__global__ void k_pack_nA(int F, const double* __restrict__ nx, const double* __restrict__ ny,
+                          const double* __restrict__ nz, const double* __restrict__ area, d4* nA) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < F) nA[f] = make_d4(nx[f], ny[f], nz[f], area[f]);
+}
+
+// ---------------------------------------------------------------------------
+// state packing: component-major caller arrays <-> per-cell interleaved records
+// ---------------------------------------------------------------------------
+
+// rad[i*B + b] = (N, F_x / c, F_y / c, F_z / c) from N[b*C + i], F[(3b+k)*C + i].
+__global__ void k_pack_rad(int C, int B, double inv_c, const double* __restrict__ N, const double* __restrict__ F,
+                           d4* rad) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C * B) return;
+  int i = t / B, b = t % B;
+  d4 v;
+  v.x = N[b * C + i];
+  if (F) {
+    v.y = F[(3 * b) * C + i] * inv_c;
+    v.z = F[(3 * b + 1) * C + i] * inv_c;
+    v.w = F[(3 * b + 2) * C + i] * inv_c;
+  } else {
+    v.y = v.z = v.w = 0.0;
+  }
+  rad[t] = v;
+}
+
+__global__ void k_unpack_rad(int C, int B, double c, const d4* __restrict__ rad, double* N, double* F) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C * B) return;
+  int i = t / B, b = t % B;
+  d4 v = rad[t];
+  if (N) N[b * C + i] = v.x;
+  if (F) {
+    F[(3 * b) * C + i] = v.y * c;
+    F[(3 * b + 1) * C + i] = v.z * c;
+    F[(3 * b + 2) * C + i] = v.w * c;
+  }
+}
+
+// sweep copy of the radiation in precision R
+template <class R> __global__ void k_shadow_rad(int n, const d4* __restrict__ rad, R4<R>* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  d4 v = rad[k];
+  R4<R> o;
+  o.x = (R)v.x; o.y = (R)v.y; o.z = (R)v.z; o.w = (R)v.w;
+  out[k] = o;
+}
+
+// ---------------------------------------------------------------------------
+// gradients + limiter
+// ---------------------------------------------------------------------------
+
+template <class R> __device__ __forceinline__ R comp(const R4<R>& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+// G[(i*B + b)*12 + q*3 + d]: limited gradient of component q of bin b.
+template <class R>
+__global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict__ rad, R* __restrict__ G,
+                                              int order, int limiter, R lim_eps2) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = g.B;
+  if (t >= g.C * B) return;
+  const int i = t / B, b = t % B;
+  R* Go = G + (size_t)t * 12;
+  if (order < 2) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) Go[k] = R(0);
+    return;
+  }
+  const R4<R> pi = ld4<R>(rad + t);
+  R r[4][3];
+  R mx[4], mn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    r[q][0] = r[q][1] = r[q][2] = R(0);
+    mx[q] = mn[q] = comp<R>(pi, q);
+  }
+  const int k0 = g.off[i], k1 = g.off[i + 1];
+  for (int k = k0; k < k1; ++k) {
+    const int e = __ldg(g.csr + k), f = e >> 1;
+    const int2 c = __ldg(g.lr + f);
+    const int j = (e & 1) ? c.x : c.y;
+    const R4<R> pj = ld4<R>(rad + (size_t)j * B + b);
+    const R4<R> w = ld4<R>(g.w + f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R vj = comp<R>(pj, q), vi = comp<R>(pi, q);
+      R dphi = (e & 1) ? (vi - vj) : (vj - vi);   // phi_R - phi_L of this face
+      r[q][0] += w.x * dphi;
+      r[q][1] += w.y * dphi;
+      r[q][2] += w.z * dphi;
+      mx[q] = vj > mx[q] ? vj : mx[q];
+      mn[q] = vj < mn[q] ? vj : mn[q];
+    }
+  }
+  const R* m = g.minv + 6 * (size_t)i;
+  const R m00 = m[0], m01 = m[1], m02 = m[2], m11 = m[3], m12 = m[4], m22 = m[5];
+  R gr[4][3], gg[4], psi[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    gr[q][0] = m00 * r[q][0] + m01 * r[q][1] + m02 * r[q][2];
+    gr[q][1] = m01 * r[q][0] + m11 * r[q][1] + m12 * r[q][2];
+    gr[q][2] = m02 * r[q][0] + m12 * r[q][1] + m22 * r[q][2];
+    gg[q] = gr[q][0] * gr[q][0] + gr[q][1] * gr[q][1] + gr[q][2] * gr[q][2];
+    psi[q] = R(1);
+  }
+  if (limiter) {
+    for (int k = k0; k < k1; ++k) {
+      const int e = __ldg(g.csr + k), f = e >> 1;
+      const R4<R> x = ld4<R>((e & 1) ? (g.rR + f) : (g.rL + f));
+      const R xx = x.x * x.x + x.y * x.y + x.z * x.z;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+        R lim = R(1);
+        if (dphi * dphi > lim_eps2 * gg[q] * xx) {
+          R vi = comp<R>(pi, q);
+          lim = dphi > R(0) ? (mx[q] - vi) / dphi : (mn[q] - vi) / dphi;
+        }
+        psi[q] = lim < psi[q] ? lim : psi[q];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Go[3 * q + 0] = gr[q][0] * psi[q];
+    Go[3 * q + 1] = gr[q][1] * psi[q];
+    Go[3 * q + 2] = gr[q][2] * psi[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// face flux
+// ---------------------------------------------------------------------------
+
+// Linear extrapolation of the cell state to the face centre, clamped to
+// N >= 0 and |F| <= c N.
+template <class R>
+__device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__ Gc, const R4<R>& x, R v[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    R d = Gc[3 * q] * x.x + Gc[3 * q + 1] * x.y + Gc[3 * q + 2] * x.z;
+    v[q] = comp<R>(p, q) + d;
+  }
+  if (v[0] < R(0)) v[0] = R(0);
+  R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+  if (fl > v[0]) {
+    R s = fl > R(0) ? v[0] / fl : R(0);
+    v[1] *= s; v[2] *= s; v[3] *= s;
+  }
+}
+
+// N D n with the Levermore M1 Eddington tensor.
+template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0, R n1, R n2, R P[3]) {
+  R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+  if (v[0] > R(0) && fl > R(0)) {
+    R f = fl / v[0];
+    f = f > R(1) ? R(1) : f;
+    R chi = (R(3) + R(4) * f * f) / (R(5) + R(2) * sqrt(R(4) - R(3) * f * f));
+    R u0 = v[1] / fl, u1 = v[2] / fl, u2 = v[3] / fl;
+    R un = u0 * n0 + u1 * n1 + u2 * n2;
+    R a = R(0.5) * (R(1) - chi), bb = R(0.5) * (R(3) * chi - R(1));
+    P[0] = v[0] * (a * n0 + bb * un * u0);
+    P[1] = v[0] * (a * n1 + bb * un * u1);
+    P[2] = v[0] * (a * n2 + bb * un * u2);
+  } else {
+    P[0] = v[0] * n0 / R(3);
+    P[1] = v[0] * n1 / R(3);
+    P[2] = v[0] * n2 / R(3);
+  }
+}
+
+// flux[f*B + b] = A (Phi_N, Phi_F) / c_red, global Lax-Friedrichs at c_red.
+template <class R>
+__global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict__ rad, const R* __restrict__ G,
+                                              R4<R>* __restrict__ flux) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = g.B;
+  if (t >= g.F * B) return;
+  const int f = t / B, b = t % B;
+  const int2 c = __ldg(g.lr + f);
+  const R4<R> nA = ld4<R>(g.nA + f);
+  R vL[4], vR[4], PL[3], PR[3];
+  {
+    const size_t sL = (size_t)c.x * B + b;
+    face_state<R>(ld4<R>(rad + sL), G + sL * 12, ld4<R>(g.rL + f), vL);
+  }
+  {
+    const size_t sR = (size_t)c.y * B + b;
+    face_state<R>(ld4<R>(rad + sR), G + sR * 12, ld4<R>(g.rR + f), vR);
+  }
+  m1_normal<R>(vL, nA.x, nA.y, nA.z, PL);
+  m1_normal<R>(vR, nA.x, nA.y, nA.z, PR);
+  const R h = R(0.5);
+  R fn = h * ((vL[1] + vR[1]) * nA.x + (vL[2] + vR[2]) * nA.y + (vL[3] + vR[3]) * nA.z);
+  R4<R> o;
+  o.x = nA.w * (fn - h * (vR[0] - vL[0]));
+  o.y = nA.w * (h * (PL[0] + PR[0]) - h * (vR[1] - vL[1]));
+  o.z = nA.w * (h * (PL[1] + PR[1]) - h * (vR[2] - vL[2]));
+  o.w = nA.w * (h * (PL[2] + PR[2]) - h * (vR[3] - vL[3]));
+  flux[t] = o;
+}
+
+// ---------------------------------------------------------------------------
+// per cell: gather + sources + chemistry
+// ---------------------------------------------------------------------------
+
+struct CellArgs {
+  int C, B;
+  const int32_t* off;
+  const int32_t* csr;
+  const double* vol;       // V_i (L_u^3)
+  d4* rad;            // master radiation (FP64)
+  double* nH;
+  double* x5;              // 5*C
+  double* T;
+  const int32_t* src_idx;  // C: index into src_rate or -1
+  const double* src_rate;  // [n_src_cells][B] photons/s
+  int32_t* nsub;           // C
+  int* status;
+  double lam;              // c_red dt / unit_length_cm
+  double dt;
+  double lu3;              // unit_length_cm^3
+  int do_gather, do_inject, do_chem;
+};
+
+template <class R, bool Fast>
+__global__ void __launch_bounds__(128) k_cell(CellArgs a, ChemParams P, const R4<R>* __restrict__ flux,
+                                              R4<R>* __restrict__ shadow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.C) return;
+  const int B = a.B;
+  CellState s;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      d4 v = a.rad[(size_t)i * B + b];
+      s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
+    }
+  }
+  if (a.do_gather) {
+    double acc[kMaxBins][4];
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0;
+    const int k0 = a.off[i], k1 = a.off[i + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int e = __ldg(a.csr + k), f = e >> 1;
+      const bool right = e & 1;
+#pragma unroll
+      for (int b = 0; b < kMaxBins; ++b) {
+        if (b < B) {
+          const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
+          if (right) {
+            acc[b][0] -= (double)v.x; acc[b][1] -= (double)v.y; acc[b][2] -= (double)v.z; acc[b][3] -= (double)v.w;
+          } else {
+            acc[b][0] += (double)v.x; acc[b][1] += (double)v.y; acc[b][2] += (double)v.z; acc[b][3] += (double)v.w;
+          }
+        }
+      }
+    }
+    const double kfac = a.lam / a.vol[i];
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) {
+      if (b < B) {
+        s.N[b] -= kfac * acc[b][0];
+        s.f[b][0] -= kfac * acc[b][1];
+        s.f[b][1] -= kfac * acc[b][2];
+        s.f[b][2] -= kfac * acc[b][3];
+      }
+    }
+  }
+  if (a.do_inject) {
+    const int si = a.src_idx[i];
+    if (si >= 0) {
+      const double vcm3 = a.vol[i] * a.lu3;
+#pragma unroll
+      for (int b = 0; b < kMaxBins; ++b)
+        if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+    }
+  }
+  if (a.do_chem) {
+    const size_t C = a.C;
+    s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+    s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+    bool capped;
+    int n = chemistry<Fast>(P, a.nH[i], a.dt, s, &capped);
+    a.nsub[i] = n;
+    if (capped) atomicOr(a.status, kStChemSubsteps);
+    a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
+    a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+  }
+  bool bad = false;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
+      if (!isfinite(s.N[b])) bad = true;
+      if (shadow) {
+        R4<R> o;
+        o.x = (R)s.N[b]; o.y = (R)s.f[b][0]; o.z = (R)s.f[b][1]; o.w = (R)s.f[b][2];
+        shadow[(size_t)i * B + b] = o;
+      }
+    }
+  }
+  if (bad) atomicOr(a.status, kStNonFinite);
+}
+
+}  // namespace m1rt

@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Mesh", "cartesian_mesh", "voronoi_mesh", "jittered_lattice",
     "lognormal_density", "grf_density", "density_peaks", "locate_cells",
-    "KPC_CM", "MPC_CM", "C_LIGHT", "helium_ratio", "SPECTRAL_SPLIT_E4",
+    "KPC_CM", "MPC_CM", "C_LIGHT", "helium_ratio", "SPECTRAL_SPLIT_E4", "GREY_SIGMA", "GREY_EPS",
 ]
 
 KPC_CM = 3.0856775814913673e21
@@ -38,6 +38,15 @@ MYR_S = 3.15576e13               # s
 # Photon-rate split over the HI / HeI / HeII bins used by the coupled HII-region
 # test of Sec. 4.2.2 (1e50, 5e48, 3e48 photons/s), applied to every source.
 SPECTRAL_SPLIT_E4 = np.array([1e50, 5e48, 3e48]) / (1e50 + 5e48 + 3e48)
+
+
+EV = 1.602176634e-12             # erg
+# Grey cross-sections [bin][HI, HeI, HeII] (cm^2) and heat per photoionisation
+# (erg) of the HI-, HeI- and HeII-ionising bins.  The paper averages them over
+# a blackbody spectrum (Sec. 4.2.2) without printing values; these are
+# proposed constants of the right magnitude (thresholds 13.6 / 24.6 / 54.4 eV).
+GREY_SIGMA = [[3.0e-18, 0.0, 0.0], [5.7e-19, 4.5e-18, 0.0], [7.9e-20, 1.1e-18, 1.1e-18]]
+GREY_EPS = [[5.3 * EV, 0.0, 0.0], [21.5 * EV, 10.5 * EV, 0.0], [52.1 * EV, 41.1 * EV, 11.3 * EV]]
 
 
 def helium_ratio(Y: float) -> float:

@@ -10,13 +10,8 @@ import numpy as np
 
 import synth
 
-EV = 1.602176634e-12
-# Grey cross-sections [bin][HI, HeI, HeII] (cm^2) and heat per photoionisation
-# (erg) for the HI-, HeI- and HeII-ionising bins.  The paper computes them
-# from a blackbody (Sec. 4.2.2) but prints no values; these are proposed
-# constants of the right magnitude (thresholds 13.6 / 24.6 / 54.4 eV).
-SIGMA3 = [[3.0e-18, 0.0, 0.0], [5.7e-19, 4.5e-18, 0.0], [7.9e-20, 1.1e-18, 1.1e-18]]
-EPS3 = [[5.3 * EV, 0.0, 0.0], [21.5 * EV, 10.5 * EV, 0.0], [52.1 * EV, 41.1 * EV, 11.3 * EV]]
+SIGMA3 = synth.GREY_SIGMA
+EPS3 = synth.GREY_EPS
 
 
 def base_config(**kw) -> dict:

@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Metric per field (as stated for the method): max|gpu - oracle| / max|oracle|.
+FP64 path: 1e-12 after one subcycle and after whole steps.  Mixed path
+(FP32 transport sweep, FP64 update and chemistry): tolerances derived from
+FP32 rounding, per field.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests._cases import base_config, config1, make_oracle, voronoi_case
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def rel(a, b):
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+def make_gpu(mesh, cfg, state, precision="fp64"):
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    assert torch.cuda.is_available()
+    c = dict(cfg)
+    c["precision"] = precision
+    rt = RT(make_config(**c), mesh)
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    if len(state.get("cells", [])):
+        rt.set_sources(state["cells"], state["Q"])
+    else:
+        rt.set_sources(None, None)
+    return rt
+
+
+def compare_state(rt, o, tol, fields=("N", "fr", "x5", "T")):
+    g = rt.fields()
+    N, fr = o.radiation()
+    x5, T = o.gas()
+    ref = dict(N=N, fr=fr, x5=x5, T=T)
+    got = dict(N=g["N"], fr=g["F"] / o.cfg.c_red, x5=g["x5"], T=g["T"])
+    errs = {}
+    for k in fields:
+        if k in ("N", "fr"):
+            errs[k] = max(rel(got[k][b], ref[k][b]) for b in range(ref[k].shape[0]))
+        elif k == "x5":
+            errs[k] = max(rel(got[k][s], ref[k][s]) for s in range(5))
+        else:
+            errs[k] = rel(got[k], ref[k])
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"errors {errs} above {tol}"
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# stages, FP64
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [13, 16])
+def test_gradients_fp64(n):
+    mesh, cfg, st = voronoi_case(n=n)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    G0, G1 = o.gradients(), rt.gradients()
+    for b in range(3):
+        for q in range(4):
+            assert rel(G1[:, b, q], G0[:, b, q]) < TOL64, (b, q)
+
+
+@pytest.mark.parametrize("order,limiter", [(2, 1), (2, 0), (1, 1)])
+def test_face_fluxes_fp64(order, limiter):
+    mesh, cfg, st = voronoi_case(n=13, order=order, limiter=limiter)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    G = o.gradients()
+    f0 = o.face_fluxes(G)
+    f1 = rt.face_fluxes(G)   # same gradients in: flux stage alone
+    f2 = rt.face_fluxes()    # own gradients
+    for b in range(3):
+        for q in range(4):
+            assert rel(f1[:, b, q], f0[:, b, q]) < TOL64
+            assert rel(f2[:, b, q], f0[:, b, q]) < TOL64
+
+
+def test_transport_fp64():
+    mesh, cfg, st = voronoi_case(n=13, chem_mode=0)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert rt.max_dt() == pytest.approx(dt, rel=1e-14)
+    for _ in range(3):
+        o.transport(dt)
+        rt.transport(dt)
+    compare_state(rt, o, TOL64, fields=("N", "fr"))
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_chemistry_fp64(mode):
+    mesh, cfg, st = voronoi_case(n=13, chem_mode=mode)
+    st["N"] *= 10
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.thermochemistry(dt) == 0
+    rt.thermochemistry(dt)
+    assert rt.sync() == 0
+    compare_state(rt, o, TOL64)
+    np.testing.assert_array_equal(rt.fields()["nsub"], o.substeps())
+
+
+# ---------------------------------------------------------------------------
+# whole steps, FP64
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,n_bins", [(13, 3), (16, 3), (11, 1)])
+def test_step_voronoi_fp64(n, n_bins):
+    """Ragged sizes (13^3 = 2197 cells is no multiple of any block), one and
+    three bins, several subcycles with sources and full chemistry."""
+    mesh, cfg, st = voronoi_case(n=n, n_bins=n_bins)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.step(4 * dt, 4) == 0
+    rt.step(4 * dt, 4)
+    assert rt.sync() == 0
+    compare_state(rt, o, TOL64)
+
+
+@pytest.mark.slow
+def test_config1_full_run_fp64():
+    """The 32^3 Cartesian workload, 100 subcycles with chemistry on."""
+    mesh, cfg, st = config1(32)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.step(100 * dt, 100) == 0
+    rt.step(100 * dt, 100)
+    assert rt.sync() == 0
+    errs = compare_state(rt, o, TOL64)
+    print("config1 FP64 errors", errs)
+
+
+def test_voronoi_2e5_one_subcycle_fp64():
+    """Full size of the 2e5-cell Voronoi workload (59^3 jittered lattice),
+    one subcycle, every cell compared."""
+    mesh, cfg, st = voronoi_case(n=59, n_src=16)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.step(dt, 1) == 0
+    rt.step(dt, 1)
+    assert rt.sync() == 0
+    compare_state(rt, o, TOL64)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision
+# ---------------------------------------------------------------------------
+
+def test_mixed_step_errors():
+    """FP32 sweep: per-field error against the FP64 oracle after a few
+    subcycles; N and F carry FP32 rounding of the fluxes (~1e-7 relative per
+    subcycle), the abundances and T follow through the chemistry."""
+    mesh, cfg, st = voronoi_case(n=16)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st, precision="mixed")
+    dt = o.max_dt()
+    assert o.step(4 * dt, 4) == 0
+    rt.step(4 * dt, 4)
+    assert rt.sync() == 0
+    errs = compare_state(rt, o, 1e-4)
+    print("mixed errors", errs)
+    assert errs["N"] < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# status and error paths (host-side or bounded device checks; nothing faults)
+# ---------------------------------------------------------------------------
+
+def test_errors_are_status_codes():
+    from paper_2404_17630_gb300 import RT, RTError, make_config
+    from paper_2404_17630_gb300.rt import RT_BAD_MESH, RT_CFL, RT_CHEM_SUBSTEPS, RT_INVALID_ARG
+    mesh, cfg, st = voronoi_case(n=8)
+    rt = make_gpu(mesh, cfg, st)
+    dt = rt.max_dt()
+    with pytest.raises(RTError) as e:
+        rt.step(3.0 * dt, 2)
+    assert e.value.status == RT_CFL
+    with pytest.raises(RTError) as e:
+        rt.set_sources(np.array([mesh.n_cells + 5]), np.ones((1, 3)))
+    assert e.value.status == RT_INVALID_ARG
+    bad = synth.voronoi_mesh(8, 10.0, 0.3, seed=1)
+    bad.right = bad.right.copy()
+    bad.right[3] = bad.n_cells + 7
+    with pytest.raises(RTError) as e:
+        RT(make_config(**cfg), bad)
+    assert e.value.status == RT_BAD_MESH
+    # substep cap: a photon-rich neutral cell needs many attempts
+    c2 = dict(cfg, max_substeps=2)
+    st2 = dict(st)
+    st2["N"] = st["N"] * 1e4
+    rt2 = make_gpu(mesh, c2, st2)
+    rt2.step(dt, 1)
+    with pytest.raises(RTError) as e:
+        rt2.sync()
+    assert e.value.status == RT_CHEM_SUBSTEPS
+    # the context stays usable after a reported error
+    rt2.sync()
