@@ -178,6 +178,36 @@ rt_status rt_profile_read(rt_ctx *ctx, int n, double *ms, int64_t *launches, int
  * was created; mesh setup and state transfer kernels are not counted. */
 rt_status rt_launch_count(rt_ctx *ctx, int64_t *out);
 
+/* Allocation-free gradients, for callers that cannot allocate device memory
+ * (a host framework that owns all device memory through its own pool, a
+ * real-time loop that must not allocate, a plug-in that only receives device
+ * pointers).  The paper has no counterpart: it is an interface of this
+ * library, not a step of the method.  It computes the same limited
+ * least-squares gradients as rt_stage_gradients, for a mesh and state that
+ * the caller passes as DEVICE arrays:
+ *   cells: centroids (volume unused); faces: left, right, area, centroids
+ *   (normals unused); cell_off[C+1] and cell_faces[2F]: per-cell face lists,
+ *   entry (face << 1) | side with side 1 where the cell is the face's right
+ *   cell, ascending face order (the layout rt_init_mesh builds);
+ *   N[B*C], F_red[3*B*C]: photon densities and reduced fluxes F / c_red;
+ *   G[C*B*12] out, layout as rt_stage_gradients; *bad_cell (device int) is
+ *   set to 1 if a cell's least-squares matrix is singular, else 0.
+ * The arrays must describe a valid mesh (ids in range); they are not checked.
+ * Its only scratch is a static device array of 6 doubles per cell for at
+ * most 262144 cells (12.6 MB held on every GPU that loads the library until
+ * the process exits); larger meshes get RT_INVALID_ARG.  Nothing is
+ * allocated.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array: work enqueued by calls
+ * that may overlap on the GPU (other streams, unordered host threads) races.
+ * Asynchronous on stream; host-side errors are returned as status codes,
+ * with a message from rt_noalloc_last_error(). */
+rt_status rt_gradients_noalloc(const rt_cells *cells, const rt_faces *faces, const int32_t *cell_off,
+                               const int32_t *cell_faces, int n_bins, int order, int limiter, double lim_eps,
+                               double box, const double *N, const double *F_red, double *G, int *bad_cell,
+                               void *stream);
+const char *rt_noalloc_last_error(void);
+
 /* Message of the last failed call on ctx (or of the last failed rt_create
  * when ctx is NULL).  Valid until the next call. */
 const char *rt_last_error(const rt_ctx *ctx);

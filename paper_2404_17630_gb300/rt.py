@@ -126,6 +126,11 @@ def load():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            lib.rt_gradients_noalloc.argtypes = [ctypes.POINTER(rt_cells), ctypes.POINTER(rt_faces), vp, vp, i32, i32,
+                                                 i32, dbl, dbl, vp, vp, vp, vp, vp]
+            lib.rt_gradients_noalloc.restype = ctypes.c_int
+            lib.rt_noalloc_last_error.argtypes = []
+            lib.rt_noalloc_last_error.restype = ctypes.c_char_p
             lib.rt_last_error.argtypes = [vp]
             lib.rt_last_error.restype = ctypes.c_char_p
             lib.rt_destroy.argtypes = [vp]
@@ -280,6 +285,26 @@ def rt_stage_transport(ctx, dt):
 def rt_stage_chemistry(ctx, dt):
     lib = load()
     return _check(lib, ctx, lib.rt_stage_chemistry(ctx, float(dt)))
+
+
+def rt_gradients_noalloc(cells: rt_cells, faces: rt_faces, cell_off, cell_faces, n_bins, order, limiter, lim_eps,
+                         box, N, F_red, G, bad_cell, stream=None):
+    """Allocation-free gradients (see include/rt.h); every array argument is
+    a device pointer (int) or a CUDA tensor; cells/faces hold device pointers."""
+    lib = load()
+    keep = []
+    p = lambda a, dt: a if isinstance(a, int) else _ptr(a, dt, keep)
+    st = lib.rt_gradients_noalloc(ctypes.byref(cells), ctypes.byref(faces), p(cell_off, np.int32),
+                                  p(cell_faces, np.int32), int(n_bins), int(order), int(limiter), float(lim_eps),
+                                  float(box), p(N, np.float64), p(F_red, np.float64), _out_ptr(G) if not isinstance(G, int) else G,
+                                  bad_cell if isinstance(bad_cell, int) else bad_cell.data_ptr(), _stream_handle(stream))
+    if st != RT_OK:
+        raise RTError(st, (lib.rt_noalloc_last_error() or b"").decode())
+    return st
+
+
+def rt_noalloc_last_error() -> str:
+    return (load().rt_noalloc_last_error() or b"").decode()
 
 
 RT_KERNEL_NAMES = ("k_cell", "k_grad", "k_flux")
