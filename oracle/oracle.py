@@ -110,6 +110,8 @@ def _lib():
             for name in ("orc_alphaB_HII", "orc_alphaB_HeII", "orc_alphaB_HeIII", "orc_beta_HI"):
                 getattr(lib, name).argtypes = [ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
+            lib.orc_adjoint.argtypes = [vp, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+            lib.orc_adjoint.restype = ctypes.c_int
             lib.orc_cooling.argtypes = [ctypes.c_double] * 7
             lib.orc_cooling.restype = ctypes.c_double
             _LIB = lib
@@ -217,3 +219,18 @@ class Oracle:
 
     def step(self, dt, n_sub) -> int:
         return self._lib.orc_step(self._h, float(dt), int(n_sub))
+
+    def adjoint(self, dt, n_sub, lam_N=None, lam_fr=None, lam_x5=None, lam_T=None):
+        """Reverse mode of step(dt, n_sub) from the current state (which it
+        advances like step does).  lam_*: cotangents of the final state
+        (zero if None).  Returns dict(status, g_src [B, C] = dL/dS per cell and
+        bin, g_nH [C], lam0 = cotangents of the initial state)."""
+        B, C = self.B, self.C
+        lN = np.zeros((B, C)) if lam_N is None else _f64(lam_N).reshape(B, C).copy()
+        lfr = np.zeros((B, 3, C)) if lam_fr is None else _f64(lam_fr).reshape(B, 3, C).copy()
+        lx = np.zeros((5, C)) if lam_x5 is None else _f64(lam_x5).reshape(5, C).copy()
+        lT = np.zeros(C) if lam_T is None else _f64(lam_T).copy()
+        g_src, g_nH = np.zeros((B, C)), np.zeros(C)
+        st = self._lib.orc_adjoint(self._h, float(dt), int(n_sub), _d(lN), _d(lfr), _d(lx), _d(lT), _d(g_src),
+                                   _d(g_nH))
+        return dict(status=st, g_src=g_src, g_nH=g_nH, lam0=dict(N=lN, fr=lfr, x5=lx, T=lT))

@@ -701,3 +701,528 @@ double orc_beta_HI(double T) { return beta_HI(T); }
 double orc_cooling(double T, double ne, double nHI, double nHII, double nHeI, double nHeII, double nHeIII) {
   return cooling(T, ne, nHI, nHII, nHeI, nHeII, nHeIII);
 }
+
+/* ======================================================================== */
+/* Adjoint: reverse mode of whole RT steps (isothermal network).            */
+/*                                                                          */
+/* The paper has no adjoint; this is the exact derivative of the discrete   */
+/* forward map above, written stage by stage in reverse: source term,       */
+/* every chemistry attempt together with the substep controller that sets   */
+/* its length (Sec. 4.1.1), gradients and limiter (active branch), face      */
+/* flux with the M1 closure, and the flux application.  Each *_vjp function */
+/* recomputes the forward values it needs and then walks back through them. */
+/* ======================================================================== */
+
+/* VJP of m1_pressure_normal: lamP -> (lamN, lamfr), accumulated. */
+static void m1_pressure_normal_vjp(double N, const double fr[3], const double n[3], const double lamP[3],
+                                   double *lamN, double lamfr[3]) {
+  double fl = sqrt(fr[0] * fr[0] + fr[1] * fr[1] + fr[2] * fr[2]);
+  double lPn = lamP[0] * n[0] + lamP[1] * n[1] + lamP[2] * n[2];
+  if (N > 0 && fl > 0) {
+    double f = fl / N;
+    int clamped = f > 1;
+    if (clamped) f = 1;
+    double s = sqrt(4.0 - 3.0 * f * f);
+    double den = 5.0 + 2.0 * s;
+    double chi = (3.0 + 4.0 * f * f) / den;
+    double u[3] = {fr[0] / fl, fr[1] / fl, fr[2] / fl};
+    double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    double a = 0.5 * (1.0 - chi), bb = 0.5 * (3.0 * chi - 1.0);
+    double lPu = lamP[0] * u[0] + lamP[1] * u[1] + lamP[2] * u[2];
+    /* P_k = N (a n_k + bb un u_k) */
+    *lamN += a * lPn + bb * un * lPu;
+    double la = N * lPn, lbb = N * un * lPu;
+    double lu[3];
+    for (int k = 0; k < 3; ++k) lu[k] = N * bb * (n[k] * lPu + un * lamP[k]);
+    double lchi = -0.5 * la + 1.5 * lbb;
+    double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f / s) / (den * den);
+    double lf = clamped ? 0.0 : lchi * dchi;
+    double lfl = lf / N;
+    *lamN -= lf * fl / (N * N);
+    double luu = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
+    for (int m = 0; m < 3; ++m) lamfr[m] += (lu[m] - luu * u[m]) / fl + lfl * u[m];
+  } else {
+    *lamN += lPn / 3.0;
+  }
+}
+
+/* VJP of face_state for cell c, face f, bin b: lamv[4] (cotangent of the
+ * face state) -> cotangents of the cell values (lamU, 4) and of the cell's
+ * gradients (lamG, [4][3]). */
+static void face_state_vjp(const orc_t *o, int64_t c, int64_t f, int b, const double lamv[4], double lamU[4],
+                           double lamG[4][3]) {
+  double x[3] = {mimage(o->fx[f] - o->cx[c], o->cfg.box), mimage(o->fy[f] - o->cy[c], o->cfg.box),
+                 mimage(o->fz[f] - o->cz[c], o->cfg.box)};
+  double v[4];
+  for (int q = 0; q < 4; ++q) {
+    const double *g = Gp(o, c, b, q);
+    v[q] = comp(o, b, q, c) + (g[0] * x[0] + g[1] * x[1] + g[2] * x[2]);
+  }
+  int clampN = v[0] < 0;
+  double v0 = clampN ? 0.0 : v[0];
+  double fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+  double lpre[4] = {lamv[0], lamv[1], lamv[2], lamv[3]};
+  if (fl > v0) {
+    /* out_k = v0 v_k / fl */
+    double lv = lamv[1] * v[1] + lamv[2] * v[2] + lamv[3] * v[3];
+    lpre[0] = lamv[0] + lv / fl;
+    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lamv[k] - lv * v[k] / (fl * fl));
+  }
+  if (clampN) lpre[0] = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    lamU[q] += lpre[q];
+    for (int d = 0; d < 3; ++d) lamG[q][d] += lpre[q] * x[d];
+  }
+}
+
+/* Cotangent arrays of the radiation: lN [b][C], lfr [b][3][C]. */
+static double *lam_comp(double *lN, double *lfr, int64_t C, int b, int q, int64_t i) {
+  return q == 0 ? &lN[b * C + i] : &lfr[(b * 3 + (q - 1)) * C + i];
+}
+
+/* Reverse of one transport step (gradients, fluxes, application over dt)
+ * taken from the radiation state currently in o.  On entry lN/lfr hold the
+ * cotangent of the updated radiation; on return that of the state before. */
+static void transport_vjp(orc_t *o, double dt, double *lN, double *lfr) {
+  const int B = o->cfg.n_bins;
+  const int64_t C = o->C;
+  const double lam = o->cfg.c_red * dt / o->cfg.unit_length_cm;
+  gradients(o);
+  double *lG = dalloc(12 * B * C);
+  /* flux application and face fluxes */
+  double *in_N = dalloc(B * C), *in_fr = dalloc(3 * B * C);
+  memcpy(in_N, lN, sizeof(double) * B * C);
+  memcpy(in_fr, lfr, sizeof(double) * 3 * B * C);
+  for (int64_t f = 0; f < o->F; ++f) {
+    int64_t L = o->left[f], R = o->right[f];
+    double n[3] = {o->nx[f], o->ny[f], o->nz[f]};
+    double A = o->area[f];
+    for (int b = 0; b < B; ++b) {
+      double lout[4];
+      for (int q = 0; q < 4; ++q)
+        lout[q] = lam * (*lam_comp(in_N, in_fr, C, b, q, R) / o->vol[R] - *lam_comp(in_N, in_fr, C, b, q, L) / o->vol[L]);
+      double NL, NR, fL[3], fR[3];
+      face_state(o, L, f, b, &NL, fL);
+      face_state(o, R, f, b, &NR, fR);
+      double lNL = 0.5 * A * lout[0], lNR = -0.5 * A * lout[0];
+      double lfn = A * lout[0];
+      double lfL[3], lfR[3], lP[3];
+      for (int k = 0; k < 3; ++k) {
+        lfL[k] = 0.5 * lfn * n[k] + 0.5 * A * lout[1 + k];
+        lfR[k] = 0.5 * lfn * n[k] - 0.5 * A * lout[1 + k];
+        lP[k] = 0.5 * A * lout[1 + k];
+      }
+      m1_pressure_normal_vjp(NL, fL, n, lP, &lNL, lfL);
+      m1_pressure_normal_vjp(NR, fR, n, lP, &lNR, lfR);
+      double lvL[4] = {lNL, lfL[0], lfL[1], lfL[2]}, lvR[4] = {lNR, lfR[0], lfR[1], lfR[2]};
+      double lUL[4] = {0, 0, 0, 0}, lUR[4] = {0, 0, 0, 0};
+      face_state_vjp(o, L, f, b, lvL, lUL, (double(*)[3])(lG + ((L * B) + b) * 12));
+      face_state_vjp(o, R, f, b, lvR, lUR, (double(*)[3])(lG + ((R * B) + b) * 12));
+      for (int q = 0; q < 4; ++q) {
+        *lam_comp(lN, lfr, C, b, q, L) += lUL[q];
+        *lam_comp(lN, lfr, C, b, q, R) += lUR[q];
+      }
+    }
+  }
+  free(in_N);
+  free(in_fr);
+  /* gradients: G = psi g, g = M^-1 r, r = sum_j A (phi_j - phi_i) d / |d|^2 */
+  if (o->cfg.order >= 2) {
+    for (int64_t i = 0; i < C; ++i) {
+      for (int b = 0; b < B; ++b) {
+        for (int q = 0; q < 4; ++q) {
+          const double *lg = lG + ((i * B + b) * 4 + q) * 3;
+          double phi_i = comp(o, b, q, i);
+          /* recompute the raw gradient, extremes (first attaining cell, self first) */
+          double r[3] = {0, 0, 0};
+          double pmax = phi_i, pmin = phi_i;
+          int64_t jmax = i, jmin = i;
+          for (int64_t k = o->off[i]; k < o->off[i + 1]; ++k) {
+            int64_t f = o->fl[k], j = other_cell(o, f, i);
+            double d[3];
+            sep(o, i, j, d);
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double phi_j = comp(o, b, q, j);
+            double wgt = o->area[f] * (phi_j - phi_i) / d2;
+            r[0] += wgt * d[0];
+            r[1] += wgt * d[1];
+            r[2] += wgt * d[2];
+            if (phi_j > pmax) { pmax = phi_j; jmax = j; }
+            if (phi_j < pmin) { pmin = phi_j; jmin = j; }
+          }
+          const double *mi = o->minv + 9 * i;
+          double g[3];
+          for (int a = 0; a < 3; ++a) g[a] = mi[3 * a] * r[0] + mi[3 * a + 1] * r[1] + mi[3 * a + 2] * r[2];
+          double lgraw[3] = {lg[0], lg[1], lg[2]};
+          if (o->cfg.limiter) {
+            double psi = 1.0, dstar = 0.0, xs[3] = {0, 0, 0};
+            int64_t jstar = -1;
+            double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+            for (int64_t k = o->off[i]; k < o->off[i + 1]; ++k) {
+              int64_t f = o->fl[k];
+              double x[3] = {mimage(o->fx[f] - o->cx[i], o->cfg.box), mimage(o->fy[f] - o->cy[i], o->cfg.box),
+                             mimage(o->fz[f] - o->cz[i], o->cfg.box)};
+              double dphi = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
+              double xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+              if (dphi * dphi > o->cfg.lim_eps * o->cfg.lim_eps * gg * xx) {
+                double lim = dphi > 0 ? (pmax - phi_i) / dphi : (pmin - phi_i) / dphi;
+                if (lim < psi) {
+                  psi = lim;
+                  dstar = dphi;
+                  xs[0] = x[0]; xs[1] = x[1]; xs[2] = x[2];
+                  jstar = dphi > 0 ? jmax : jmin;
+                }
+              }
+            }
+            if (jstar >= 0) {
+              /* G = psi g, psi = (p* - phi_i) / (g . x*) */
+              double sdot = lg[0] * g[0] + lg[1] * g[1] + lg[2] * g[2];
+              for (int a = 0; a < 3; ++a) lgraw[a] = psi * lg[a] - sdot * psi / dstar * xs[a];
+              *lam_comp(lN, lfr, C, b, q, jstar) += sdot / dstar;
+              *lam_comp(lN, lfr, C, b, q, i) -= sdot / dstar;
+            }
+          }
+          /* g = M^-1 r  ->  lam_r = M^-T lam_g */
+          double lr[3];
+          for (int a = 0; a < 3; ++a) lr[a] = mi[a] * lgraw[0] + mi[3 + a] * lgraw[1] + mi[6 + a] * lgraw[2];
+          for (int64_t k = o->off[i]; k < o->off[i + 1]; ++k) {
+            int64_t f = o->fl[k], j = other_cell(o, f, i);
+            double d[3];
+            sep(o, i, j, d);
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double c = o->area[f] * (lr[0] * d[0] + lr[1] * d[1] + lr[2] * d[2]) / d2;
+            *lam_comp(lN, lfr, C, b, q, j) += c;
+            *lam_comp(lN, lfr, C, b, q, i) -= c;
+          }
+        }
+      }
+    }
+  }
+  free(lG);
+}
+
+/* ---- chemistry ---------------------------------------------------------- */
+
+typedef struct {
+  double lam_s[4 * ORC_MAXB + 6];
+  double lam_dt;
+  double lam_nH;
+} chem_cot;
+
+/* VJP of one isothermal photochem_attempt of cell i: given the cotangents
+ * of its output state lt[] and of its substep measure lf, accumulate those of
+ * its input state, of dt and of n_H into cc. */
+static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const double *s, const double *lt,
+                                  double lf, chem_cot *cc) {
+  const orc_config *cf = &o->cfg;
+  const int B = cf->n_bins;
+  const double c = cf->c_red, nH = o->nH[i], yhe = cf->y_he, nHe = yhe * nH;
+  const double T = s[4 * B + 5];
+  const int recomb = cf->chem_flags & 1, coll = cf->chem_flags & 2;
+  const double aHII = recomb ? alphaB_HII(T) : 0.0, aHeII = recomb ? alphaB_HeII(T) : 0.0,
+               aHeIII = recomb ? alphaB_HeIII(T) : 0.0;
+  const double bHI = coll ? beta_HI(T) : 0.0, bHeI = coll ? beta_HeI(T) : 0.0, bHeII = coll ? beta_HeII(T) : 0.0;
+  const double xHI = s[4 * B], xHII = s[4 * B + 1], yI = s[4 * B + 2], yII = s[4 * B + 3], yIII = s[4 * B + 4];
+  /* forward values */
+  double ns[3] = {nH * xHI, nHe * yI, nHe * yII};
+  double kap[ORC_MAXB], den[ORC_MAXB], Nbar[ORC_MAXB], Gm[3] = {0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    kap[b] = cf->sigma[b][0] * ns[0] + cf->sigma[b][1] * ns[1] + cf->sigma[b][2] * ns[2];
+    den[b] = 1.0 + c * dt * kap[b];
+    Nbar[b] = s[b] / den[b];
+    for (int sp = 0; sp < 3; ++sp) Gm[sp] += c * cf->sigma[b][sp] * Nbar[b];
+  }
+  double ne0 = nH * xHII + nHe * (yII + 2.0 * yIII);
+  double aH = dt * (Gm[0] + bHI * ne0), bH = dt * aHII * ne0;
+  double D1 = 1.0 + aH + bH;
+  double xHI1 = (xHI * (1.0 + bH) + bH * xHII) / D1;
+  double xHII1 = (xHII * (1.0 + aH) + aH * xHI) / D1;
+  double ne1 = nH * xHII1 + nHe * (yII + 2.0 * yIII);
+  double A = dt * (Gm[1] + bHeI * ne1), Bb = dt * aHeII * ne1, Cc = dt * (Gm[2] + bHeII * ne1),
+         Dd = dt * aHeIII * ne1;
+  double opA = 1.0 + A, opD = 1.0 + Dd;
+  double num = yII + A * yI / opA + Dd * yIII / opD;
+  double dn = 1.0 + Bb / opA + Cc / opD;
+  double yII1 = num / dn;
+  double yI1 = (yI + Bb * yII1) / opA;
+  double yIII1 = (yIII + Cc * yII1) / opD;
+  double m[3] = {nH * xHI1, nHe * yI1, nHe * yII1};
+  double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
+  const double in_x[5] = {xHI, xHII, yI, yII, yIII};
+
+  double *ls = cc->lam_s;
+  double lx1[5];
+  for (int q = 0; q < 5; ++q) lx1[q] = lt[4 * B + q];
+  ls[4 * B + 5] += lt[4 * B + 5]; /* T passes through (isothermal) */
+  double lxin[5] = {0, 0, 0, 0, 0};
+  /* substep measure f = max_k |out_k - in_k| / max(|in_k|, floor) */
+  if (lf != 0.0) {
+    int nk = yhe > 0 ? 5 : 2;
+    double best = -1.0;
+    int kb = -1;
+    for (int k = 0; k < nk; ++k) {
+      double r = rel_change(in_x[k], out_x[k], cf->x_floor);
+      if (r > best) { best = r; kb = k; }
+    }
+    if (best > 0) {
+      double a = in_x[kb], bo = out_x[kb];
+      double mm = fabs(a) > cf->x_floor ? fabs(a) : cf->x_floor;
+      double sg = bo > a ? 1.0 : -1.0;
+      lx1[kb] += lf * sg / mm;
+      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - a) / (mm * mm)) * (fabs(a) > cf->x_floor ? (a > 0 ? 1.0 : -1.0) : 0.0);
+    }
+  }
+  /* photon removal and flux scaling */
+  double lNbar[ORC_MAXB] = {0}, lm[3] = {0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    double sm = cf->sigma[b][0] * m[0] + cf->sigma[b][1] * m[1] + cf->sigma[b][2] * m[2];
+    double rem = c * dt * Nbar[b] * sm;
+    double N1 = s[b] - rem;
+    int clamped = N1 < 0;
+    if (clamped) N1 = 0;
+    double scale = s[b] > 0 ? N1 / s[b] : 0.0;
+    double lscale = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      ls[B + 3 * b + k] += lt[B + 3 * b + k] * scale;
+      lscale += lt[B + 3 * b + k] * s[B + 3 * b + k];
+    }
+    double lN1 = lt[b];
+    if (s[b] > 0) {
+      lN1 += lscale / s[b];
+      ls[b] -= lscale * N1 / (s[b] * s[b]);
+    }
+    if (!clamped) {
+      ls[b] += lN1;
+      double lrem = -lN1;
+      lNbar[b] += lrem * c * dt * sm;
+      cc->lam_dt += lrem * c * Nbar[b] * sm;
+      for (int sp = 0; sp < 3; ++sp) lm[sp] += lrem * c * dt * Nbar[b] * cf->sigma[b][sp];
+    }
+  }
+  /* m = (nH xHI1, nHe yI1, nHe yII1) */
+  lx1[0] += lm[0] * nH;
+  lx1[2] += lm[1] * nHe;
+  lx1[3] += lm[2] * nHe;
+  cc->lam_nH += lm[0] * xHI1 + lm[1] * yhe * yI1 + lm[2] * yhe * yII1;
+  /* helium backward Euler */
+  double lyII1 = lx1[3], lyI1 = lx1[2], lyIII1 = lx1[4];
+  double lCc = 0, lBb = 0, lA = 0, lDd = 0, lopA = 0, lopD = 0;
+  lxin[4] += lyIII1 / opD;
+  lCc += lyIII1 * yII1 / opD;
+  lyII1 += lyIII1 * Cc / opD;
+  lopD -= lyIII1 * yIII1 / opD;
+  lxin[2] += lyI1 / opA;
+  lBb += lyI1 * yII1 / opA;
+  lyII1 += lyI1 * Bb / opA;
+  lopA -= lyI1 * yI1 / opA;
+  double lnum = lyII1 / dn, ldn = -lyII1 * yII1 / dn;
+  lBb += ldn / opA;
+  lopA -= ldn * Bb / (opA * opA);
+  lCc += ldn / opD;
+  lopD -= ldn * Cc / (opD * opD);
+  lxin[3] += lnum;
+  lA += lnum * yI / opA;
+  lxin[2] += lnum * A / opA;
+  lopA -= lnum * A * yI / (opA * opA);
+  lDd += lnum * yIII / opD;
+  lxin[4] += lnum * Dd / opD;
+  lopD -= lnum * Dd * yIII / (opD * opD);
+  lA += lopA;
+  lDd += lopD;
+  cc->lam_dt += lA * (Gm[1] + bHeI * ne1) + lBb * aHeII * ne1 + lCc * (Gm[2] + bHeII * ne1) + lDd * aHeIII * ne1;
+  double lG[3] = {0, lA * dt, lCc * dt};
+  double lne1 = lA * dt * bHeI + lBb * dt * aHeII + lCc * dt * bHeII + lDd * dt * aHeIII;
+  double lxHII1 = lx1[1] + lne1 * nH;
+  double lxHI1 = lx1[0];
+  cc->lam_nH += lne1 * (xHII1 + yhe * (yII + 2.0 * yIII));
+  lxin[3] += lne1 * nHe;
+  lxin[4] += lne1 * 2.0 * nHe;
+  /* hydrogen backward Euler */
+  double lD1 = -(lxHI1 * xHI1 + lxHII1 * xHII1) / D1;
+  lxin[1] += lxHII1 * (1.0 + aH) / D1 + lxHI1 * bH / D1;
+  lxin[0] += lxHII1 * aH / D1 + lxHI1 * (1.0 + bH) / D1;
+  double laH = lxHII1 * (xHII + xHI) / D1 + lD1;
+  double lbH = lxHI1 * (xHI + xHII) / D1 + lD1;
+  cc->lam_dt += laH * (Gm[0] + bHI * ne0) + lbH * aHII * ne0;
+  lG[0] += laH * dt;
+  double lne0 = laH * dt * bHI + lbH * dt * aHII;
+  lxin[1] += lne0 * nH;
+  cc->lam_nH += lne0 * (xHII + yhe * (yII + 2.0 * yIII));
+  lxin[3] += lne0 * nHe;
+  lxin[4] += lne0 * 2.0 * nHe;
+  /* rates Gamma_sp = sum_b c sigma_bsp Nbar_b; Nbar = N / (1 + c dt kap) */
+  double lns[3] = {0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    lNbar[b] += c * (cf->sigma[b][0] * lG[0] + cf->sigma[b][1] * lG[1] + cf->sigma[b][2] * lG[2]);
+    ls[b] += lNbar[b] / den[b];
+    double lden = -lNbar[b] * Nbar[b] / den[b];
+    cc->lam_dt += lden * c * kap[b];
+    double lkap = lden * c * dt;
+    for (int sp = 0; sp < 3; ++sp) lns[sp] += lkap * cf->sigma[b][sp];
+  }
+  lxin[0] += lns[0] * nH;
+  lxin[2] += lns[1] * nHe;
+  lxin[3] += lns[2] * nHe;
+  cc->lam_nH += lns[0] * xHI + lns[1] * yhe * yI + lns[2] * yhe * yII;
+  for (int q = 0; q < 5; ++q) ls[4 * B + q] += lxin[q];
+}
+
+typedef struct {
+  double s[4 * ORC_MAXB + 6];
+  double dt, rem, f;
+  int accepted, grow_is_ratio, clipped;
+} attempt_rec;
+
+/* Reverse of chemistry_cell over dt_sub from the cell state s0: lam (in/out)
+ * is the cotangent of the cell state; *lam_nH accumulates.  Re-runs the
+ * forward attempt sequence to record it.  Returns ST_CHEM if the cap hit. */
+static int chemistry_cell_vjp(orc_t *o, int64_t i, double dt_sub, const double *s0, double *lam, double *lam_nH) {
+  const orc_config *cf = &o->cfg;
+  const int B = cf->n_bins, nv = 4 * B + 6;
+  attempt_rec *rec = (attempt_rec *)malloc(sizeof(attempt_rec) * (size_t)(cf->max_substeps > 0 ? cf->max_substeps : 1));
+  double s[4 * ORC_MAXB + 6], t[4 * ORC_MAXB + 6];
+  memcpy(s, s0, sizeof(double) * nv);
+  double rem = dt_sub, dt = dt_sub;
+  int n = 0;
+  while (rem > 0) {
+    if (n >= cf->max_substeps) { free(rec); return ST_CHEM; }
+    attempt_rec *r = &rec[n++];
+    memcpy(r->s, s, sizeof(double) * nv);
+    r->dt = dt;
+    r->rem = rem;
+    double f = photochem_attempt(o, i, dt, s, t);
+    r->f = f;
+    if (f > cf->f_max) {
+      r->accepted = 0;
+      dt = dt * (cf->f_s / f);
+      continue;
+    }
+    r->accepted = 1;
+    memcpy(s, t, sizeof(double) * nv);
+    rem = (dt == rem) ? 0.0 : rem - dt;
+    double grow = (f > 0) ? cf->f_s / f : 2.0;
+    r->grow_is_ratio = f > 0 && grow <= 2.0;
+    if (grow > 2.0) grow = 2.0;
+    double dtn = dt * grow;
+    r->clipped = dtn > rem;
+    dt = r->clipped ? rem : dtn;
+  }
+  /* reverse */
+  double lt[4 * ORC_MAXB + 6];
+  memcpy(lt, lam, sizeof(double) * nv);
+  double ldt = 0.0, lrem = 0.0;
+  for (int k = n - 1; k >= 0; --k) {
+    attempt_rec *r = &rec[k];
+    chem_cot cc;
+    memset(&cc, 0, sizeof cc);
+    if (r->accepted) {
+      double grow = r->grow_is_ratio ? cf->f_s / r->f : 2.0;
+      double ldtg = 0.0;
+      if (r->clipped) lrem += ldt;
+      else ldtg = ldt;
+      double ldtk = ldtg * grow;
+      double lg = ldtg * r->dt;
+      double lf = r->grow_is_ratio ? -lg * cf->f_s / (r->f * r->f) : 0.0;
+      double lremk = lrem;
+      ldtk -= lrem;
+      photochem_attempt_vjp(o, i, r->dt, r->s, lt, lf, &cc);
+      memcpy(lt, cc.lam_s, sizeof(double) * nv);
+      ldt = ldtk + cc.lam_dt;
+      lrem = lremk;
+    } else {
+      double ldtk = ldt * cf->f_s / r->f;
+      double lf = -ldt * r->dt * cf->f_s / (r->f * r->f);
+      double zero[4 * ORC_MAXB + 6];
+      memset(zero, 0, sizeof zero);
+      photochem_attempt_vjp(o, i, r->dt, r->s, zero, lf, &cc);
+      for (int q = 0; q < nv; ++q) lt[q] += cc.lam_s[q];
+      ldt = ldtk + cc.lam_dt;
+    }
+    *lam_nH += cc.lam_nH;
+  }
+  memcpy(lam, lt, sizeof(double) * nv);
+  free(rec);
+  return ST_OK;
+}
+
+/*
+ * Reverse mode of orc_step(dt, n_sub) from the current state (isothermal
+ * chemistry or transport only).  Runs the forward step, recording the state
+ * before each chemistry pass and before each transport pass, and leaves the
+ * final state in o, as orc_step does.  Inputs: cotangents of the final state
+ * (lN [B*C], lfr [3B*C], lx5 [5*C], lT [C]); they are overwritten with the
+ * cotangents of the initial state.  Outputs (accumulated, caller zeroes):
+ * g_src [B*C] = dL/dS_b of each cell's photon rate (photons/s), g_nH [C] =
+ * dL/dn_H.  Returns 0, 1 (unsupported mode), ST_CFL or ST_CHEM.
+ */
+int orc_adjoint(orc_t *o, double dt, int n_sub, double *lN, double *lfr, double *lx5, double *lT, double *g_src,
+                double *g_nH) {
+  if (n_sub < 1 || o->cfg.chem_mode == 2) return 1;
+  const double dts = dt / n_sub;
+  if (dts > orc_max_dt(o) * (1.0 + 1e-12)) return ST_CFL;
+  const int B = o->cfg.n_bins, nv = 4 * B + 6;
+  const int64_t C = o->C;
+  double *pre_chem = dalloc((int64_t)n_sub * nv * C);
+  double *pre_trans = dalloc((int64_t)n_sub * 4 * B * C);
+  int st = ST_OK;
+  for (int s = 0; s < n_sub; ++s) {
+    inject_sources(o, dts);
+    double *pc = pre_chem + (int64_t)s * nv * C;
+    for (int64_t i = 0; i < C; ++i) {
+      for (int b = 0; b < B; ++b) {
+        pc[i * nv + b] = o->N[b * C + i];
+        for (int k = 0; k < 3; ++k) pc[i * nv + B + 3 * b + k] = o->fr[(b * 3 + k) * C + i];
+      }
+      pc[i * nv + 4 * B] = o->xHI[i]; pc[i * nv + 4 * B + 1] = o->xHII[i];
+      pc[i * nv + 4 * B + 2] = o->yI[i]; pc[i * nv + 4 * B + 3] = o->yII[i];
+      pc[i * nv + 4 * B + 4] = o->yIII[i]; pc[i * nv + 4 * B + 5] = o->T[i];
+    }
+    if (o->cfg.chem_mode > 0)
+      for (int64_t i = 0; i < C; ++i) {
+        int c = chemistry_cell(o, i, dts);
+        if (c) st = c;
+      }
+    double *pt = pre_trans + (int64_t)s * 4 * B * C;
+    memcpy(pt, o->N, sizeof(double) * B * C);
+    memcpy(pt + B * C, o->fr, sizeof(double) * 3 * B * C);
+    orc_transport(o, dts);
+  }
+  if (st) { free(pre_chem); free(pre_trans); return st; }
+  /* keep the final radiation; the gas arrays are already final */
+  double *finN = dalloc(B * C), *finfr = dalloc(3 * B * C);
+  memcpy(finN, o->N, sizeof(double) * B * C);
+  memcpy(finfr, o->fr, sizeof(double) * 3 * B * C);
+  const double lu = o->cfg.unit_length_cm;
+  for (int s = n_sub - 1; s >= 0 && st == ST_OK; --s) {
+    double *pt = pre_trans + (int64_t)s * 4 * B * C;
+    memcpy(o->N, pt, sizeof(double) * B * C);
+    memcpy(o->fr, pt + B * C, sizeof(double) * 3 * B * C);
+    transport_vjp(o, dts, lN, lfr);
+    double *pc = pre_chem + (int64_t)s * nv * C;
+    if (o->cfg.chem_mode > 0) {
+      for (int64_t i = 0; i < C && st == ST_OK; ++i) {
+        double lam[4 * ORC_MAXB + 6];
+        for (int b = 0; b < B; ++b) {
+          lam[b] = lN[b * C + i];
+          for (int k = 0; k < 3; ++k) lam[B + 3 * b + k] = lfr[(b * 3 + k) * C + i];
+        }
+        for (int q = 0; q < 5; ++q) lam[4 * B + q] = lx5[q * C + i];
+        lam[4 * B + 5] = lT[i];
+        st = chemistry_cell_vjp(o, i, dts, pc + i * nv, lam, &g_nH[i]);
+        for (int b = 0; b < B; ++b) {
+          lN[b * C + i] = lam[b];
+          for (int k = 0; k < 3; ++k) lfr[(b * 3 + k) * C + i] = lam[B + 3 * b + k];
+        }
+        for (int q = 0; q < 5; ++q) lx5[q * C + i] = lam[4 * B + q];
+        lT[i] = lam[4 * B + 5];
+      }
+    }
+    /* source term: N_b += S_b dt / (V lu^3) */
+    for (int64_t i = 0; i < C; ++i)
+      for (int b = 0; b < B; ++b) g_src[b * C + i] += lN[b * C + i] * dts / (o->vol[i] * (lu * lu * lu));
+  }
+  memcpy(o->N, finN, sizeof(double) * B * C);
+  memcpy(o->fr, finfr, sizeof(double) * 3 * B * C);
+  free(finN); free(finfr); free(pre_chem); free(pre_trans);
+  return st;
+}

@@ -1,0 +1,141 @@
+"""Pins of the oracle's adjoint: central finite differences of the forward
+oracle, taken where no substep decision changes between the two runs."""
+import numpy as np
+import pytest
+
+from tests._cases import make_oracle, voronoi_case
+
+
+def _setup(n=7, chem_mode=1, n_bins=3, **kw):
+    mesh, cfg, st = voronoi_case(n=n, n_bins=n_bins, chem_mode=chem_mode, n_src=2, **kw)
+    st["N"] *= 0.1
+    st["fr"] *= 0.1
+    # target region: cells whose centroid lies in the lower half-box corner
+    c = mesh.centroids()
+    R = np.all(c < 0.5 * mesh.box, axis=1)
+    return mesh, cfg, st, R
+
+
+def _loss(o, mesh, st, R):
+    x5, _ = o.gas()
+    m = st["nH"][R] * mesh.volume[R]
+    return float((m * x5[1][R]).sum() / m.sum())
+
+
+def _run(mesh, cfg, st, R, n_sub):
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    assert o.step(dt, n_sub) == 0
+    return _loss(o, mesh, st, R), o.substeps().copy()
+
+
+def _adjoint(mesh, cfg, st, R, n_sub):
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    C = mesh.n_cells
+    m = st["nH"] * mesh.volume
+    M = m[R].sum()
+    lx = np.zeros((5, C))
+    lx[1][R] = m[R] / M
+    out = o.adjoint(dt, n_sub, lam_x5=lx)
+    assert out["status"] == 0
+    L = _loss(o, mesh, st, R)
+    x5, _ = o.gas()
+    # direct dependence of the mass-weighted loss on n_H
+    g_nH = out["g_nH"].copy()
+    g_nH[R] += mesh.volume[R] * (x5[1][R] - L) / M
+    g_Q = out["g_src"][:, st["cells"]].T  # [n_src, B]
+    return L, g_Q, g_nH
+
+
+def _fd(mesh, cfg, st, R, n_sub, key, idx, h_rel=1e-4):
+    vals, pats = [], []
+    for sgn in (1, -1):
+        s2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+        base = s2[key][idx]
+        s2[key][idx] = base * (1 + sgn * h_rel)
+        L, pat = _run(mesh, cfg, s2, R, n_sub)
+        vals.append(L)
+        pats.append(pat)
+    same = np.array_equal(pats[0], pats[1])
+    return (vals[0] - vals[1]) / (2 * h_rel * st[key][idx]), same
+
+
+@pytest.mark.parametrize("n_sub", [3])
+def test_adjoint_luminosities_and_densities_vs_fd(n_sub):
+    mesh, cfg, st, R = _setup()
+    L, g_Q, g_nH = _adjoint(mesh, cfg, st, R, n_sub)
+    L0, _ = _run(mesh, cfg, st, R, n_sub)
+    assert L == L0
+    checked = 0
+    for k in range(len(st["cells"])):
+        for b in range(cfg["n_bins"]):
+            fd, same = _fd(mesh, cfg, st, R, n_sub, "Q", (k, b))
+            if not same:
+                continue
+            scale = max(abs(fd), 1e-12 * abs(L))
+            assert abs(g_Q[k, b] - fd) <= 1e-5 * scale + 1e-9 * np.abs(g_Q).max(), (k, b, g_Q[k, b], fd)
+            checked += 1
+    assert checked >= 4
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([rng.choice(np.where(R)[0], 4, replace=False),
+                            rng.choice(np.where(~R)[0], 2, replace=False), st["cells"]])
+    for i in cells:
+        fd, same = _fd(mesh, cfg, st, R, n_sub, "nH", i)
+        if not same:
+            continue
+        scale = max(abs(fd), 1e-3 * np.abs(g_nH).max())
+        assert abs(g_nH[i] - fd) <= 1e-5 * scale, (i, g_nH[i], fd)
+        checked += 1
+    assert checked >= 10
+
+
+def test_adjoint_transport_only_vs_fd():
+    """Transport only (absorption off): the photon number in the region R
+    after three subcycles, differentiated w.r.t. source rates and the
+    initial radiation; exercises gradients, limiter, M1 and the gather."""
+    mesh, cfg, st, R = _setup(chem_mode=0)
+    n_sub = 3
+    C, B = mesh.n_cells, cfg["n_bins"]
+    V = mesh.volume
+
+    def loss(o):
+        N, _ = o.radiation()
+        return float((N[:, R] * V[R]).sum() + 0.3 * (N[0] * V * np.sin(np.arange(C))).sum())
+
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    lN = np.zeros((B, C))
+    lN[:, R] = V[R]
+    lN[0] += 0.3 * V * np.sin(np.arange(C))
+    out = o.adjoint(dt, n_sub, lam_N=lN)
+    assert out["status"] == 0
+    gQ = out["g_src"][:, st["cells"]].T
+    for k in range(2):
+        for b in range(B):
+            vals = []
+            for sg in (1, -1):
+                s2 = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in st.items()}
+                h = 1e-4 * s2["Q"][k, b]
+                s2["Q"][k, b] += sg * h
+                o2 = make_oracle(mesh, cfg, s2)
+                assert o2.step(dt, n_sub) == 0
+                vals.append(loss(o2))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(gQ[k, b] - fd) <= 1e-5 * abs(fd), (k, b, gQ[k, b], fd)
+    # initial radiation, a few components
+    lam0 = out["lam0"]
+    rng = np.random.default_rng(1)
+    for i in rng.choice(C, 6, replace=False):
+        for (arr, idx) in (("N", (1, i)), ("fr", (2, 1, i))):
+            vals = []
+            for sg in (1, -1):
+                s2 = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in st.items()}
+                h = 1e-5 * max(abs(s2["N"]).max(), 1e-30)
+                s2[arr][idx] += sg * h
+                o2 = make_oracle(mesh, cfg, s2)
+                assert o2.step(dt, n_sub) == 0
+                vals.append(loss(o2))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            g = lam0[arr][idx]
+            assert abs(g - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(lam0["N"]).max()), (arr, idx, g, fd)
