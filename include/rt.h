@@ -88,6 +88,8 @@ typedef struct {
   double y_he;            /* n_He / n_H */
   double sigma[3][3];     /* grey cross-sections [bin][HI, HeI, HeII], cm^2 */
   double eps[3][3];       /* heat per photoionisation [bin][species], erg */
+  int gather_sum;         /* RT_MIXED only: 0 = each FP32 face flux widened and summed in FP64;
+                             1 = compensated FP32 pair (error-free two_sum), widened to FP64 once per cell */
 } rt_config;
 
 /* Cells of the static mesh (structure of arrays, n entries each). */
@@ -170,7 +172,7 @@ rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
  * class k (RT_KERNEL_*), the summed device time ms[k] (milliseconds) and the
  * number of launches[k] since the last reset; reset != 0 clears them.
  * n = length of the caller's arrays (at most RT_KERNEL_COUNT are filled). */
-enum { RT_KERNEL_CELL = 0, RT_KERNEL_GRAD = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_COUNT = 3 };
+enum { RT_KERNEL_CHEM = 0, RT_KERNEL_GRAD = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_GATHER = 3, RT_KERNEL_COUNT = 4 };
 rt_status rt_profile_enable(rt_ctx *ctx, int on);
 rt_status rt_profile_read(rt_ctx *ctx, int n, double *ms, int64_t *launches, int reset);
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/rt.h"
+#include "rt_ctx.h"
 #include "rt_kernels.cuh"
 
 using namespace m1rt;
@@ -22,46 +23,6 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
-struct rt_ctx {
-  rt_config cfg{};
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  std::string err;
-  bool mesh_ready = false;
-  int C = 0, F = 0, B = 0, max_deg = 0;
-  double min_dx_cm = 0;
-  // FP64 cell and face data
-  double *vol = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
-  int32_t *off = nullptr, *csr = nullptr;
-  int2* lr = nullptr;
-  d4 *nA64 = nullptr, *rL64 = nullptr, *rR64 = nullptr, *w64 = nullptr;
-  double* minv64 = nullptr;
-  // FP32 copies (mixed precision)
-  float4 *nA32 = nullptr, *rL32 = nullptr, *rR32 = nullptr, *w32 = nullptr;
-  float* minv32 = nullptr;
-  // state
-  d4* rad = nullptr;      // master [C][B]
-  float4* shadow = nullptr;    // FP32 sweep copy [C][B] (mixed)
-  double *nH = nullptr, *x5 = nullptr, *T = nullptr;
-  int32_t* src_idx = nullptr;
-  double* src_rate = nullptr;
-  int n_src_cells = 0, src_cap = 0;
-  int32_t* nsub = nullptr;
-  // work
-  void* G = nullptr;           // [C][B][12] in sweep precision
-  void* flux = nullptr;        // [F][B] 4-vectors in sweep precision
-  double* stage = nullptr;     // staging for caller arrays (max(4BC, 5C) doubles)
-  size_t stage_n = 0;
-  int* status = nullptr;
-  std::vector<void*> allocs;
-  // profiling: event pairs around launches, per kernel class
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_used;   // (class, index of start event)
-  double prof_ms[RT_KERNEL_COUNT] = {0, 0, 0};
-  int64_t prof_n[RT_KERNEL_COUNT] = {0, 0, 0};
-  int64_t launches = 0;
-};
 
 namespace {
 
@@ -129,6 +90,7 @@ rt_status copy_out(rt_ctx* ctx, void* dst, const void* src, size_t bytes) {
 }
 
 bool mixed(const rt_ctx* ctx) { return ctx->cfg.precision == RT_MIXED; }
+bool comp_sum(const rt_ctx* ctx) { return ctx->cfg.gather_sum == 1; }
 
 rt_status check_config(const rt_config* c) {
   if (c->n_bins < 1 || c->n_bins > 3) return fail(nullptr, RT_INVALID_ARG, "n_bins must be 1..3");
@@ -140,15 +102,16 @@ rt_status check_config(const rt_config* c) {
   if (c->chem_mode > 0 && (!(c->f_s > 0) || !(c->f_max > 0) || c->max_substeps < 1 || c->x_floor < 0))
     return fail(nullptr, RT_INVALID_ARG, "bad substep parameters");
   if (c->y_he < 0 || c->lim_eps < 0) return fail(nullptr, RT_INVALID_ARG, "y_he and lim_eps must be >= 0");
+  if (c->gather_sum < 0 || c->gather_sum > 1) return fail(nullptr, RT_INVALID_ARG, "gather_sum must be 0 or 1");
   return RT_OK;
 }
 
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
-  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64};
+  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
-  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32};
+  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32};
 }
 
 ChemParams chem_params(const rt_ctx* ctx) {
@@ -228,15 +191,25 @@ template <class R> void launch_flux(rt_ctx* ctx) {
                                                                             (const R*)ctx->G, (R4<R>*)ctx->flux);
 }
 
-void launch_cell(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
-  ProfScope ps(ctx, RT_KERNEL_CELL);
-  CellArgs a = cell_args(ctx, dt, gather, inject, chem);
+void launch_gather(rt_ctx* ctx, double dt) {
+  ProfScope ps(ctx, RT_KERNEL_GATHER);
+  CellArgs a = cell_args(ctx, dt, 1, 0, 0);
+  const long long n = (long long)ctx->C * ctx->B;
+  if (mixed(ctx) && comp_sum(ctx))
+    k_gather<float, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
+  else if (mixed(ctx))
+    k_gather<float, false><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
+  else
+    k_gather<double, false><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const d4*)ctx->flux, nullptr);
+}
+
+void launch_chem(rt_ctx* ctx, double dt) {
+  ProfScope ps(ctx, RT_KERNEL_CHEM);
+  CellArgs a = cell_args(ctx, dt, 0, 1, 1);
   ChemParams P = chem_params(ctx);
   const int t = 128;
-  if (mixed(ctx))
-    k_cell<float, true><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, (const float4*)ctx->flux, ctx->shadow);
-  else
-    k_cell<double, false><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, (const d4*)ctx->flux, nullptr);
+  if (mixed(ctx)) k_chem<true><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, ctx->shadow);
+  else k_chem<false><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, nullptr);
 }
 
 void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
@@ -338,11 +311,13 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   for (int i = 0; i < C; ++i) {
     if (off[i + 1] == off[i]) return fail(ctx, RT_BAD_MESH, "cell %d has no faces", i);
   }
-  std::vector<int32_t> csr(2 * (size_t)F);
+  std::vector<int32_t> csr(2 * (size_t)F), nbr(2 * (size_t)F);
   {
     std::vector<int32_t> fill(off.begin(), off.end() - 1);
     for (int f = 0; f < F; ++f) {     // ascending face index within each cell
+      nbr[fill[L[f]]] = Rr[f];
       csr[fill[L[f]]++] = f << 1;
+      nbr[fill[Rr[f]]] = L[f];
       csr[fill[Rr[f]]++] = (f << 1) | 1;
     }
   }
@@ -352,7 +327,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   rt_status st;
 #define AL(p, n) if ((st = dalloc(ctx, &(p), (n), #p))) return st
   AL(ctx->vol, C); AL(ctx->cx, C); AL(ctx->cy, C); AL(ctx->cz, C);
-  AL(ctx->off, C + 1); AL(ctx->csr, 2 * (size_t)F); AL(ctx->lr, F);
+  AL(ctx->off, C + 1); AL(ctx->csr, 2 * (size_t)F); AL(ctx->nbr, 2 * (size_t)F); AL(ctx->lr, F);
   AL(ctx->nA64, F); AL(ctx->rL64, F); AL(ctx->rR64, F); AL(ctx->w64, F); AL(ctx->minv64, 6 * (size_t)C);
   AL(ctx->rad, (size_t)C * B); AL(ctx->nH, C); AL(ctx->x5, 5 * (size_t)C); AL(ctx->T, C);
   AL(ctx->src_idx, C); AL(ctx->nsub, C); AL(ctx->status, 1);
@@ -381,6 +356,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   if ((st = copy_in(ctx, ctx->cz, cells->cz, (size_t)C * 8))) return st;
   CK(cudaMemcpyAsync(ctx->off, off.data(), (C + 1) * 4, cudaMemcpyHostToDevice, ctx->stream), "off");
   CK(cudaMemcpyAsync(ctx->csr, csr.data(), 2 * (size_t)F * 4, cudaMemcpyHostToDevice, ctx->stream), "csr");
+  CK(cudaMemcpyAsync(ctx->nbr, nbr.data(), 2 * (size_t)F * 4, cudaMemcpyHostToDevice, ctx->stream), "nbr");
   {
     std::vector<int2> lr(F);
     for (int f = 0; f < F; ++f) lr[f] = make_int2(L[f], Rr[f]);
@@ -532,15 +508,13 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   const double dmax = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
   if (dts > dmax * (1.0 + 1e-12))
     return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
-  // Subcycle s: sources + chemistry, gradients, fluxes, application.  The
-  // application of subcycle s is fused with the sources and chemistry of
-  // subcycle s+1 in one per-cell kernel.
+  // Subcycle: sources + chemistry, gradients, fluxes, application.
   for (int s = 0; s < n_sub; ++s) {
-    launch_cell(ctx, dts, s > 0, 1, 1);
+    launch_chem(ctx, dts);
     launch_grad_any(ctx);
     launch_flux_any(ctx);
+    launch_gather(ctx, dts);
   }
-  launch_cell(ctx, dts, 1, 0, 0);
   return launched(ctx, "rt_step");
 }
 
@@ -660,7 +634,7 @@ rt_status rt_stage_transport(rt_ctx* ctx, double dt) {
   if (!(dt >= 0)) return fail(ctx, RT_INVALID_ARG, "dt must be >= 0");
   launch_grad_any(ctx);
   launch_flux_any(ctx);
-  launch_cell(ctx, dt, 1, 0, 0);
+  launch_gather(ctx, dt);
   return launched(ctx, "transport");
 }
 
@@ -668,7 +642,7 @@ rt_status rt_stage_chemistry(rt_ctx* ctx, double dt) {
   rt_status st = need_mesh(ctx);
   if (st) return st;
   if (!(dt >= 0)) return fail(ctx, RT_INVALID_ARG, "dt must be >= 0");
-  launch_cell(ctx, dt, 0, 1, 1);
+  launch_chem(ctx, dt);
   return launched(ctx, "chemistry");
 }
 

@@ -214,6 +214,111 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   return f;
 }
 
+// FP64 reciprocal: FP32 hardware seed (23 bits) refined by two Newton steps
+// in FP64 (46, then ~53 bits); within an ulp or two of 1/x for x in the FP32
+// normal range, which every denominator of the chemistry step lies in.
+__device__ __forceinline__ double rcp64(double x) {
+  const float xf = (float)x;
+  if (!(fabsf(xf) < 1e30f && fabsf(xf) > 1e-30f)) return 1.0 / x;
+  double y = (double)__frcp_rn(xf);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+__device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
+  float m = fmaxf(fabsf((float)a), fl);
+  return fabsf((float)(b - a)) / m;
+}
+
+// The same attempt as photochem_attempt, arranged for GB300's small FP64
+// unit: divisions become FP64 reciprocals (one per distinct denominator),
+// the photon removal uses N_b' = N_b (1 - tau'_b / (1 + tau_b)) instead of a
+// division by N_b, and the substep-control measure f (which only steers step
+// lengths and the accept test) is formed in FP32.  State, rates products and
+// all updates stay FP64.
+__device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const CellState& s,
+                                          CellState& t) {
+  const int B = P.B;
+  const double c = P.c_red;
+  const double cdt = c * dt;
+  const double nHe = P.y_he * nH;
+  const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
+  const Rates r = RateEval<true>::eval(s.T);
+
+  const double ns0 = nH * s.xHI, ns1 = nHe * s.yI, ns2 = nHe * s.yII;
+  double inv1pt[kMaxBins], Nbar[kMaxBins];
+  double G0 = 0, G1 = 0, G2 = 0;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      double kap = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
+      inv1pt[b] = rcp64(1.0 + cdt * kap);
+      Nbar[b] = s.N[b] * inv1pt[b];
+      G0 += P.sigma[b][0] * Nbar[b];
+      G1 += P.sigma[b][1] * Nbar[b];
+      G2 += P.sigma[b][2] * Nbar[b];
+    }
+  }
+  const double ne0 = nH * s.xHII + nHe * (s.yII + 2.0 * s.yIII);
+  const double aH = cdt * G0 + (coll ? dt * r.bHI * ne0 : 0.0);
+  const double bH = recomb ? dt * r.aHII * ne0 : 0.0;
+  const double iden = rcp64(1.0 + aH + bH);
+  t.xHI = (s.xHI * (1.0 + bH) + bH * s.xHII) * iden;
+  t.xHII = (s.xHII * (1.0 + aH) + aH * s.xHI) * iden;
+  const double ne1 = nH * t.xHII + nHe * (s.yII + 2.0 * s.yIII);
+  const double A = cdt * G1 + (coll ? dt * r.bHeI * ne1 : 0.0);
+  const double Bb = recomb ? dt * r.aHeII * ne1 : 0.0;
+  const double Cc = cdt * G2 + (coll ? dt * r.bHeII * ne1 : 0.0);
+  const double D = recomb ? dt * r.aHeIII * ne1 : 0.0;
+  const double iA = rcp64(1.0 + A), iD = rcp64(1.0 + D);
+  t.yII = (s.yII + A * s.yI * iA + D * s.yIII * iD) * rcp64(1.0 + Bb * iA + Cc * iD);
+  t.yI = (s.yI + Bb * t.yII) * iA;
+  t.yIII = (s.yIII + Cc * t.yII) * iD;
+
+  const double m0 = nH * t.xHI, m1 = nHe * t.yI, m2 = nHe * t.yII;
+  double heat_e = 0.0;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      const double a0 = P.sigma[b][0] * m0, a1 = P.sigma[b][1] * m1, a2 = P.sigma[b][2] * m2;
+      const double taup = cdt * ((a0 + a1) + a2);
+      double sc = 1.0 - taup * inv1pt[b];
+      sc = sc > 0.0 ? sc : 0.0;
+      if (heat) heat_e += cdt * Nbar[b] * (P.eps[b][0] * a0 + P.eps[b][1] * a1 + P.eps[b][2] * a2);
+      t.N[b] = s.N[b] * sc;
+      t.f[b][0] = s.f[b][0] * sc;
+      t.f[b][1] = s.f[b][1] * sc;
+      t.f[b][2] = s.f[b][2] * sc;
+    }
+  }
+  const float fl = (float)P.x_floor;
+  float f = 0.0f;
+  if (P.mode == 2) {
+    const double ntot0 = nH * (1.0 + P.y_he) + ne0;
+    const double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
+    const double lam = cool ? RateEval<true>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
+                                                      nHe * s.yIII)
+                            : 0.0;
+    const double e1 = e0 + heat_e - dt * lam;
+    const double ne2 = nH * t.xHII + nHe * (t.yII + 2.0 * t.yIII);
+    const double ntot1 = nH * (1.0 + P.y_he) + ne2;
+    t.T = e1 * rcp64(1.5 * kBoltzmann * ntot1);
+    f = rel_change_f(e0, e1, 0.0f);
+  } else {
+    t.T = s.T;
+  }
+  f = fmaxf(f, rel_change_f(s.xHI, t.xHI, fl));
+  f = fmaxf(f, rel_change_f(s.xHII, t.xHII, fl));
+  if (P.y_he > 0) {
+    f = fmaxf(f, rel_change_f(s.yI, t.yI, fl));
+    f = fmaxf(f, rel_change_f(s.yII, t.yII, fl));
+    f = fmaxf(f, rel_change_f(s.yIII, t.yIII, fl));
+  }
+  return (double)f;
+}
+
 // Adaptive substeps of Sec. 4.1.1 over dt_sub: first attempt = the whole
 // subcycle; reject if f > f_max and retry with dt f_s / f; after an accepted
 // attempt the next is dt min(f_s / f, 2), clipped to the remaining time.
@@ -227,7 +332,7 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
   while (rem > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;
-    double f = photochem_attempt<Fast>(P, nH, dt, s, t);
+    double f = Fast ? photochem_attempt_mixed(P, nH, dt, s, t) : photochem_attempt<false>(P, nH, dt, s, t);
     if (f > P.f_max) {
       dt = dt * (P.f_s / f);
       continue;

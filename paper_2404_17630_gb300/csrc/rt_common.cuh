@@ -45,6 +45,7 @@ template <class R> struct Geo {
   int C, F, B;
   const int32_t* off;     // C+1 CSR offsets
   const int32_t* csr;     // 2F entries: (face << 1) | side, side 1 = this cell is the right cell
+  const int32_t* nbr;     // 2F entries: the other cell of the same face
   const int2* lr;         // F: (left, right)
   const R4<R>* nA;        // F: (n_x, n_y, n_z, A)
   const R4<R>* rL;        // F: x_f - s_L (minimum image), w unused

@@ -1,0 +1,65 @@
+// Private: the library context shared by the translation units of libm1rt.
+#pragma once
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rt.h"
+#include "rt_common.cuh"
+
+using m1rt::d4;
+
+struct rt_ctx {
+  rt_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool mesh_ready = false;
+  int C = 0, F = 0, B = 0, max_deg = 0;
+  double min_dx_cm = 0;
+  // FP64 cell and face data
+  double *vol = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
+  int32_t *off = nullptr, *csr = nullptr, *nbr = nullptr;
+  int2* lr = nullptr;
+  d4 *nA64 = nullptr, *rL64 = nullptr, *rR64 = nullptr, *w64 = nullptr;
+  double* minv64 = nullptr;
+  // FP32 copies (mixed precision)
+  float4 *nA32 = nullptr, *rL32 = nullptr, *rR32 = nullptr, *w32 = nullptr;
+  float* minv32 = nullptr;
+  // state
+  d4* rad = nullptr;      // master [C][B]
+  float4* shadow = nullptr;    // FP32 sweep copy [C][B] (mixed)
+  double *nH = nullptr, *x5 = nullptr, *T = nullptr;
+  int32_t* src_idx = nullptr;
+  double* src_rate = nullptr;
+  int n_src_cells = 0, src_cap = 0;
+  int32_t* nsub = nullptr;
+  // work
+  void* G = nullptr;           // [C][B][12] in sweep precision
+  void* flux = nullptr;        // [F][B] 4-vectors in sweep precision
+  double* stage = nullptr;     // staging for caller arrays (max(4BC, 5C) doubles)
+  size_t stage_n = 0;
+  int* status = nullptr;
+  std::vector<void*> allocs;
+  // profiling: event pairs around launches, per kernel class
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;   // (class, index of start event)
+  double prof_ms[RT_KERNEL_COUNT] = {};
+  int64_t prof_n[RT_KERNEL_COUNT] = {};
+  int64_t launches = 0;
+  // sources as last given (for per-source adjoint outputs)
+  std::vector<int64_t> src_cells;
+  // adjoint buffers (allocated on first use)
+  struct Adj {
+    int nseg = 0, k = 0;
+    size_t rec_cap = 0;
+    d4 *ck_rad = nullptr, *tp_rad_chem = nullptr, *tp_rad_trans = nullptr, *fin_rad = nullptr;
+    double *ck_x5 = nullptr, *ck_T = nullptr, *tp_x5 = nullptr, *tp_T = nullptr, *fin_x5 = nullptr, *fin_T = nullptr;
+    d4 *lam_rad = nullptr, *lam_part = nullptr, *lam_in = nullptr, *lampre = nullptr, *lamr = nullptr;
+    double *lam_x5 = nullptr, *lam_T = nullptr, *lam_nH = nullptr, *lam_S = nullptr, *lim_coef = nullptr;
+    int32_t *lim_cell = nullptr, *count = nullptr, *chem_off = nullptr;
+    void* rec = nullptr;
+    std::vector<void*> allocs;
+  } adj;
+};

@@ -6,9 +6,10 @@
 //                  (cell, bin)  (Sec. 2.3.2, 4.1.2)
 //   k_flux<R>      face reconstruction, M1 closure, Lax-Friedrichs flux, one
 //                  thread per (face, bin)  (Sec. 2.3.3, 4.1.3)
-//   k_cell<R,Fast> per cell: deterministic CSR gather of the stored face
-//                  fluxes with FP64 accumulation, source injection and
-//                  thermochemistry (Sec. 4.1.3, Eq. E, Sec. 4.1.1)
+//   k_gather<R>    per (cell, bin): deterministic CSR gather of the stored
+//                  face fluxes, FP64 update (Sec. 4.1.3)
+//   k_chem<Fast>   per cell: source injection and thermochemistry (Eq. E,
+//                  Sec. 2.3.1, 4.1.1)
 //
 // R is the precision of the transport sweep (double, or float in the mixed
 // mode of Sec. 6.2); the master state, the gather sums, the volume divisions
@@ -179,10 +180,10 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     mx[q] = mn[q] = comp<R>(pi, q);
   }
   const int k0 = g.off[i], k1 = g.off[i + 1];
+#pragma unroll 4
   for (int k = k0; k < k1; ++k) {
     const int e = __ldg(g.csr + k), f = e >> 1;
-    const int2 c = __ldg(g.lr + f);
-    const int j = (e & 1) ? c.x : c.y;
+    const int j = __ldg(g.nbr + k);
     const R4<R> pj = ld4<R>(rad + (size_t)j * B + b);
     const R4<R> w = ld4<R>(g.w + f);
 #pragma unroll
@@ -208,6 +209,15 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     psi[q] = R(1);
   }
   if (limiter) {
+    // psi = min over faces of (max - phi_i) / (g.x) for g.x > 0 and
+    // (min - phi_i) / (g.x) for g.x < 0.  Rounded division is monotone in
+    // the divisor, so each of these minima is the quotient by the largest
+    // (most negative) g.x: two divisions per component instead of one per
+    // face, with bitwise the same result.
+    R dpos[4], dneg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = R(0);
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
       const int e = __ldg(g.csr + k), f = e >> 1;
       const R4<R> x = ld4<R>((e & 1) ? (g.rR + f) : (g.rL + f));
@@ -215,20 +225,38 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-        R lim = R(1);
         if (dphi * dphi > lim_eps2 * gg[q] * xx) {
-          R vi = comp<R>(pi, q);
-          lim = dphi > R(0) ? (mx[q] - vi) / dphi : (mn[q] - vi) / dphi;
+          dpos[q] = dphi > dpos[q] ? dphi : dpos[q];
+          dneg[q] = dphi < dneg[q] ? dphi : dneg[q];
         }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const R vi = comp<R>(pi, q);
+      if (dpos[q] > R(0)) {
+        R lim = (mx[q] - vi) / dpos[q];
+        psi[q] = lim < psi[q] ? lim : psi[q];
+      }
+      if (dneg[q] < R(0)) {
+        R lim = (mn[q] - vi) / dneg[q];
         psi[q] = lim < psi[q] ? lim : psi[q];
       }
     }
   }
+  R o[12];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    Go[3 * q + 0] = gr[q][0] * psi[q];
-    Go[3 * q + 1] = gr[q][1] * psi[q];
-    Go[3 * q + 2] = gr[q][2] * psi[q];
+    o[3 * q + 0] = gr[q][0] * psi[q];
+    o[3 * q + 1] = gr[q][1] * psi[q];
+    o[3 * q + 2] = gr[q][2] * psi[q];
+  }
+  R4<R>* G4 = reinterpret_cast<R4<R>*>(Go);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    R4<R> w;
+    w.x = o[4 * v]; w.y = o[4 * v + 1]; w.z = o[4 * v + 2]; w.w = o[4 * v + 3];
+    G4[v] = w;
   }
 }
 
@@ -239,7 +267,11 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
 // Linear extrapolation of the cell state to the face centre, clamped to
 // N >= 0 and |F| <= c N.
 template <class R>
-__device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__ Gc, const R4<R>& x, R v[4]) {
+__device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__ Gp, const R4<R>& x, R v[4]) {
+  // the 12 gradient words of one (cell, bin) as three aligned 4-vectors
+  const R4<R>* G4 = reinterpret_cast<const R4<R>*>(Gp);
+  const R4<R> a = ld4<R>(G4), b = ld4<R>(G4 + 1), c = ld4<R>(G4 + 2);
+  const R Gc[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     R d = Gc[3 * q] * x.x + Gc[3 * q + 1] * x.y + Gc[3 * q + 2] * x.z;
@@ -327,9 +359,74 @@ struct CellArgs {
   int do_gather, do_inject, do_chem;
 };
 
-template <class R, bool Fast>
-__global__ void __launch_bounds__(128) k_cell(CellArgs a, ChemParams P, const R4<R>* __restrict__ flux,
-                                              R4<R>* __restrict__ shadow) {
+// Error-free sum of two floats (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Flux application, one thread per (cell, bin): the cell's stored face
+// fluxes are summed in CSR order (ascending face index, + where the cell is
+// the left cell, - where it is the right cell) and U <- U - c dt / V * sum in
+// FP64.  Comp (mixed precision): the FP32 terms are summed as an unevaluated
+// FP32 pair hi + lo (error-free two_sum), widened to FP64 once; otherwise
+// each term is widened and summed in FP64.  Writes the FP32 shadow if given.
+template <class R, bool Comp>
+__global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
+                                                float4* __restrict__ shadow) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = a.B;
+  if (t >= a.C * B) return;
+  const int i = t / B, b = t % B;
+  const int k0 = a.off[i], k1 = a.off[i + 1];
+  double acc[4];
+  if (Comp) {
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+      const int e = __ldg(a.csr + k), f = e >> 1;
+      const float sg = (e & 1) ? -1.0f : 1.0f;
+      const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
+      const float tv[4] = {sg * (float)v.x, sg * (float)v.y, sg * (float)v.z, sg * (float)v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float sum, err;
+        two_sum(hi[q], tv[q], sum, err);
+        hi[q] = sum;
+        lo[q] += err;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = (double)hi[q] + (double)lo[q];
+  } else {
+    acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+      const int e = __ldg(a.csr + k), f = e >> 1;
+      const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
+      if (e & 1) {
+        acc[0] -= (double)v.x; acc[1] -= (double)v.y; acc[2] -= (double)v.z; acc[3] -= (double)v.w;
+      } else {
+        acc[0] += (double)v.x; acc[1] += (double)v.y; acc[2] += (double)v.z; acc[3] += (double)v.w;
+      }
+    }
+  }
+  const double kfac = a.lam / a.vol[i];
+  d4 u = a.rad[t];
+  u.x -= kfac * acc[0];
+  u.y -= kfac * acc[1];
+  u.z -= kfac * acc[2];
+  u.w -= kfac * acc[3];
+  a.rad[t] = u;
+  if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
+  if (shadow) shadow[t] = make_float4((float)u.x, (float)u.y, (float)u.z, (float)u.w);
+}
+
+// Sources and thermochemistry, one thread per cell (Eq. E source term,
+// Sec. 2.3.1, 4.1.1).  Writes the FP32 shadow of the radiation if given.
+template <bool Fast>
+__global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* __restrict__ shadow) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.C) return;
   const int B = a.B;
@@ -339,37 +436,6 @@ __global__ void __launch_bounds__(128) k_cell(CellArgs a, ChemParams P, const R4
     if (b < B) {
       d4 v = a.rad[(size_t)i * B + b];
       s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
-    }
-  }
-  if (a.do_gather) {
-    double acc[kMaxBins][4];
-#pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.0;
-    const int k0 = a.off[i], k1 = a.off[i + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int e = __ldg(a.csr + k), f = e >> 1;
-      const bool right = e & 1;
-#pragma unroll
-      for (int b = 0; b < kMaxBins; ++b) {
-        if (b < B) {
-          const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
-          if (right) {
-            acc[b][0] -= (double)v.x; acc[b][1] -= (double)v.y; acc[b][2] -= (double)v.z; acc[b][3] -= (double)v.w;
-          } else {
-            acc[b][0] += (double)v.x; acc[b][1] += (double)v.y; acc[b][2] += (double)v.z; acc[b][3] += (double)v.w;
-          }
-        }
-      }
-    }
-    const double kfac = a.lam / a.vol[i];
-#pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) {
-      if (b < B) {
-        s.N[b] -= kfac * acc[b][0];
-        s.f[b][0] -= kfac * acc[b][1];
-        s.f[b][1] -= kfac * acc[b][2];
-        s.f[b][2] -= kfac * acc[b][3];
-      }
     }
   }
   if (a.do_inject) {
@@ -398,11 +464,8 @@ __global__ void __launch_bounds__(128) k_cell(CellArgs a, ChemParams P, const R4
     if (b < B) {
       a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
       if (!isfinite(s.N[b])) bad = true;
-      if (shadow) {
-        R4<R> o;
-        o.x = (R)s.N[b]; o.y = (R)s.f[b][0]; o.z = (R)s.f[b][1]; o.w = (R)s.f[b][2];
-        shadow[(size_t)i * B + b] = o;
-      }
+      if (shadow) shadow[(size_t)i * B + b] = make_float4((float)s.N[b], (float)s.f[b][0], (float)s.f[b][1],
+                                                          (float)s.f[b][2]);
     }
   }
   if (bad) atomicOr(a.status, kStNonFinite);

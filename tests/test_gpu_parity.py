@@ -21,12 +21,13 @@ def rel(a, b):
     return np.abs(a - b).max() / (s if s > 0 else 1.0)
 
 
-def make_gpu(mesh, cfg, state, precision="fp64"):
+def make_gpu(mesh, cfg, state, precision="fp64", **extra):
     import torch
     from paper_2404_17630_gb300 import RT, make_config
     assert torch.cuda.is_available()
     c = dict(cfg)
     c["precision"] = precision
+    c.update(extra)
     rt = RT(make_config(**c), mesh)
     rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
     rt.set_gas(state["nH"], state["x5"], state["T"])
@@ -154,12 +155,13 @@ def test_voronoi_2e5_one_subcycle_fp64():
 # mixed precision
 # ---------------------------------------------------------------------------
 
-def test_mixed_step_errors():
+@pytest.mark.parametrize("gather_sum", [0, 1])
+def test_mixed_step_errors(gather_sum):
     """FP32 sweep: per-field error against the FP64 oracle after a few
     subcycles; N and F carry FP32 rounding of the fluxes (~1e-7 relative per
     subcycle), the abundances and T follow through the chemistry."""
     mesh, cfg, st = voronoi_case(n=16)
-    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st, precision="mixed")
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st, precision="mixed", gather_sum=gather_sum)
     dt = o.max_dt()
     assert o.step(4 * dt, 4) == 0
     rt.step(4 * dt, 4)
