@@ -166,6 +166,24 @@ rt_status rt_stage_fluxes(rt_ctx *ctx, const double *G, double *flux);
 rt_status rt_stage_transport(rt_ctx *ctx, double dt);
 rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
 
+/* Reverse mode of rt_step(dt, n_sub), FP64 precision, chem_mode 0 or 1.
+ * The paper has no adjoint; this is the exact derivative of the discrete
+ * forward map (sources, every chemistry attempt with the substep controller
+ * of Sec. 4.1.1, gradients and limiter on their active branch, M1 face
+ * fluxes, flux application).  Starting from the context's current state it
+ * runs the step (leaving the final state, as rt_step does), keeping a full
+ * checkpoint every checkpoint_every subcycles, then walks back segment by
+ * segment, recomputing each segment's tape.
+ * In (cotangents of the final fields, caller layout, NULL = zero):
+ *   lam_N[B*C], lam_F[3*B*C] (w.r.t. F, photons cm^-2 s^-1), lam_x5[5*C], lam_T[C].
+ * Out (NULL = not wanted): dL_dQ[n_src*B] per source of the last
+ *   rt_set_sources call (photons/s), dL_dnH[C], and the cotangents of the
+ *   initial fields lam0_N, lam0_F, lam0_x5, lam0_T (same layouts).
+ * Synchronous.  RT_INVALID_ARG for RT_MIXED or chem_mode 2. */
+rt_status rt_adjoint(rt_ctx *ctx, double dt, int n_sub, int checkpoint_every, const double *lam_N,
+                     const double *lam_F, const double *lam_x5, const double *lam_T, double *dL_dQ,
+                     double *dL_dnH, double *lam0_N, double *lam0_F, double *lam0_x5, double *lam0_T);
+
 /* Per-kernel timing: with profiling on, every kernel that rt_step and the
  * stage entry points launch is bracketed by CUDA events on the context's
  * stream.  rt_profile_read waits for the stream and returns, per kernel

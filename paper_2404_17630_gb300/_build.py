@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libm1rt.so")
 SOURCES = ["rt_api.cu", "rt_noalloc.cu"]
-HEADERS = ["rt_common.cuh", "rt_chem.cuh", "rt_kernels.cuh", "rt_ctx.h"]
+HEADERS = ["rt_common.cuh", "rt_chem.cuh", "rt_kernels.cuh", "rt_ctx.h", "rt_adjoint.cuh"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
 

@@ -1,0 +1,650 @@
+// Adjoint kernels: reverse mode of the FP64 subcycle (isothermal chemistry
+// or transport only).  The paper has no adjoint; these are the exact
+// derivatives of the forward kernels, organised as gathers (no atomics):
+//
+//   k_adj_face      per (face, bin): cotangent of the face flux from the two
+//                   cells' cotangents, back through Lax-Friedrichs, the M1
+//                   closure and the face-state clamps -> cotangent of each
+//                   side's extrapolated state (4 + 4 per face and bin)
+//   k_adj_cellgrad  per (cell, bin): gathers its faces' side cotangents into
+//                   the cotangents of its value and its gradients, then back
+//                   through the limiter (active branch) and M^-1
+//   k_adj_cellsum   per (cell, bin): the least-squares right-hand side and
+//                   the limiter extremes read neighbour values; their
+//                   cotangents are gathered here from the neighbours' records
+//   k_chem_count / k_chem_record / k_chem_adj
+//                   per cell: re-run the chemistry attempts of one subcycle,
+//                   lay them out in a tape, walk back through them together
+//                   with the substep controller (Sec. 4.1.1) and the source
+//                   term.
+#pragma once
+#include "rt_kernels.cuh"
+
+namespace m1rt {
+
+// ---------------------------------------------------------------------------
+// transport
+// ---------------------------------------------------------------------------
+
+// Reverse of m1_normal (N D n): lamP -> lamN, lamf (accumulated).
+__device__ __forceinline__ void m1_normal_vjp(const double v[4], double n0, double n1, double n2, const double lP[3],
+                                              double& lN, double lf[3]) {
+  const double fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+  const double lPn = lP[0] * n0 + lP[1] * n1 + lP[2] * n2;
+  if (v[0] > 0.0 && fl > 0.0) {
+    double f = fl / v[0];
+    const bool clamped = f > 1.0;
+    if (clamped) f = 1.0;
+    const double s = sqrt(4.0 - 3.0 * f * f);
+    const double den = 5.0 + 2.0 * s;
+    const double chi = (3.0 + 4.0 * f * f) / den;
+    const double u0 = v[1] / fl, u1 = v[2] / fl, u2 = v[3] / fl;
+    const double un = u0 * n0 + u1 * n1 + u2 * n2;
+    const double a = 0.5 * (1.0 - chi), bb = 0.5 * (3.0 * chi - 1.0);
+    const double lPu = lP[0] * u0 + lP[1] * u1 + lP[2] * u2;
+    lN += a * lPn + bb * un * lPu;
+    const double la = v[0] * lPn, lbb = v[0] * un * lPu;
+    const double lu0 = v[0] * bb * (n0 * lPu + un * lP[0]);
+    const double lu1 = v[0] * bb * (n1 * lPu + un * lP[1]);
+    const double lu2 = v[0] * bb * (n2 * lPu + un * lP[2]);
+    const double lchi = -0.5 * la + 1.5 * lbb;
+    const double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f / s) / (den * den);
+    const double lff = clamped ? 0.0 : lchi * dchi;
+    const double lfl = lff / v[0];
+    lN -= lff * fl / (v[0] * v[0]);
+    const double luu = lu0 * u0 + lu1 * u1 + lu2 * u2;
+    lf[0] += (lu0 - luu * u0) / fl + lfl * u0;
+    lf[1] += (lu1 - luu * u1) / fl + lfl * u1;
+    lf[2] += (lu2 - luu * u2) / fl + lfl * u2;
+  } else {
+    lN += lPn / 3.0;
+  }
+}
+
+// Face state before the clamps (the linear extrapolation) of one side.
+__device__ __forceinline__ void face_pre(const d4& p, const double* __restrict__ Gp, const d4& x, double v[4]) {
+  const d4* G4 = reinterpret_cast<const d4*>(Gp);
+  const d4 a = G4[0], b = G4[1], c = G4[2];
+  const double Gc[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+  const double pc[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = pc[q] + (Gc[3 * q] * x.x + Gc[3 * q + 1] * x.y + Gc[3 * q + 2] * x.z);
+}
+
+// Clamps of the face state (N >= 0, |F| <= c N), forward.
+__device__ __forceinline__ void face_post(const double pre[4], double v[4]) {
+  v[0] = pre[0] < 0.0 ? 0.0 : pre[0];
+  v[1] = pre[1]; v[2] = pre[2]; v[3] = pre[3];
+  const double fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+  if (fl > v[0]) {
+    const double s = fl > 0.0 ? v[0] / fl : 0.0;
+    v[1] *= s; v[2] *= s; v[3] *= s;
+  }
+}
+
+// Reverse of face_post: lv (cotangent of the clamped state) -> lpre.
+__device__ __forceinline__ void face_post_vjp(const double pre[4], const double lv[4], double lpre[4]) {
+  const bool clampN = pre[0] < 0.0;
+  const double v0 = clampN ? 0.0 : pre[0];
+  const double fl = sqrt(pre[1] * pre[1] + pre[2] * pre[2] + pre[3] * pre[3]);
+  lpre[0] = lv[0]; lpre[1] = lv[1]; lpre[2] = lv[2]; lpre[3] = lv[3];
+  if (fl > v0) {
+    const double lvf = lv[1] * pre[1] + lv[2] * pre[2] + lv[3] * pre[3];
+    lpre[0] = lv[0] + lvf / fl;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lv[k] - lvf * pre[k] / (fl * fl));
+  }
+  if (clampN) lpre[0] = 0.0;
+}
+
+struct AdjArgs {
+  int C, F, B;
+  const int32_t* off;
+  const int32_t* csr;
+  const int32_t* nbr;
+  const int2* lr;
+  const d4* nA;
+  const d4* rL;
+  const d4* rR;
+  const d4* w;
+  const double* minv;
+  const double* vol;
+  const d4* rad;          // state before the transport pass
+  const double* G;        // its limited gradients
+  const d4* lam_out;      // cotangent of the state after the pass
+  d4* lampre;             // [F][B][2] cotangents of the extrapolated face states
+  d4* lamr;               // [C][B][3] cotangents of the least-squares right-hand sides
+  double* lim_coef;       // [C][B][4] cotangent owed to the limiting extreme
+  int32_t* lim_cell;      // [C][B][4] the cell holding that extreme (-1: none)
+  d4* lam_part;           // [C][B] partial cotangent of the state before the pass
+  d4* lam_in;             // [C][B] result: cotangent of the state before the pass
+  double lam;             // c_red dt / unit_length_cm
+  int order, limiter;
+  double lim_eps2;
+};
+
+__global__ void __launch_bounds__(256) k_adj_face(AdjArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = a.B;
+  if (t >= a.F * B) return;
+  const int f = t / B, b = t % B;
+  const int2 c = a.lr[f];
+  const d4 nA = a.nA[f];
+  const size_t sL = (size_t)c.x * B + b, sR = (size_t)c.y * B + b;
+  const d4 lo_L = a.lam_out[sL], lo_R = a.lam_out[sR];
+  const double iVL = 1.0 / a.vol[c.x], iVR = 1.0 / a.vol[c.y];
+  double lout[4] = {a.lam * (lo_R.x * iVR - lo_L.x * iVL), a.lam * (lo_R.y * iVR - lo_L.y * iVL),
+                    a.lam * (lo_R.z * iVR - lo_L.z * iVL), a.lam * (lo_R.w * iVR - lo_L.w * iVL)};
+  double preL[4], preR[4], vL[4], vR[4];
+  face_pre(a.rad[sL], a.G + sL * 12, a.rL[f], preL);
+  face_pre(a.rad[sR], a.G + sR * 12, a.rR[f], preR);
+  face_post(preL, vL);
+  face_post(preR, vR);
+  const double A = nA.w;
+  const double lfn = A * lout[0];
+  double lvL[4], lvR[4], lP[3];
+  lvL[0] = 0.5 * A * lout[0];
+  lvR[0] = -0.5 * A * lout[0];
+  const double n[3] = {nA.x, nA.y, nA.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lvL[1 + k] = 0.5 * lfn * n[k] + 0.5 * A * lout[1 + k];
+    lvR[1 + k] = 0.5 * lfn * n[k] - 0.5 * A * lout[1 + k];
+    lP[k] = 0.5 * A * lout[1 + k];
+  }
+  m1_normal_vjp(vL, n[0], n[1], n[2], lP, lvL[0], lvL + 1);
+  m1_normal_vjp(vR, n[0], n[1], n[2], lP, lvR[0], lvR + 1);
+  double pL[4], pR[4];
+  face_post_vjp(preL, lvL, pL);
+  face_post_vjp(preR, lvR, pR);
+  a.lampre[(size_t)t * 2] = make_d4(pL[0], pL[1], pL[2], pL[3]);
+  a.lampre[(size_t)t * 2 + 1] = make_d4(pR[0], pR[1], pR[2], pR[3]);
+}
+
+__device__ __forceinline__ double d4c(const d4& v, int q) { return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w)); }
+
+__global__ void __launch_bounds__(256) k_adj_cellgrad(AdjArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = a.B;
+  if (t >= a.C * B) return;
+  const int i = t / B, b = t % B;
+  const int k0 = a.off[i], k1 = a.off[i + 1];
+  const d4 lo = a.lam_out[t];
+  double lU[4] = {lo.x, lo.y, lo.z, lo.w};
+  double lG[4][3] = {};
+  for (int k = k0; k < k1; ++k) {
+    const int e = a.csr[k], f = e >> 1, side = e & 1;
+    const d4 lp = a.lampre[((size_t)f * B + b) * 2 + side];
+    const d4 x = side ? a.rR[f] : a.rL[f];
+    const double l4[4] = {lp.x, lp.y, lp.z, lp.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lU[q] += l4[q];
+      lG[q][0] += l4[q] * x.x;
+      lG[q][1] += l4[q] * x.y;
+      lG[q][2] += l4[q] * x.z;
+    }
+  }
+  double lr_out[4][3] = {};
+  double coef[4] = {0, 0, 0, 0};
+  int jst[4] = {-1, -1, -1, -1};
+  if (a.order >= 2) {
+    const d4 pi4 = a.rad[t];
+    double r[4][3] = {}, mx[4], mn[4];
+    int jmx[4], jmn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { mx[q] = mn[q] = d4c(pi4, q); jmx[q] = jmn[q] = i; }
+    for (int k = k0; k < k1; ++k) {
+      const int e = a.csr[k], f = e >> 1;
+      const int j = a.nbr[k];
+      const d4 pj = a.rad[(size_t)j * B + b];
+      const d4 w = a.w[f];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double vj = d4c(pj, q), vi = d4c(pi4, q);
+        const double dphi = (e & 1) ? (vi - vj) : (vj - vi);
+        r[q][0] += w.x * dphi; r[q][1] += w.y * dphi; r[q][2] += w.z * dphi;
+        if (vj > mx[q]) { mx[q] = vj; jmx[q] = j; }
+        if (vj < mn[q]) { mn[q] = vj; jmn[q] = j; }
+      }
+    }
+    const double* m = a.minv + 6 * (size_t)i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double g[3];
+      g[0] = m[0] * r[q][0] + m[1] * r[q][1] + m[2] * r[q][2];
+      g[1] = m[1] * r[q][0] + m[3] * r[q][1] + m[4] * r[q][2];
+      g[2] = m[2] * r[q][0] + m[4] * r[q][1] + m[5] * r[q][2];
+      double lg[3] = {lG[q][0], lG[q][1], lG[q][2]};
+      if (a.limiter) {
+        const double vi = d4c(pi4, q);
+        const double gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        double psi = 1.0, dstar = 0.0, xs[3] = {0, 0, 0};
+        int js = -1;
+        for (int k = k0; k < k1; ++k) {
+          const int e = a.csr[k], f = e >> 1;
+          const d4 x = (e & 1) ? a.rR[f] : a.rL[f];
+          const double dphi = g[0] * x.x + g[1] * x.y + g[2] * x.z;
+          const double xx = x.x * x.x + x.y * x.y + x.z * x.z;
+          if (dphi * dphi > a.lim_eps2 * gg * xx) {
+            const double lim = dphi > 0.0 ? (mx[q] - vi) / dphi : (mn[q] - vi) / dphi;
+            if (lim < psi) {
+              psi = lim; dstar = dphi; xs[0] = x.x; xs[1] = x.y; xs[2] = x.z;
+              js = dphi > 0.0 ? jmx[q] : jmn[q];
+            }
+          }
+        }
+        if (js >= 0) {
+          const double sdot = lG[q][0] * g[0] + lG[q][1] * g[1] + lG[q][2] * g[2];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) lg[d] = psi * lG[q][d] - sdot * psi / dstar * xs[d];
+          if (js != i) {
+            lU[q] -= sdot / dstar;
+            coef[q] = sdot / dstar;
+            jst[q] = js;
+          }
+        }
+      }
+      lr_out[q][0] = m[0] * lg[0] + m[1] * lg[1] + m[2] * lg[2];
+      lr_out[q][1] = m[1] * lg[0] + m[3] * lg[1] + m[4] * lg[2];
+      lr_out[q][2] = m[2] * lg[0] + m[4] * lg[1] + m[5] * lg[2];
+    }
+  }
+  d4* lr4 = a.lamr + (size_t)t * 3;
+  lr4[0] = make_d4(lr_out[0][0], lr_out[0][1], lr_out[0][2], lr_out[1][0]);
+  lr4[1] = make_d4(lr_out[1][1], lr_out[1][2], lr_out[2][0], lr_out[2][1]);
+  lr4[2] = make_d4(lr_out[2][2], lr_out[3][0], lr_out[3][1], lr_out[3][2]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a.lim_coef[(size_t)t * 4 + q] = coef[q];
+    a.lim_cell[(size_t)t * 4 + q] = jst[q];
+  }
+  a.lam_part[t] = make_d4(lU[0], lU[1], lU[2], lU[3]);
+}
+
+__device__ __forceinline__ void load_lamr(const d4* lamr, size_t t, double o[12]) {
+  const d4 a = lamr[t * 3], b = lamr[t * 3 + 1], c = lamr[t * 3 + 2];
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+  o[6] = b.z; o[7] = b.w; o[8] = c.x; o[9] = c.y; o[10] = c.z; o[11] = c.w;
+}
+
+__global__ void __launch_bounds__(256) k_adj_cellsum(AdjArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = a.B;
+  if (t >= a.C * B) return;
+  const int i = t / B, b = t % B;
+  const d4 p = a.lam_part[t];
+  double lU[4] = {p.x, p.y, p.z, p.w};
+  if (a.order >= 2) {
+    for (int k = a.off[i]; k < a.off[i + 1]; ++k) {
+      const int e = a.csr[k], f = e >> 1;
+      const int j = a.nbr[k];
+      const int2 c = a.lr[f];
+      double rl[12], rr[12];
+      load_lamr(a.lamr, (size_t)c.x * B + b, rl);
+      load_lamr(a.lamr, (size_t)c.y * B + b, rr);
+      const d4 w = a.w[f];
+      const double sg = (e & 1) ? 1.0 : -1.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        lU[q] += sg * (w.x * (rl[3 * q] + rr[3 * q]) + w.y * (rl[3 * q + 1] + rr[3 * q + 1]) +
+                       w.z * (rl[3 * q + 2] + rr[3 * q + 2]));
+        const size_t jq = ((size_t)j * B + b) * 4 + q;
+        if (a.lim_cell[jq] == i) lU[q] += a.lim_coef[jq];
+      }
+    }
+  }
+  a.lam_in[t] = make_d4(lU[0], lU[1], lU[2], lU[3]);
+}
+
+// ---------------------------------------------------------------------------
+// chemistry (isothermal network, FP64)
+// ---------------------------------------------------------------------------
+
+constexpr int kNv = 4 * kMaxBins + 6;
+
+struct ChemRec {
+  double s[kNv];     // state entering the attempt (N[B], f[3B], xHI, xHII, yI, yII, yIII, T)
+  double dt, rem, f;
+  int accepted, grow_is_ratio, clipped, pad;
+};
+
+__device__ __forceinline__ void pack_state(const CellState& c, int B, double* s) {
+  for (int b = 0; b < B; ++b) {
+    s[b] = c.N[b];
+    s[B + 3 * b] = c.f[b][0]; s[B + 3 * b + 1] = c.f[b][1]; s[B + 3 * b + 2] = c.f[b][2];
+  }
+  s[4 * B] = c.xHI; s[4 * B + 1] = c.xHII; s[4 * B + 2] = c.yI; s[4 * B + 3] = c.yII; s[4 * B + 4] = c.yIII;
+  s[4 * B + 5] = c.T;
+}
+
+__device__ __forceinline__ void unpack_state(const double* s, int B, CellState& c) {
+  for (int b = 0; b < B; ++b) {
+    c.N[b] = s[b];
+    c.f[b][0] = s[B + 3 * b]; c.f[b][1] = s[B + 3 * b + 1]; c.f[b][2] = s[B + 3 * b + 2];
+  }
+  c.xHI = s[4 * B]; c.xHII = s[4 * B + 1]; c.yI = s[4 * B + 2]; c.yII = s[4 * B + 3]; c.yIII = s[4 * B + 4];
+  c.T = s[4 * B + 5];
+}
+
+// Reverse of one isothermal attempt (photochem_attempt<false> with mode 1):
+// lt = cotangent of the output state, lf = of the substep measure;
+// accumulates into ls (input state), ldt, lnH.
+__device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const double* s, const double* lt, double lf,
+                            double* ls, double& ldt, double& lnH) {
+  const int B = P.B;
+  const double c = P.c_red, yhe = P.y_he, nHe = yhe * nH;
+  const bool recomb = P.flags & 1, coll = P.flags & 2;
+  const double T = s[4 * B + 5];
+  const Rates rt = RateEval<false>::eval(T);
+  const double aHII = recomb ? rt.aHII : 0.0, aHeII = recomb ? rt.aHeII : 0.0, aHeIII = recomb ? rt.aHeIII : 0.0;
+  const double bHI = coll ? rt.bHI : 0.0, bHeI = coll ? rt.bHeI : 0.0, bHeII = coll ? rt.bHeII : 0.0;
+  const double xHI = s[4 * B], xHII = s[4 * B + 1], yI = s[4 * B + 2], yII = s[4 * B + 3], yIII = s[4 * B + 4];
+  const double ns0 = nH * xHI, ns1 = nHe * yI, ns2 = nHe * yII;
+  double kap[kMaxBins], den[kMaxBins], Nbar[kMaxBins];
+  double Gm0 = 0, Gm1 = 0, Gm2 = 0;
+  for (int b = 0; b < B; ++b) {
+    kap[b] = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
+    den[b] = 1.0 + c * dt * kap[b];
+    Nbar[b] = s[b] / den[b];
+    Gm0 += c * P.sigma[b][0] * Nbar[b];
+    Gm1 += c * P.sigma[b][1] * Nbar[b];
+    Gm2 += c * P.sigma[b][2] * Nbar[b];
+  }
+  const double ne0 = nH * xHII + nHe * (yII + 2.0 * yIII);
+  const double aH = dt * (Gm0 + bHI * ne0), bH = dt * aHII * ne0;
+  const double D1 = 1.0 + aH + bH;
+  const double xHI1 = (xHI * (1.0 + bH) + bH * xHII) / D1;
+  const double xHII1 = (xHII * (1.0 + aH) + aH * xHI) / D1;
+  const double ne1 = nH * xHII1 + nHe * (yII + 2.0 * yIII);
+  const double A = dt * (Gm1 + bHeI * ne1), Bb = dt * aHeII * ne1, Cc = dt * (Gm2 + bHeII * ne1),
+               Dd = dt * aHeIII * ne1;
+  const double opA = 1.0 + A, opD = 1.0 + Dd;
+  const double num = yII + A * yI / opA + Dd * yIII / opD;
+  const double dn = 1.0 + Bb / opA + Cc / opD;
+  const double yII1 = num / dn;
+  const double yI1 = (yI + Bb * yII1) / opA;
+  const double yIII1 = (yIII + Cc * yII1) / opD;
+  const double m0 = nH * xHI1, m1 = nHe * yI1, m2 = nHe * yII1;
+  const double in_x[5] = {xHI, xHII, yI, yII, yIII};
+  const double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
+
+  double lx1[5], lxin[5] = {0, 0, 0, 0, 0};
+  for (int q = 0; q < 5; ++q) lx1[q] = lt[4 * B + q];
+  ls[4 * B + 5] += lt[4 * B + 5];
+  if (lf != 0.0) {
+    const int nk = yhe > 0 ? 5 : 2;
+    double best = -1.0;
+    int kb = -1;
+    for (int k = 0; k < nk; ++k) {
+      const double r = rel_change(in_x[k], out_x[k], P.x_floor);
+      if (r > best) { best = r; kb = k; }
+    }
+    if (best > 0) {
+      const double av = in_x[kb], bo = out_x[kb];
+      const double mm = fabs(av) > P.x_floor ? fabs(av) : P.x_floor;
+      const double sg = bo > av ? 1.0 : -1.0;
+      lx1[kb] += lf * sg / mm;
+      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - av) / (mm * mm)) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
+    }
+  }
+  double lNbar[kMaxBins] = {0, 0, 0}, lm0 = 0, lm1 = 0, lm2 = 0;
+  for (int b = 0; b < B; ++b) {
+    const double sm = P.sigma[b][0] * m0 + P.sigma[b][1] * m1 + P.sigma[b][2] * m2;
+    const double rem = c * dt * Nbar[b] * sm;
+    double N1 = s[b] - rem;
+    const bool clamped = N1 < 0;
+    if (clamped) N1 = 0;
+    const double scale = s[b] > 0 ? N1 / s[b] : 0.0;
+    double lscale = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      ls[B + 3 * b + k] += lt[B + 3 * b + k] * scale;
+      lscale += lt[B + 3 * b + k] * s[B + 3 * b + k];
+    }
+    double lN1 = lt[b];
+    if (s[b] > 0) {
+      lN1 += lscale / s[b];
+      ls[b] -= lscale * N1 / (s[b] * s[b]);
+    }
+    if (!clamped) {
+      ls[b] += lN1;
+      const double lrem = -lN1;
+      lNbar[b] += lrem * c * dt * sm;
+      ldt += lrem * c * Nbar[b] * sm;
+      lm0 += lrem * c * dt * Nbar[b] * P.sigma[b][0];
+      lm1 += lrem * c * dt * Nbar[b] * P.sigma[b][1];
+      lm2 += lrem * c * dt * Nbar[b] * P.sigma[b][2];
+    }
+  }
+  lx1[0] += lm0 * nH;
+  lx1[2] += lm1 * nHe;
+  lx1[3] += lm2 * nHe;
+  lnH += lm0 * xHI1 + lm1 * yhe * yI1 + lm2 * yhe * yII1;
+  double lyII1 = lx1[3];
+  const double lyI1 = lx1[2], lyIII1 = lx1[4];
+  double lCc = 0, lBb = 0, lA = 0, lDd = 0, lopA = 0, lopD = 0;
+  lxin[4] += lyIII1 / opD;
+  lCc += lyIII1 * yII1 / opD;
+  lyII1 += lyIII1 * Cc / opD;
+  lopD -= lyIII1 * yIII1 / opD;
+  lxin[2] += lyI1 / opA;
+  lBb += lyI1 * yII1 / opA;
+  lyII1 += lyI1 * Bb / opA;
+  lopA -= lyI1 * yI1 / opA;
+  const double lnum = lyII1 / dn, ldn = -lyII1 * yII1 / dn;
+  lBb += ldn / opA;
+  lopA -= ldn * Bb / (opA * opA);
+  lCc += ldn / opD;
+  lopD -= ldn * Cc / (opD * opD);
+  lxin[3] += lnum;
+  lA += lnum * yI / opA;
+  lxin[2] += lnum * A / opA;
+  lopA -= lnum * A * yI / (opA * opA);
+  lDd += lnum * yIII / opD;
+  lxin[4] += lnum * Dd / opD;
+  lopD -= lnum * Dd * yIII / (opD * opD);
+  lA += lopA;
+  lDd += lopD;
+  ldt += lA * (Gm1 + bHeI * ne1) + lBb * aHeII * ne1 + lCc * (Gm2 + bHeII * ne1) + lDd * aHeIII * ne1;
+  double lG0 = 0.0;
+  const double lG1 = lA * dt, lG2 = lCc * dt;
+  const double lne1 = lA * dt * bHeI + lBb * dt * aHeII + lCc * dt * bHeII + lDd * dt * aHeIII;
+  const double lxHII1 = lx1[1] + lne1 * nH;
+  const double lxHI1 = lx1[0];
+  lnH += lne1 * (xHII1 + yhe * (yII + 2.0 * yIII));
+  lxin[3] += lne1 * nHe;
+  lxin[4] += lne1 * 2.0 * nHe;
+  const double lD1 = -(lxHI1 * xHI1 + lxHII1 * xHII1) / D1;
+  lxin[1] += lxHII1 * (1.0 + aH) / D1 + lxHI1 * bH / D1;
+  lxin[0] += lxHII1 * aH / D1 + lxHI1 * (1.0 + bH) / D1;
+  const double laH = lxHII1 * (xHII + xHI) / D1 + lD1;
+  const double lbH = lxHI1 * (xHI + xHII) / D1 + lD1;
+  ldt += laH * (Gm0 + bHI * ne0) + lbH * aHII * ne0;
+  lG0 += laH * dt;
+  const double lne0 = laH * dt * bHI + lbH * dt * aHII;
+  lxin[1] += lne0 * nH;
+  lnH += lne0 * (xHII + yhe * (yII + 2.0 * yIII));
+  lxin[3] += lne0 * nHe;
+  lxin[4] += lne0 * 2.0 * nHe;
+  double lns0 = 0, lns1 = 0, lns2 = 0;
+  for (int b = 0; b < B; ++b) {
+    lNbar[b] += c * (P.sigma[b][0] * lG0 + P.sigma[b][1] * lG1 + P.sigma[b][2] * lG2);
+    ls[b] += lNbar[b] / den[b];
+    const double lden = -lNbar[b] * Nbar[b] / den[b];
+    ldt += lden * c * kap[b];
+    const double lkap = lden * c * dt;
+    lns0 += lkap * P.sigma[b][0];
+    lns1 += lkap * P.sigma[b][1];
+    lns2 += lkap * P.sigma[b][2];
+  }
+  lxin[0] += lns0 * nH;
+  lxin[2] += lns1 * nHe;
+  lxin[3] += lns2 * nHe;
+  lnH += lns0 * xHI + lns1 * yhe * yI + lns2 * yhe * yII;
+  for (int q = 0; q < 5; ++q) ls[4 * B + q] += lxin[q];
+}
+
+struct ChemAdjArgs {
+  int C, B;
+  const d4* rad;          // tape: radiation after the source term, before chemistry
+  const double* x5;       // tape: abundances before chemistry
+  const double* T;
+  const double* nH;
+  const double* vol;
+  const int32_t* off;     // C+1 attempt offsets into rec
+  int32_t* count;         // C attempts per cell
+  ChemRec* rec;
+  d4* lam_rad;            // in/out: cotangent of the cell's radiation
+  double* lam_x5;         // in/out
+  double* lam_T;          // in/out
+  double* lam_nH;         // accumulated
+  double* lam_S;          // [B][C] accumulated dL/dS
+  int* status;
+  const int32_t* src_idx; // C: index into src_rate or -1
+  const double* src_rate; // [n][B] photons/s
+  double dt;              // subcycle length
+  double lu3;
+  int do_inject, do_chem;
+  int record;             // 0: count only, 1: write records
+};
+
+__device__ __forceinline__ void load_cell(const ChemAdjArgs& a, int i, CellState& s) {
+  const int B = a.B;
+  for (int b = 0; b < B; ++b) {
+    const d4 v = a.rad[(size_t)i * B + b];
+    s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
+  }
+  const size_t C = a.C;
+  s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+  s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+  if (a.do_inject) {   // the source term, exactly as in k_chem
+    const int si = a.src_idx[i];
+    if (si >= 0) {
+      const double vcm3 = a.vol[i] * a.lu3;
+      for (int b = 0; b < B; ++b) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+    }
+  }
+}
+
+// Re-run the attempts of the forward chemistry_cell<false>; count them, or
+// write their records.
+__global__ void __launch_bounds__(128) k_chem_tape(ChemAdjArgs a, ChemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.C) return;
+  CellState s, t;
+  load_cell(a, i, s);
+  const double nH = a.nH[i];
+  double rem = a.dt, dt = a.dt;
+  int n = 0;
+  ChemRec* out = a.record ? a.rec + a.off[i] : nullptr;
+  while (rem > 0) {
+    if (n >= P.max_sub) { atomicOr(a.status, kStChemSubsteps); break; }
+    if (out) {
+      pack_state(s, a.B, out[n].s);
+      out[n].dt = dt;
+      out[n].rem = rem;
+    }
+    const double f = photochem_attempt<false>(P, nH, dt, s, t);
+    if (out) out[n].f = f;
+    ++n;
+    if (f > P.f_max) {
+      if (out) { out[n - 1].accepted = 0; out[n - 1].grow_is_ratio = 0; out[n - 1].clipped = 0; }
+      dt = dt * (P.f_s / f);
+      continue;
+    }
+    s = t;
+    rem = (dt == rem) ? 0.0 : rem - dt;
+    double grow = (f > 0) ? P.f_s / f : 2.0;
+    const int ratio = f > 0 && grow <= 2.0;
+    if (grow > 2.0) grow = 2.0;
+    const double dtn = dt * grow;
+    const int clipped = dtn > rem;
+    dt = clipped ? rem : dtn;
+    if (out) { out[n - 1].accepted = 1; out[n - 1].grow_is_ratio = ratio; out[n - 1].clipped = clipped; }
+  }
+  if (!a.record) a.count[i] = n;
+}
+
+// Reverse over the recorded attempts of one cell, then the source term.
+__global__ void __launch_bounds__(128) k_chem_adj(ChemAdjArgs a, ChemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.C) return;
+  const int B = a.B, nv = 4 * B + 6;
+  const size_t C = a.C;
+  double lt[kNv], ls[kNv];
+  for (int b = 0; b < B; ++b) {
+    const d4 v = a.lam_rad[(size_t)i * B + b];
+    lt[b] = v.x; lt[B + 3 * b] = v.y; lt[B + 3 * b + 1] = v.z; lt[B + 3 * b + 2] = v.w;
+  }
+  for (int q = 0; q < 5; ++q) lt[4 * B + q] = a.lam_x5[q * C + i];
+  lt[4 * B + 5] = a.lam_T[i];
+  const double nH = a.nH[i];
+  double ldt = 0.0, lrem = 0.0, lnH = 0.0;
+  const ChemRec* rec = a.do_chem ? a.rec + a.off[i] : nullptr;
+  const int n = a.do_chem ? a.off[i + 1] - a.off[i] : 0;
+  for (int k = n - 1; k >= 0; --k) {
+    const ChemRec& r = rec[k];
+    for (int q = 0; q < nv; ++q) ls[q] = 0.0;
+    double cdt = 0.0;
+    if (r.accepted) {
+      const double grow = r.grow_is_ratio ? P.f_s / r.f : 2.0;
+      double ldtg = 0.0;
+      if (r.clipped) lrem += ldt;
+      else ldtg = ldt;
+      double ldtk = ldtg * grow;
+      const double lg = ldtg * r.dt;
+      const double lf = r.grow_is_ratio ? -lg * P.f_s / (r.f * r.f) : 0.0;
+      ldtk -= lrem;
+      attempt_vjp(P, nH, r.dt, r.s, lt, lf, ls, cdt, lnH);
+      for (int q = 0; q < nv; ++q) lt[q] = ls[q];
+      ldt = ldtk + cdt;
+    } else {
+      const double ldtk = ldt * P.f_s / r.f;
+      const double lf = -ldt * r.dt * P.f_s / (r.f * r.f);
+      double zero[kNv];
+      for (int q = 0; q < nv; ++q) zero[q] = 0.0;
+      attempt_vjp(P, nH, r.dt, r.s, zero, lf, ls, cdt, lnH);
+      for (int q = 0; q < nv; ++q) lt[q] += ls[q];
+      ldt = ldtk + cdt;
+    }
+  }
+  for (int b = 0; b < B; ++b) {
+    a.lam_rad[(size_t)i * B + b] = make_d4(lt[b], lt[B + 3 * b], lt[B + 3 * b + 1], lt[B + 3 * b + 2]);
+    // source term N_b += S_b dt / (V lu^3)
+    a.lam_S[(size_t)b * C + i] += lt[b] * a.dt / (a.vol[i] * a.lu3);
+  }
+  for (int q = 0; q < 5; ++q) a.lam_x5[q * C + i] = lt[4 * B + q];
+  a.lam_T[i] = lt[4 * B + 5];
+  a.lam_nH[i] += lnH;
+}
+
+// Exclusive scan of per-cell counts into offsets (one block of 1024 threads,
+// serial chunks per thread): off[0] = 0, off[i+1] = off[i] + count[i].
+__global__ void __launch_bounds__(1024) k_scan_counts(int C, const int32_t* __restrict__ count, int32_t* off,
+                                                      int* overflow) {
+  __shared__ long long part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (C + 1023) / 1024;
+  const int b0 = tid * chunk, b1 = min(C, b0 + chunk);
+  long long s = 0;
+  for (int i = b0; i < b1; ++i) s += count[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    long long v = tid >= d ? part[tid - d] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  long long base = tid > 0 ? part[tid - 1] : 0;
+  for (int i = b0; i < b1; ++i) {
+    off[i] = (int32_t)base;
+    base += count[i];
+  }
+  if (tid == 1023) {
+    off[C] = (int32_t)part[1023];
+    if (part[1023] > 0x7fffffffLL) *overflow = 1;
+  }
+}
+
+}  // namespace m1rt

@@ -10,7 +10,7 @@
 
 #include "../../include/rt.h"
 #include "rt_ctx.h"
-#include "rt_kernels.cuh"
+#include "rt_adjoint.cuh"
 
 using namespace m1rt;
 
@@ -480,6 +480,7 @@ rt_status rt_set_sources(rt_ctx* ctx, int64_t n, const int64_t* cell, const doub
        "sources");
   CK(cudaStreamSynchronize(ctx->stream), "sources");
   ctx->n_src_cells = m;
+  ctx->src_cells.assign(hc.begin(), hc.end());
   return RT_OK;
 }
 
@@ -677,12 +678,247 @@ rt_status rt_launch_count(rt_ctx* ctx, int64_t* out) {
   return RT_OK;
 }
 
+}  // extern "C"
+
+// ---- adjoint ------------------------------------------------------------------
+
+namespace {
+
+template <class T> rt_status aalloc(rt_ctx* ctx, T** p, size_t n, const char* what) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  ctx->adj.allocs.push_back(q);
+  *p = (T*)q;
+  return RT_OK;
+}
+
+void adj_free(rt_ctx* ctx) {
+  for (void* p : ctx->adj.allocs) cudaFree(p);
+  ctx->adj = rt_ctx::Adj();
+}
+
+rt_status adj_prepare(rt_ctx* ctx, int nseg, int k) {
+  auto& A = ctx->adj;
+  if (A.nseg >= nseg && A.k >= k && A.lam_rad) return RT_OK;
+  adj_free(ctx);
+  const size_t C = ctx->C, F = ctx->F, B = ctx->B;
+  rt_status st;
+#define AA(p, n) if ((st = aalloc(ctx, &(p), (n), #p))) return st
+  AA(A.ck_rad, nseg * C * B); AA(A.ck_x5, nseg * 5 * C); AA(A.ck_T, nseg * C);
+  AA(A.tp_rad_chem, k * C * B); AA(A.tp_rad_trans, k * C * B); AA(A.tp_x5, k * 5 * C); AA(A.tp_T, k * C);
+  AA(A.fin_rad, C * B); AA(A.fin_x5, 5 * C); AA(A.fin_T, C);
+  AA(A.lam_rad, C * B); AA(A.lam_part, C * B); AA(A.lam_in, C * B); AA(A.lampre, F * B * 2); AA(A.lamr, C * B * 3);
+  AA(A.lam_x5, 5 * C); AA(A.lam_T, C); AA(A.lam_nH, C); AA(A.lam_S, B * C); AA(A.lim_coef, C * B * 4);
+  AA(A.lim_cell, C * B * 4); AA(A.count, C); AA(A.chem_off, C + 1);
+#undef AA
+  A.nseg = nseg;
+  A.k = k;
+  return RT_OK;
+}
+
+rt_status adj_copy_state(rt_ctx* ctx, d4* rad, double* x5, double* T, bool save) {
+  const size_t C = ctx->C, B = ctx->B;
+  cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (save) {
+    CK(cudaMemcpyAsync(rad, ctx->rad, C * B * sizeof(d4), k, ctx->stream), "checkpoint");
+    CK(cudaMemcpyAsync(x5, ctx->x5, 5 * C * 8, k, ctx->stream), "checkpoint");
+    CK(cudaMemcpyAsync(T, ctx->T, C * 8, k, ctx->stream), "checkpoint");
+  } else {
+    CK(cudaMemcpyAsync(ctx->rad, rad, C * B * sizeof(d4), k, ctx->stream), "restore");
+    CK(cudaMemcpyAsync(ctx->x5, x5, 5 * C * 8, k, ctx->stream), "restore");
+    CK(cudaMemcpyAsync(ctx->T, T, C * 8, k, ctx->stream), "restore");
+  }
+  return RT_OK;
+}
+
+AdjArgs adj_args(rt_ctx* ctx, const d4* rad, double dt) {
+  AdjArgs a;
+  a.C = ctx->C; a.F = ctx->F; a.B = ctx->B; a.off = ctx->off; a.csr = ctx->csr; a.nbr = ctx->nbr; a.lr = ctx->lr;
+  a.nA = ctx->nA64; a.rL = ctx->rL64; a.rR = ctx->rR64; a.w = ctx->w64; a.minv = ctx->minv64; a.vol = ctx->vol;
+  a.rad = rad; a.G = (const double*)ctx->G; a.lam_out = ctx->adj.lam_rad; a.lampre = ctx->adj.lampre;
+  a.lamr = ctx->adj.lamr; a.lim_coef = ctx->adj.lim_coef; a.lim_cell = ctx->adj.lim_cell;
+  a.lam_part = ctx->adj.lam_part; a.lam_in = ctx->adj.lam_in;
+  a.lam = ctx->cfg.c_red * dt / ctx->cfg.unit_length_cm;
+  a.order = ctx->cfg.order; a.limiter = ctx->cfg.limiter; a.lim_eps2 = ctx->cfg.lim_eps * ctx->cfg.lim_eps;
+  return a;
+}
+
+ChemAdjArgs chem_adj_args(rt_ctx* ctx, const d4* rad, const double* x5, const double* T, double dt) {
+  ChemAdjArgs a;
+  a.C = ctx->C; a.B = ctx->B; a.rad = rad; a.x5 = x5; a.T = T; a.nH = ctx->nH; a.vol = ctx->vol;
+  a.off = ctx->adj.chem_off; a.count = ctx->adj.count; a.rec = (ChemRec*)ctx->adj.rec;
+  a.lam_rad = ctx->adj.lam_rad; a.lam_x5 = ctx->adj.lam_x5; a.lam_T = ctx->adj.lam_T; a.lam_nH = ctx->adj.lam_nH;
+  a.lam_S = ctx->adj.lam_S; a.status = ctx->status; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
+  a.dt = dt;
+  const double lu = ctx->cfg.unit_length_cm;
+  a.lu3 = lu * lu * lu;
+  a.do_inject = ctx->n_src_cells > 0;
+  a.do_chem = ctx->cfg.chem_mode > 0;
+  a.record = 0;
+  return a;
+}
+
+// Reverse of one subcycle: transport (from the recorded pre-transport
+// radiation), then chemistry and sources (from the recorded pre-chemistry state).
+rt_status adj_subcycle(rt_ctx* ctx, int slot, double dts) {
+  auto& A = ctx->adj;
+  const size_t C = ctx->C, B = ctx->B;
+  const long long nCB = (long long)C * B, nFB = (long long)ctx->F * B;
+  const d4* rt_rad = A.tp_rad_trans + slot * C * B;
+  // gradients of the recorded state
+  k_grad<double><<<nblk(nCB), kThreads, 0, ctx->stream>>>(
+      Geo<double>{ctx->C, ctx->F, ctx->B, ctx->off, ctx->csr, ctx->nbr, ctx->lr, ctx->nA64, ctx->rL64, ctx->rR64,
+                  ctx->w64, ctx->minv64},
+      rt_rad, (double*)ctx->G, ctx->cfg.order, ctx->cfg.limiter, ctx->cfg.lim_eps * ctx->cfg.lim_eps);
+  AdjArgs a = adj_args(ctx, rt_rad, dts);
+  k_adj_face<<<nblk(nFB), kThreads, 0, ctx->stream>>>(a);
+  k_adj_cellgrad<<<nblk(nCB), kThreads, 0, ctx->stream>>>(a);
+  k_adj_cellsum<<<nblk(nCB), kThreads, 0, ctx->stream>>>(a);
+  std::swap(A.lam_rad, A.lam_in);
+  rt_status st = launched(ctx, "adjoint transport");
+  if (st) return st;
+  // chemistry tape: count, offsets, records, reverse
+  const d4* pc_rad = A.tp_rad_chem + slot * C * B;
+  const double* pc_x5 = A.tp_x5 + slot * 5 * C;
+  const double* pc_T = A.tp_T + slot * C;
+  ChemParams P = chem_params(ctx);
+  ChemAdjArgs ca = chem_adj_args(ctx, pc_rad, pc_x5, pc_T, dts);
+  const int t = 128;
+  if (ca.do_chem) {
+    k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
+    CK(cudaMemsetAsync(ctx->stage, 0, sizeof(int), ctx->stream), "scan");
+    k_scan_counts<<<1, 1024, 0, ctx->stream>>>((int)C, A.count, A.chem_off, (int*)ctx->stage);
+    int32_t total = 0, ovf = 0;
+    CK(cudaMemcpyAsync(&total, A.chem_off + C, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
+    CK(cudaMemcpyAsync(&ovf, ctx->stage, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
+    CK(cudaStreamSynchronize(ctx->stream), "scan");
+    if (ovf) return fail(ctx, RT_OOM, "adjoint: chemistry tape exceeds 2^31 attempts");
+    if ((size_t)total > A.rec_cap) {
+      if (A.rec) {
+        cudaFree(A.rec);
+        A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.rec));
+      }
+      size_t cap = std::max<size_t>((size_t)total + total / 4, 1024);
+      ChemRec* r = nullptr;
+      if ((st = aalloc(ctx, &r, cap, "chemistry tape"))) return st;
+      A.rec = r;
+      A.rec_cap = cap;
+    }
+    ca.rec = (ChemRec*)A.rec;
+    ca.record = 1;
+    k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
+  }
+  k_chem_adj<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
+  return launched(ctx, "adjoint chemistry");
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, const double* lam_N,
+                     const double* lam_F, const double* lam_x5, const double* lam_T, double* dL_dQ,
+                     double* dL_dnH, double* lam0_N, double* lam0_F, double* lam0_x5, double* lam0_T) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  if (mixed(ctx) || ctx->cfg.chem_mode == 2)
+    return fail(ctx, RT_INVALID_ARG, "rt_adjoint supports FP64 precision with chem_mode 0 or 1");
+  if (n_sub < 1 || !(dt > 0) || !std::isfinite(dt) || checkpoint_every < 1)
+    return fail(ctx, RT_INVALID_ARG, "need dt > 0, n_sub >= 1, checkpoint_every >= 1");
+  const double dts = dt / n_sub;
+  const double dmax = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
+  if (dts > dmax * (1.0 + 1e-12)) return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
+  const int k = std::min(checkpoint_every, n_sub);
+  const int nseg = (n_sub + k - 1) / k;
+  if ((st = adj_prepare(ctx, nseg, k))) return st;
+  auto& A = ctx->adj;
+  const size_t C = ctx->C, B = ctx->B;
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  // forward with checkpoints
+  for (int s = 0; s < n_sub; ++s) {
+    if (s % k == 0 && (st = adj_copy_state(ctx, A.ck_rad + (s / k) * C * B, A.ck_x5 + (s / k) * 5 * C,
+                                           A.ck_T + (s / k) * C, true)))
+      return st;
+    launch_chem(ctx, dts);
+    launch_grad_any(ctx);
+    launch_flux_any(ctx);
+    launch_gather(ctx, dts);
+  }
+  if ((st = launched(ctx, "adjoint forward"))) return st;
+  if ((st = adj_copy_state(ctx, A.fin_rad, A.fin_x5, A.fin_T, true))) return st;
+  // cotangents of the final state
+  double* sN = ctx->stage;
+  double* sF = ctx->stage + B * C;
+  CK(cudaMemsetAsync(ctx->stage, 0, 4 * B * C * 8, ctx->stream), "adjoint");
+  if (lam_N && (st = copy_in(ctx, sN, lam_N, B * C * 8))) return st;
+  if (lam_F && (st = copy_in(ctx, sF, lam_F, 3 * B * C * 8))) return st;
+  // dL/d(F/c) = c dL/dF
+  k_pack_rad<<<nblk((long long)B * C), kThreads, 0, ctx->stream>>>((int)C, (int)B, ctx->cfg.c_red, sN, sF, A.lam_rad);
+  CK(cudaMemsetAsync(A.lam_x5, 0, 5 * C * 8, ctx->stream), "adjoint");
+  CK(cudaMemsetAsync(A.lam_T, 0, C * 8, ctx->stream), "adjoint");
+  if (lam_x5 && (st = copy_in(ctx, A.lam_x5, lam_x5, 5 * C * 8))) return st;
+  if (lam_T && (st = copy_in(ctx, A.lam_T, lam_T, C * 8))) return st;
+  CK(cudaMemsetAsync(A.lam_nH, 0, C * 8, ctx->stream), "adjoint");
+  CK(cudaMemsetAsync(A.lam_S, 0, B * C * 8, ctx->stream), "adjoint");
+  // reverse, segment by segment
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int s0 = seg * k, s1 = std::min(n_sub, s0 + k);
+    if ((st = adj_copy_state(ctx, A.ck_rad + seg * C * B, A.ck_x5 + seg * 5 * C, A.ck_T + seg * C, false)))
+      return st;
+    for (int s = s0; s < s1; ++s) {
+      const int slot = s - s0;
+      CK(cudaMemcpyAsync(A.tp_rad_chem + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
+                         ctx->stream), "tape");
+      CK(cudaMemcpyAsync(A.tp_x5 + slot * 5 * C, ctx->x5, 5 * C * 8, cudaMemcpyDeviceToDevice, ctx->stream), "tape");
+      CK(cudaMemcpyAsync(A.tp_T + slot * C, ctx->T, C * 8, cudaMemcpyDeviceToDevice, ctx->stream), "tape");
+      launch_chem(ctx, dts);
+      CK(cudaMemcpyAsync(A.tp_rad_trans + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
+                         ctx->stream), "tape");
+      launch_grad_any(ctx);
+      launch_flux_any(ctx);
+      launch_gather(ctx, dts);
+    }
+    for (int s = s1 - 1; s >= s0; --s)
+      if ((st = adj_subcycle(ctx, s - s0, dts))) return st;
+  }
+  if ((st = adj_copy_state(ctx, A.fin_rad, A.fin_x5, A.fin_T, false))) return st;
+  // outputs
+  if (dL_dQ && !ctx->src_cells.empty()) {
+    std::vector<double> hS(B * C);
+    CK(cudaMemcpyAsync(hS.data(), A.lam_S, B * C * 8, cudaMemcpyDeviceToHost, ctx->stream), "adjoint");
+    CK(cudaStreamSynchronize(ctx->stream), "adjoint");
+    std::vector<double> q(ctx->src_cells.size() * B);
+    for (size_t s = 0; s < ctx->src_cells.size(); ++s)
+      for (size_t b = 0; b < B; ++b) q[s * B + b] = hS[b * C + ctx->src_cells[s]];
+    if (is_device_ptr(dL_dQ)) CK(cudaMemcpy(dL_dQ, q.data(), q.size() * 8, cudaMemcpyHostToDevice), "dL_dQ");
+    else std::memcpy(dL_dQ, q.data(), q.size() * 8);
+  }
+  if (dL_dnH && (st = copy_out(ctx, dL_dnH, A.lam_nH, C * 8))) return st;
+  if (lam0_N || lam0_F) {
+    k_unpack_rad<<<nblk((long long)B * C), kThreads, 0, ctx->stream>>>((int)C, (int)B, 1.0 / ctx->cfg.c_red,
+                                                                        A.lam_rad, sN, sF);
+    if (lam0_N && (st = copy_out(ctx, lam0_N, sN, B * C * 8))) return st;
+    if (lam0_F && (st = copy_out(ctx, lam0_F, sF, 3 * B * C * 8))) return st;
+  }
+  if (lam0_x5 && (st = copy_out(ctx, lam0_x5, A.lam_x5, 5 * C * 8))) return st;
+  if (lam0_T && (st = copy_out(ctx, lam0_T, A.lam_T, C * 8))) return st;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
+  CK(cudaStreamSynchronize(ctx->stream), "adjoint");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  if (h & kStChemSubsteps) return fail(ctx, RT_CHEM_SUBSTEPS, "a cell reached max_substeps");
+  if (h & kStNonFinite) return fail(ctx, RT_NONFINITE, "non-finite photon density");
+  return launched(ctx, "adjoint");
+}
+
 const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 void rt_destroy(rt_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  adj_free(ctx);
   free_all(ctx);
   delete ctx;
 }

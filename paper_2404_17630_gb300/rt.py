@@ -122,6 +122,7 @@ def load():
                 "rt_profile_enable": [vp, i32],
                 "rt_profile_read": [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
                 "rt_launch_count": [vp, ctypes.POINTER(i64)],
+                "rt_adjoint": [vp, dbl, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -308,6 +309,18 @@ def rt_noalloc_last_error() -> str:
     return (load().rt_noalloc_last_error() or b"").decode()
 
 
+def rt_adjoint(ctx, dt, n_sub, checkpoint_every, lam_N=None, lam_F=None, lam_x5=None, lam_T=None, dL_dQ=None,
+               dL_dnH=None, lam0_N=None, lam0_F=None, lam0_x5=None, lam0_T=None):
+    """Reverse mode of rt_step (see include/rt.h).  Inputs may be None;
+    outputs are writable float64 arrays/tensors or None."""
+    lib, keep = load(), []
+    o = lambda a: None if a is None else _out_ptr(a)
+    return _check(lib, ctx, lib.rt_adjoint(ctx, float(dt), int(n_sub), int(checkpoint_every),
+                                           _ptr(lam_N, np.float64, keep), _ptr(lam_F, np.float64, keep),
+                                           _ptr(lam_x5, np.float64, keep), _ptr(lam_T, np.float64, keep),
+                                           o(dL_dQ), o(dL_dnH), o(lam0_N), o(lam0_F), o(lam0_x5), o(lam0_T)))
+
+
 RT_KERNEL_NAMES = ("k_chem", "k_grad", "k_flux", "k_gather")
 
 
@@ -406,6 +419,17 @@ class RT:
     def face_fluxes(self, G=None):
         out = np.empty((self.F, self.B, 4))
         rt_stage_fluxes(self.ctx, G, out)
+        return out
+
+    def adjoint(self, dt, n_sub, checkpoint_every, lam_N=None, lam_F=None, lam_x5=None, lam_T=None, n_src=0):
+        """Reverse mode of step(dt, n_sub) from the current state (which it
+        advances).  Returns numpy dL/dQ [n_src, B], dL/dn_H [C] and the
+        cotangents of the initial fields."""
+        B, C = self.B, self.C
+        out = dict(dQ=np.empty((n_src, B)), dnH=np.empty(C), N=np.empty((B, C)), F=np.empty((B, 3, C)),
+                   x5=np.empty((5, C)), T=np.empty(C))
+        rt_adjoint(self.ctx, dt, n_sub, checkpoint_every, lam_N, lam_F, lam_x5, lam_T,
+                   out["dQ"] if n_src else None, out["dnH"], out["N"], out["F"], out["x5"], out["T"])
         return out
 
     def transport(self, dt):

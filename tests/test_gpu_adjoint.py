@@ -1,0 +1,119 @@
+"""GPU reverse mode (rt_adjoint) against the oracle's reverse mode and
+against central finite differences of the GPU forward."""
+import numpy as np
+import pytest
+
+from tests._cases import make_oracle, voronoi_case
+from tests.test_gpu_parity import make_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n=8, chem_mode=1, n_src=2):
+    mesh, cfg, st = voronoi_case(n=n, n_bins=3, chem_mode=chem_mode, n_src=n_src)
+    st["N"] *= 0.1
+    st["fr"] *= 0.1
+    c = mesh.centroids()
+    R = np.all(c < 0.5 * mesh.box, axis=1)
+    return mesh, cfg, st, R
+
+
+def _loss_cot(mesh, st, R):
+    m = st["nH"] * mesh.volume
+    lx = np.zeros((5, mesh.n_cells))
+    lx[1][R] = m[R] / m[R].sum()
+    return lx
+
+
+def rel(a, b):
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+@pytest.mark.parametrize("chem_mode,k", [(1, 4), (1, 2), (0, 3)])
+def test_adjoint_matches_oracle(chem_mode, k):
+    mesh, cfg, st, R = _setup(chem_mode=chem_mode)
+    n_sub = 4
+    lx = _loss_cot(mesh, st, R)
+    lN = np.zeros((3, mesh.n_cells))
+    lN[:, R] = mesh.volume[R]
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    ref = o.adjoint(dt, n_sub, lam_N=lN, lam_x5=lx)
+    assert ref["status"] == 0
+    rt = make_gpu(mesh, cfg, st)
+    got = rt.adjoint(dt, n_sub, k, lam_N=lN, lam_x5=lx, n_src=len(st["cells"]))
+    gQ_ref = ref["g_src"][:, st["cells"]].T
+    assert rel(got["dQ"], gQ_ref) < 1e-9
+    assert rel(got["dnH"], ref["g_nH"]) < 1e-9
+    assert rel(got["N"], ref["lam0"]["N"]) < 1e-9
+    # dL/dF = dL/d(F/c) / c
+    assert rel(got["F"], ref["lam0"]["fr"] / cfg["c_red"]) < 1e-9
+    assert rel(got["x5"], ref["lam0"]["x5"]) < 1e-9
+    # the forward part left the same final state as a plain step
+    N1, _ = o.radiation()
+    assert rel(rt.radiation()[0], N1) < 1e-12
+
+
+def test_adjoint_checkpointing_is_exact():
+    mesh, cfg, st, R = _setup()
+    lx = _loss_cot(mesh, st, R)
+    outs = []
+    for k in (1, 3, 6):
+        rt = make_gpu(mesh, cfg, st)
+        dt = rt.max_dt() * 6
+        outs.append(rt.adjoint(dt, 6, k, lam_x5=lx, n_src=2))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o["dQ"], outs[0]["dQ"])
+        np.testing.assert_array_equal(o["dnH"], outs[0]["dnH"])
+
+
+def test_autograd_function_vs_fd():
+    """torch.autograd through RTStepFunction: dL/dQ and dL/dn_H of the
+    mass-weighted ionised fraction in a region, against central FD
+    (h = 1e-4 relative) of the GPU forward."""
+    import torch
+    from paper_2404_17630_gb300 import rt_step_autograd
+    mesh, cfg, st, R = _setup()
+    dev = torch.device("cuda", 0)
+    rt = make_gpu(mesh, cfg, st)
+    n_sub = 5
+    dt = rt.max_dt() * n_sub
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    Rm = t(R.astype(np.float64))
+    V = t(mesh.volume)
+    Q = t(st["Q"]).requires_grad_(True)
+    nH = t(st["nH"]).requires_grad_(True)
+    args = (t(st["N"]), t(st["fr"] * cfg["c_red"]), t(st["x5"]), t(st["T"]))
+
+    def loss(Qv, nHv):
+        N, F, x5, T = rt_step_autograd(rt, st["cells"], Qv, nHv, *args, dt, n_sub, 2)
+        m = nHv * V * Rm
+        return (m * x5[1]).sum() / m.sum()
+
+    L = loss(Q, nH)
+    L.backward()
+    gQ, gn = Q.grad.cpu().numpy(), nH.grad.cpu().numpy()
+
+    def Lval(Qv, nHv):
+        with torch.no_grad():
+            return float(loss(Qv, nHv))
+
+    for kk in range(2):
+        for b in range(3):
+            vals = []
+            for sg in (1, -1):
+                Q2 = Q.detach().clone()
+                Q2[kk, b] *= (1 + sg * 1e-4)
+                vals.append(Lval(Q2, nH.detach()))
+            fd = (vals[0] - vals[1]) / (2e-4 * float(Q.detach()[kk, b]))
+            assert abs(gQ[kk, b] - fd) <= 1e-5 * abs(fd) + 1e-8 * np.abs(gQ).max(), (kk, b, gQ[kk, b], fd)
+    rng = np.random.default_rng(2)
+    for i in list(rng.choice(np.where(R)[0], 3, replace=False)) + list(st["cells"]):
+        vals = []
+        for sg in (1, -1):
+            n2 = nH.detach().clone()
+            n2[i] *= (1 + sg * 1e-4)
+            vals.append(Lval(Q.detach(), n2))
+        fd = (vals[0] - vals[1]) / (2e-4 * float(nH.detach()[i]))
+        assert abs(gn[i] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gn).max()), (i, gn[i], fd)
