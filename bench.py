@@ -38,6 +38,55 @@ L_BOX = 10.0
 L2_BYTES = 129e6
 
 
+def thesan_like(n=128, seed=4, n_peaks=4096):
+    """THESAN-like box: Voronoi mesh of an n^3 jittered lattice in a periodic
+    box of 3.58 Mpc (physical, 23.3 cMpc at z = 5.5), n_H = exp(GRF) with
+    P(k) ~ k^-2, sigma 1.5, mean 2e-4 cm^-3 (128^3 FFT grid, nearest node),
+    sources at the n_peaks highest density maxima with Q = 1e49 rho/rho_min
+    clipped to 1e52 photons/s, c_red = 0.2 c."""
+    import synth
+    L = 3580.0  # kpc
+    mesh = synth.voronoi_mesh(n, L, 0.3, seed=seed)
+    C = mesh.n_cells
+    nH, rho = synth.grf_density(mesh.gen, L, 128, 1.5, 2e-4, seed + 1)
+    peaks = synth.density_peaks(rho, n_peaks)
+    pos = (peaks + 0.5) * (L / 128)
+    cells = synth.locate_cells(mesh, pos).astype(np.int64)
+    rp = rho[tuple(peaks.T)]
+    Qtot = np.minimum(1e49 * rp / rp.min(), 1e52)
+    Q = np.outer(Qtot, synth.SPECTRAL_SPLIT_E4)
+    x5 = np.zeros((5, C)); x5[0] = 1.0; x5[2] = 1.0
+    cfg = dict(n_bins=3, c_red=0.2 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L, cfl=0.3, chem_mode=2,
+               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
+               max_substeps=10000, y_he=synth.helium_ratio(0.24), sigma=synth.GREY_SIGMA, eps=synth.GREY_EPS)
+    state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q)
+    return mesh, cfg, state
+
+
+def differentiable(n=64, seed=7, n_src=8):
+    """Differentiable workload: n^3 jittered-lattice Voronoi mesh (box 10 kpc),
+    lognormal n_H (sigma_ln 1), 8 sources with Q ~ U(1e49, 1e50) photons/s,
+    isothermal H+He network, FP64; loss = mass-weighted ionised fraction of
+    the cells whose generators lie in a 16^3-lattice sub-cube."""
+    import synth
+    mesh = synth.voronoi_mesh(n, L_BOX, 0.3, seed=seed)
+    C = mesh.n_cells
+    nH = synth.lognormal_density(C, 1e-3, 1.0, seed + 1)
+    srng = np.random.default_rng(seed + 2)
+    cells = srng.choice(C, size=n_src, replace=False).astype(np.int64)
+    Q = np.outer(srng.uniform(1e49, 1e50, n_src), synth.SPECTRAL_SPLIT_E4)
+    x5 = np.zeros((5, C)); x5[0] = 1.0; x5[2] = 1.0
+    cfg = dict(n_bins=3, c_red=0.01 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L_BOX, cfl=0.3, chem_mode=1,
+               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
+               max_substeps=10000, y_he=synth.helium_ratio(0.24), sigma=synth.GREY_SIGMA, eps=synth.GREY_EPS)
+    idx = np.arange(C)
+    ijk = np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1)
+    region = np.all(ijk < 16, axis=1)
+    state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q,
+                 region=region)
+    return mesh, cfg, state
+
+
 def workload(n=LATTICE, seed=1, n_src=16):
     """Seeded inputs of the 2e5-cell Voronoi workload (see module doc)."""
     import synth
@@ -319,6 +368,91 @@ def cpu_baseline(mesh, cfg, state, budget_s=12.0):
                       f"({sec:.1f} s, FP64, single thread)"}
 
 
+def measure_large(steps, warmup, dev):
+    """Mixed precision on the 2.1M-cell THESAN-like box, 100 subcycles/step."""
+    t0 = time.perf_counter()
+    mesh, cfg, state = thesan_like()
+    build_s = time.perf_counter() - t0
+    n_sub = 100
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision="mixed", gather_sum=1, **cfg), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dt = rt.max_dt() * n_sub
+    for _ in range(warmup):
+        rt.step(dt, n_sub)
+    rt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(steps):
+        rt.step(dt, n_sub)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, True)
+    rt.step(dt, n_sub)
+    prof = rtb.rt_profile_read(rt.ctx, reset=True)
+    rt.sync()
+    C, F, _ = rt.mesh_info()
+    res = dict(ms=ms, C=C, F=F, prof=prof)
+    peaks, kind = measured_peaks()
+    rf, kern = roofline(res, "mixed", peaks, kind)
+    f = rt.fields()
+    return {"workload": f"THESAN-like voronoi 128^3 ({C} cells, {F} faces), GRF n_H, 4096 peak sources, "
+                        f"c_red 0.2c, {n_sub} subcycles/step, mixed", "value": C * n_sub * steps / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "roofline": rf,
+            "kernels": kern, "mesh_build_s": round(build_s, 1), "x_HII_mean": float(f["x5"][1].mean())}
+
+
+def measure_adjoint(dev, n=64, n_sub=50, k=10):
+    """FP64 forward and reverse mode on the 262k-cell differentiable workload."""
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    mesh, cfg, state = differentiable(n)
+    C = mesh.n_cells
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision="fp64", **cfg), mesh, stream=stream)
+
+    def reset():
+        rt.set_gas(state["nH"], state["x5"], state["T"])
+        rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+        rt.set_sources(state["cells"], state["Q"])
+
+    reset()
+    dt = rt.max_dt() * n_sub
+    R = state["region"]
+    m = state["nH"] * mesh.volume
+    lx = np.zeros((5, C))
+    lx[1][R] = m[R] / m[R].sum()
+    lx_d = torch.as_tensor(lx, device=dev)
+    # forward
+    rt.step(dt, n_sub); rt.sync(); reset()
+    t0 = time.perf_counter()
+    rt.step(dt, n_sub)
+    rt.sync()
+    fwd = time.perf_counter() - t0
+    reset()
+    out = rt.adjoint(dt, n_sub, k, lam_x5=lx_d, n_src=len(state["cells"]))  # warm-up (allocations)
+    reset()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    out = rt.adjoint(dt, n_sub, k, lam_x5=lx_d, n_src=len(state["cells"]))
+    torch.cuda.synchronize(dev)
+    adj = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info(dev)
+    return {"workload": f"voronoi {n}^3 ({C} cells), {n_sub} FP64 subcycles, isothermal H+He, 8 sources, "
+                        f"checkpoint every {k}", "forward_value": C * n_sub / fwd, "adjoint_value": C * n_sub / adj,
+            "unit": UNIT, "forward_s": round(fwd, 4), "adjoint_s": round(adj, 4),
+            "adjoint_over_forward": round(adj / fwd, 2), "dL_dQ": out["dQ"].sum(axis=1).tolist(),
+            "device_mem_used_GB": round((total - free) / 1e9, 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,6 +462,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2.1M-cell THESAN-like run")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode run")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -366,6 +502,8 @@ def main():
         fp64sum = {"value": world * r["C"] * N_SUB * n64s / (r["ms"] / 1e3), "ms_per_step": r["ms"] / n64s,
                    "note": "mixed precision with each FP32 face flux widened and summed in FP64 (gather_sum=0)"}
     e2e = None if args.no_e2e else e2e_measure("mixed", mesh, cfg, state, max(2, args.steps // 2), args.warmup, dev)
+    large = None if args.no_large else measure_large(3, 1, dev)
+    adjoint = None if args.no_adjoint else measure_adjoint(dev)
     if rank != 0:
         return
     C, F = res["C"], res["F"]
@@ -388,6 +526,7 @@ def main():
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "mixed_fp64_sums": fp64sum,
         "e2e": e2e, "cpu_baseline": cpu,
+        "thesan_like_2M": large, "adjoint": adjoint,
         "gpu_launches": res["launches"], "clocks": cl,
     }
     print(json.dumps(out))

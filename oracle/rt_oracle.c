@@ -738,7 +738,7 @@ static void m1_pressure_normal_vjp(double N, const double fr[3], const double n[
     double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f / s) / (den * den);
     double lf = clamped ? 0.0 : lchi * dchi;
     double lfl = lf / N;
-    *lamN -= lf * fl / (N * N);
+    *lamN -= lf * (fl / N) / N;
     double luu = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
     for (int m = 0; m < 3; ++m) lamfr[m] += (lu[m] - luu * u[m]) / fl + lfl * u[m];
   } else {
@@ -766,7 +766,7 @@ static void face_state_vjp(const orc_t *o, int64_t c, int64_t f, int b, const do
     /* out_k = v0 v_k / fl */
     double lv = lamv[1] * v[1] + lamv[2] * v[2] + lamv[3] * v[3];
     lpre[0] = lamv[0] + lv / fl;
-    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lamv[k] - lv * v[k] / (fl * fl));
+    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lamv[k] - (lv / fl) * (v[k] / fl));
   }
   if (clampN) lpre[0] = 0.0;
   for (int q = 0; q < 4; ++q) {
@@ -969,7 +969,7 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
       double mm = fabs(a) > cf->x_floor ? fabs(a) : cf->x_floor;
       double sg = bo > a ? 1.0 : -1.0;
       lx1[kb] += lf * sg / mm;
-      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - a) / (mm * mm)) * (fabs(a) > cf->x_floor ? (a > 0 ? 1.0 : -1.0) : 0.0);
+      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - a) / mm / mm) * (fabs(a) > cf->x_floor ? (a > 0 ? 1.0 : -1.0) : 0.0);
     }
   }
   /* photon removal and flux scaling */
@@ -989,7 +989,7 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
     double lN1 = lt[b];
     if (s[b] > 0) {
       lN1 += lscale / s[b];
-      ls[b] -= lscale * N1 / (s[b] * s[b]);
+      ls[b] -= lscale * (N1 / s[b]) / s[b];
     }
     if (!clamped) {
       ls[b] += lN1;

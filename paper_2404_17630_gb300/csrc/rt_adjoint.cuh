@@ -51,7 +51,7 @@ __device__ __forceinline__ void m1_normal_vjp(const double v[4], double n0, doub
     const double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f / s) / (den * den);
     const double lff = clamped ? 0.0 : lchi * dchi;
     const double lfl = lff / v[0];
-    lN -= lff * fl / (v[0] * v[0]);
+    lN -= lff * (fl / v[0]) / v[0];
     const double luu = lu0 * u0 + lu1 * u1 + lu2 * u2;
     lf[0] += (lu0 - luu * u0) / fl + lfl * u0;
     lf[1] += (lu1 - luu * u1) / fl + lfl * u1;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void face_post_vjp(const double pre[4], const double 
     const double lvf = lv[1] * pre[1] + lv[2] * pre[2] + lv[3] * pre[3];
     lpre[0] = lv[0] + lvf / fl;
 #pragma unroll
-    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lv[k] - lvf * pre[k] / (fl * fl));
+    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lv[k] - (lvf / fl) * (pre[k] / fl));
   }
   if (clampN) lpre[0] = 0.0;
 }
@@ -385,7 +385,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
       const double mm = fabs(av) > P.x_floor ? fabs(av) : P.x_floor;
       const double sg = bo > av ? 1.0 : -1.0;
       lx1[kb] += lf * sg / mm;
-      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - av) / (mm * mm)) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
+      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - av) / mm / mm) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
     }
   }
   double lNbar[kMaxBins] = {0, 0, 0}, lm0 = 0, lm1 = 0, lm2 = 0;
@@ -404,7 +404,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
     double lN1 = lt[b];
     if (s[b] > 0) {
       lN1 += lscale / s[b];
-      ls[b] -= lscale * N1 / (s[b] * s[b]);
+      ls[b] -= lscale * (N1 / s[b]) / s[b];
     }
     if (!clamped) {
       ls[b] += lN1;

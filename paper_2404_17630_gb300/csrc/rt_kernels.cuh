@@ -180,12 +180,7 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     mx[q] = mn[q] = comp<R>(pi, q);
   }
   const int k0 = g.off[i], k1 = g.off[i + 1];
-#pragma unroll 4
-  for (int k = k0; k < k1; ++k) {
-    const int e = __ldg(g.csr + k), f = e >> 1;
-    const int j = __ldg(g.nbr + k);
-    const R4<R> pj = ld4<R>(rad + (size_t)j * B + b);
-    const R4<R> w = ld4<R>(g.w + f);
+  auto acc_face = [&](int e, const R4<R>& pj, const R4<R>& w) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       R vj = comp<R>(pj, q), vi = comp<R>(pi, q);
@@ -196,6 +191,23 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
       mx[q] = vj > mx[q] ? vj : mx[q];
       mn[q] = vj < mn[q] ? vj : mn[q];
     }
+  };
+  int k = k0;
+  // batches of four faces, loads first, accumulation in CSR order
+  for (; k + 4 <= k1; k += 4) {
+    int e[4], j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { e[u] = __ldg(g.csr + k + u); j[u] = __ldg(g.nbr + k + u); }
+    R4<R> pj[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { pj[u] = ld4<R>(rad + (size_t)j[u] * B + b); w[u] = ld4<R>(g.w + (e[u] >> 1)); }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc_face(e[u], pj[u], w[u]);
+  }
+  for (; k < k1; ++k) {
+    const int e = __ldg(g.csr + k);
+    const int j = __ldg(g.nbr + k);
+    acc_face(e, ld4<R>(rad + (size_t)j * B + b), ld4<R>(g.w + (e >> 1)));
   }
   const R* m = g.minv + 6 * (size_t)i;
   const R m00 = m[0], m01 = m[1], m02 = m[2], m11 = m[3], m12 = m[4], m22 = m[5];
@@ -278,15 +290,44 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
     v[q] = comp<R>(p, q) + d;
   }
   if (v[0] < R(0)) v[0] = R(0);
-  R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-  if (fl > v[0]) {
-    R s = fl > R(0) ? v[0] / fl : R(0);
-    v[1] *= s; v[2] *= s; v[3] *= s;
+  if constexpr (sizeof(R) == 4) {
+    // FP32 sweep: |F| <= c N tested on squares, scale by rsqrt
+    const float fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    if (fl2 > v[0] * v[0]) {
+      const float s = v[0] * rsqrtf(fl2);
+      v[1] *= s; v[2] *= s; v[3] *= s;
+    }
+  } else {
+    R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    if (fl > v[0]) {
+      R s = fl > R(0) ? v[0] / fl : R(0);
+      v[1] *= s; v[2] *= s; v[3] *= s;
+    }
   }
 }
 
 // N D n with the Levermore M1 Eddington tensor.
 template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0, R n1, R n2, R P[3]) {
+  if constexpr (sizeof(R) == 4) {
+    // FP32 sweep: one rsqrt for |F|, fast reciprocals
+    const float fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    if (v[0] > 0.0f && fl2 > 0.0f) {
+      const float ifl = rsqrtf(fl2);
+      float f = fl2 * ifl * __frcp_rn(v[0]);
+      f = f > 1.0f ? 1.0f : f;
+      const float chi = __fdividef(3.0f + 4.0f * f * f, 5.0f + 2.0f * sqrtf(4.0f - 3.0f * f * f));
+      const float u0 = v[1] * ifl, u1 = v[2] * ifl, u2 = v[3] * ifl;
+      const float un = u0 * n0 + u1 * n1 + u2 * n2;
+      const float a = 0.5f * (1.0f - chi), bb = 0.5f * (3.0f * chi - 1.0f) * un;
+      P[0] = v[0] * (a * n0 + bb * u0);
+      P[1] = v[0] * (a * n1 + bb * u1);
+      P[2] = v[0] * (a * n2 + bb * u2);
+    } else {
+      const float t = v[0] * (1.0f / 3.0f);
+      P[0] = t * n0; P[1] = t * n1; P[2] = t * n2;
+    }
+    return;
+  }
   R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
   if (v[0] > R(0) && fl > R(0)) {
     R f = fl / v[0];
@@ -383,11 +424,8 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   double acc[4];
   if (Comp) {
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-      const int e = __ldg(a.csr + k), f = e >> 1;
+    auto add = [&](int e, const R4<R>& v) {
       const float sg = (e & 1) ? -1.0f : 1.0f;
-      const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
       const float tv[4] = {sg * (float)v.x, sg * (float)v.y, sg * (float)v.z, sg * (float)v.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -396,20 +434,43 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
         hi[q] = sum;
         lo[q] += err;
       }
+    };
+    int k = k0;
+    // batches of four faces: all index and flux loads issued before use;
+    // the terms are still added in CSR order
+    for (; k + 4 <= k1; k += 4) {
+      const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
+                e3 = __ldg(a.csr + k + 3);
+      const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
+                  v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
+      add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
+    }
+    for (; k < k1; ++k) {
+      const int e = __ldg(a.csr + k);
+      add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = (double)hi[q] + (double)lo[q];
   } else {
     acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-      const int e = __ldg(a.csr + k), f = e >> 1;
-      const R4<R> v = ld4<R>(flux + (size_t)f * B + b);
+    auto add = [&](int e, const R4<R>& v) {
       if (e & 1) {
         acc[0] -= (double)v.x; acc[1] -= (double)v.y; acc[2] -= (double)v.z; acc[3] -= (double)v.w;
       } else {
         acc[0] += (double)v.x; acc[1] += (double)v.y; acc[2] += (double)v.z; acc[3] += (double)v.w;
       }
+    };
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
+                e3 = __ldg(a.csr + k + 3);
+      const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
+                  v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
+      add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
+    }
+    for (; k < k1; ++k) {
+      const int e = __ldg(a.csr + k);
+      add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
     }
   }
   const double kfac = a.lam / a.vol[i];

@@ -55,6 +55,18 @@ def test_adjoint_matches_oracle(chem_mode, k):
     assert rel(rt.radiation()[0], N1) < 1e-12
 
 
+def test_adjoint_finite_for_tiny_radiation():
+    mesh, cfg, st, R = _setup(n=6)
+    st["N"] *= 1e-160
+    st["fr"] *= 1e-160
+    rt = make_gpu(mesh, cfg, st)
+    lx = np.zeros((5, mesh.n_cells))
+    lx[1] = 1.0
+    out = rt.adjoint(rt.max_dt() * 3, 3, 2, lam_x5=lx, n_src=2)
+    for k in ("dQ", "dnH", "N", "F", "x5"):
+        assert np.isfinite(out[k]).all(), k
+
+
 def test_adjoint_checkpointing_is_exact():
     mesh, cfg, st, R = _setup()
     lx = _loss_cot(mesh, st, R)

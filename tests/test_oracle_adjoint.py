@@ -139,3 +139,18 @@ def test_adjoint_transport_only_vs_fd():
             fd = (vals[0] - vals[1]) / (2 * h)
             g = lam0[arr][idx]
             assert abs(g - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(lam0["N"]).max()), (arr, idx, g, fd)
+
+
+def test_adjoint_finite_for_tiny_radiation():
+    """Photon densities near 1e-160 (far from any source): no squared
+    magnitude in a denominator may underflow to zero in the reverse pass."""
+    mesh, cfg, st, R = _setup(n=6)
+    st["N"] *= 1e-160
+    st["fr"] *= 1e-160
+    o = make_oracle(mesh, cfg, st)
+    lx = np.zeros((5, mesh.n_cells))
+    lx[1] = 1.0
+    out = o.adjoint(o.max_dt() * 3, 3, lam_x5=lx)
+    assert out["status"] == 0
+    for a in (out["g_src"], out["g_nH"], out["lam0"]["N"], out["lam0"]["fr"], out["lam0"]["x5"]):
+        assert np.isfinite(a).all()
