@@ -278,7 +278,8 @@ def run_gpu(precision, mesh, cfg, state, steps, warmup, rank, world, dev, dist, 
     rtb.rt_profile_enable(rt.ctx, False)
     rt.sync()
     C, F, _ = rt.mesh_info()
-    return dict(ms=ms, C=C, F=F, launches=launches, prof=prof, rt=rt)
+    attempts = float(rt.fields()["nsub"].sum())  # chemistry attempts of the last subcycle
+    return dict(ms=ms, C=C, F=F, launches=launches, prof=prof, rt=rt, attempts=attempts)
 
 
 class _Null:
@@ -328,25 +329,54 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
                 ms_per_step=1e3 * sec / steps)
 
 
-def roofline(res, precision, peaks, peak_kind):
+# FP64 work of one chemistry attempt of the mixed path (2 x DFMA + DMUL + DADD
+# thread instructions, from ncu on the 2e5-cell workload in steady state,
+# one attempt per cell): the unit count behind k_chem's ALU roofline.
+FP64_FLOP_PER_ATTEMPT = {"mixed": 292.0, "fp64": None}
+# GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
+# clock per SM (ncu: 16 cycles per warp instruction on the FP64 pipe) x 2 FLOP
+# x 2.07 GHz = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def roofline(res, precision, peaks, peak_kind, attempts=None):
+    """Roofline of the kernel with the largest time share.  Memory-bound
+    kernels (k_grad, k_flux, k_gather) against the measured HBM copy
+    bandwidth; k_chem (FP64 chemistry) against the FP64 peak when its FP64
+    work per attempt is known."""
     C, F, B = res["C"], res["F"], 3
     w = 4 if precision == "mixed" else 8
     prof = res["prof"]
     total = sum(v[0] for v in prof.values())
     shares = {k: (v[0] / total if total else 0.0) for k, v in prof.items()}
-    top = max(prof, key=lambda k: prof[k][0])
-    ms, n = prof[top]
-    per_launch_s = ms / 1e3 / max(n, 1)
-    alg = algorithmic_bytes(top, C, F, B, w)
-    ach = alg / per_launch_s / 1e9
-    peak = float(peaks["hbm_gbs"])
     kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": round(shares[k], 4),
                 "alg_bytes_per_launch": algorithmic_bytes(k, C, F, B, w),
                 "GBs": algorithmic_bytes(k, C, F, B, w) / (v[0] / 1e3 / max(v[1], 1)) / 1e9 if v[0] else None}
             for k, v in prof.items()}
-    return {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(ach / peak, 4), "peak_source": f"hbm_gbs of {peak_kind}",
-            "traffic": ncu_traffic(top, precision), "alg_bytes_per_launch": alg}, kern
+    peak = float(peaks["hbm_gbs"])
+    for k in kern:
+        kern[k]["hbm_frac"] = round(kern[k]["GBs"] / peak, 4) if kern[k]["GBs"] else None
+
+    def hbm_line(k):
+        return {"kernel": k, "bound": "hbm", "achieved": round(kern[k]["GBs"], 1), "peak": peak, "unit": "GB/s",
+                "frac": kern[k]["hbm_frac"], "peak_source": f"hbm_gbs of {peak_kind}",
+                "traffic": ncu_traffic(k, precision), "alg_bytes_per_launch": kern[k]["alg_bytes_per_launch"]}
+
+    top = max(prof, key=lambda k: prof[k][0])
+    mem = [k for k in prof if k != "k_chem"]
+    top_mem = max(mem, key=lambda k: prof[k][0])
+    flop = FP64_FLOP_PER_ATTEMPT.get(precision)
+    if top == "k_chem" and flop and attempts:
+        per_launch_s = prof[top][0] / 1e3 / max(prof[top][1], 1)
+        ach = flop * attempts / per_launch_s / 1e12
+        line = {"kernel": "k_chem", "bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "FP64 units x clock (152 SMs x 2 FMA lanes/clk x 2 x 2.07 GHz)",
+                "traffic": ncu_traffic("k_chem", precision),
+                "alg_flop_per_launch": flop * attempts, "attempts_per_launch": attempts}
+    else:
+        line = hbm_line(top)
+    return line, kern, hbm_line(top_mem)
 
 
 def cpu_baseline(mesh, cfg, state, budget_s=12.0):
@@ -402,11 +432,12 @@ def measure_large(steps, warmup, dev):
     C, F, _ = rt.mesh_info()
     res = dict(ms=ms, C=C, F=F, prof=prof)
     peaks, kind = measured_peaks()
-    rf, kern = roofline(res, "mixed", peaks, kind)
     f = rt.fields()
+    rf, kern, rf_mem = roofline(res, "mixed", peaks, kind, attempts=float(f["nsub"].sum()))
     return {"workload": f"THESAN-like voronoi 128^3 ({C} cells, {F} faces), GRF n_H, 4096 peak sources, "
                         f"c_red 0.2c, {n_sub} subcycles/step, mixed", "value": C * n_sub * steps / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "roofline": rf,
+            "roofline_memory_kernel": rf_mem,
             "kernels": kern, "mesh_build_s": round(build_s, 1), "x_HII_mean": float(f["x5"][1].mean())}
 
 
@@ -492,8 +523,9 @@ def main():
         r64 = run_gpu("fp64", mesh, cfg, state, max(2, args.steps // 5), 1, rank, world, dev, dist)
         fp64 = {"value": world * r64["C"] * N_SUB * max(2, args.steps // 5) / (r64["ms"] / 1e3),
                 "ms_per_step": r64["ms"] / max(2, args.steps // 5), "dtype": "f64"}
-        rf64, k64 = roofline(r64, "fp64", peaks, peak_kind)
+        rf64, k64, rf64m = roofline(r64, "fp64", peaks, peak_kind)
         fp64["roofline"] = rf64
+        fp64["roofline_memory_kernel"] = rf64m
         fp64["kernels"] = k64
     fp64sum = None
     if not args.no_fp64:
@@ -508,7 +540,7 @@ def main():
         return
     C, F = res["C"], res["F"]
     value = world * C * N_SUB * args.steps / (res["ms"] / 1e3)
-    rf, kern = roofline(res, "mixed", peaks, peak_kind)
+    rf, kern, rf_mem = roofline(res, "mixed", peaks, peak_kind, attempts=res.get("attempts"))
     cpu = None if args.no_cpu else cpu_baseline(mesh, cfg, state)
     ws = (C * 3 * (32 + 16 + 48) + F * (64 + 48) + C * 200)
     out = {
@@ -521,7 +553,7 @@ def main():
                    "precision": "mixed (FP32 sweep; FP64 state, update and chemistry; face-flux sums as compensated FP32 pairs)",
                    "l2": f"working set ~{ws / 1e6:.0f} MB > L2 129 MB (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": rf, "kernels": kern,
+        "roofline": rf, "roofline_memory_kernel": rf_mem, "kernels": kern,
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "mixed_fp64_sums": fp64sum,

@@ -76,40 +76,40 @@ __device__ __forceinline__ float fexp(float x) { return exp2f(x * 1.442695040888
 
 template <> struct RateEval<true> {
   __device__ static Rates eval(double Td) {
-    float T = (float)Td;
+    float T = d2f_int(Td);
     float iT = __frcp_rn(T);
     Rates r;
     float lH = 315614.0f * iT;
-    r.aHII = 2.753e-14f * fpow(lH, 1.5f) / fpow(1.0f + fpow(lH * (1.0f / 2.740f), 0.407f), 2.242f);
+    r.aHII = f2d_int(2.753e-14f * fpow(lH, 1.5f) / fpow(1.0f + fpow(lH * (1.0f / 2.740f), 0.407f), 2.242f));
     float lHe = 570670.0f * iT;
-    r.aHeII = 1.26e-14f * fpow(lHe, 0.750f) +
-              1.9e-3f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    r.aHeII = f2d_int(1.26e-14f * fpow(lHe, 0.750f) +
+                      1.9e-3f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT)));
     float lHe2 = 1263030.0f * iT;
-    r.aHeIII = 2.0f * 2.753e-14f * fpow(lHe2, 1.5f) / fpow(1.0f + fpow(lHe2 * (1.0f / 2.740f), 0.407f), 2.242f);
+    r.aHeIII = f2d_int(2.0f * 2.753e-14f * fpow(lHe2, 1.5f) / fpow(1.0f + fpow(lHe2 * (1.0f / 2.740f), 0.407f), 2.242f));
     float sT = sqrtf(T);
     float tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
-    r.bHI = 5.85e-11f * sT * fexp(-157809.1f * iT) * tf;
-    r.bHeI = 2.38e-11f * sT * fexp(-285335.4f * iT) * tf;
-    r.bHeII = 5.68e-12f * sT * fexp(-631515.0f * iT) * tf;
+    r.bHI = f2d_int(5.85e-11f * sT * fexp(-157809.1f * iT) * tf);
+    r.bHeI = f2d_int(2.38e-11f * sT * fexp(-285335.4f * iT) * tf);
+    r.bHeII = f2d_int(5.68e-12f * sT * fexp(-631515.0f * iT) * tf);
     return r;
   }
   __device__ static double cooling(double Td, double ne, double nHI, double nHII, double nHeI, double nHeII,
                                    double nHeIII) {
-    float T = (float)Td, iT = __frcp_rn(T);
+    float T = d2f_int(Td), iT = __frcp_rn(T);
     float sT = sqrtf(T), tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
     // coefficients in FP32 (erg cm^3 s^-1 scale fits FP32), densities in FP64
-    double c_ceH = 7.50e-19f * fexp(-118348.0f * iT) * tf;
-    double c_ceHe = 5.54e-17f * fpow(T, -0.397f) * fexp(-473638.0f * iT) * tf;
-    double c_ciH = 1.27e-21f * sT * fexp(-157809.1f * iT) * tf;
-    double c_ciHe = 9.38e-22f * sT * fexp(-285335.4f * iT) * tf;
-    double c_ciHe2 = 4.95e-22f * sT * fexp(-631515.0f * iT) * tf;
+    const double c_ceH = f2d_int(7.50e-19f * fexp(-118348.0f * iT) * tf);
+    const double c_ceHe = f2d_int(5.54e-17f * fpow(T, -0.397f) * fexp(-473638.0f * iT) * tf);
+    const double c_ciH = f2d_int(1.27e-21f * sT * fexp(-157809.1f * iT) * tf);
+    const double c_ciHe = f2d_int(9.38e-22f * sT * fexp(-285335.4f * iT) * tf);
+    const double c_ciHe2 = f2d_int(4.95e-22f * sT * fexp(-631515.0f * iT) * tf);
     float t3 = fpow(T * 1e-3f, -0.2f) / (1.0f + fpow(T * 1e-6f, 0.7f));
-    double c_rH = 8.70e-27f * sT * t3;
-    double c_rHe = 1.55e-26f * fpow(T, 0.3647f);
-    double c_rHe2 = 3.48e-26f * sT * t3;
-    double c_di = 1.24e-13f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    const double c_rH = f2d_int(8.70e-27f * sT * t3);
+    const double c_rHe = f2d_int(1.55e-26f * fpow(T, 0.3647f));
+    const double c_rHe2 = f2d_int(3.48e-26f * sT * t3);
+    const double c_di = f2d_int(1.24e-13f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT)));
     float lg = __log10f(T);
-    double c_br = 1.42e-27f * (1.1f + 0.34f * fexp(-(5.5f - lg) * (5.5f - lg) * (1.0f / 3.0f))) * sT;
+    const double c_br = f2d_int(1.42e-27f * (1.1f + 0.34f * fexp(-(5.5f - lg) * (5.5f - lg) * (1.0f / 3.0f))) * sT);
     return ne * (c_ceH * nHI + c_ceHe * nHeII + c_ciH * nHI + c_ciHe * nHeI + c_ciHe2 * nHeII +
                  c_rH * nHII + c_rHe * nHeII + c_rHe2 * nHeIII + c_di * nHeII +
                  c_br * (nHII + nHeII + 4.0 * nHeIII));
@@ -218,18 +218,25 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
 // in FP64 (46, then ~53 bits); within an ulp or two of 1/x for x in the FP32
 // normal range, which every denominator of the chemistry step lies in.
 __device__ __forceinline__ double rcp64(double x) {
-  const float xf = (float)x;
+  const float xf = d2f_int(x);
   if (!(fabsf(xf) < 1e30f && fabsf(xf) > 1e-30f)) return 1.0 / x;
-  double y = (double)__frcp_rn(xf);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+  double y = f2d_int(yf);
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
 
+// Relative change |b - a| / max(|a|, floor) in FP32 from the FP32 images of
+// a and b: it only steers substep lengths and the 10% test, and the FP32
+// cancellation for nearly equal a, b changes f by ~1e-7, far below both
+// the 0.1 threshold and the growth cap's switch point.
 __device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
-  float m = fmaxf(fabsf((float)a), fl);
-  return fabsf((float)(b - a)) / m;
+  const float af = d2f_int(a), bf = d2f_int(b);
+  const float m = fmaxf(fabsf(af), fl);
+  return __fdividef(fabsf(bf - af), m);
 }
 
 // The same attempt as photochem_attempt, arranged for GB300's small FP64
@@ -316,7 +323,7 @@ __device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double
     f = fmaxf(f, rel_change_f(s.yII, t.yII, fl));
     f = fmaxf(f, rel_change_f(s.yIII, t.yIII, fl));
   }
-  return (double)f;
+  return f2d_int(f);
 }
 
 // Adaptive substeps of Sec. 4.1.1 over dt_sub: first attempt = the whole

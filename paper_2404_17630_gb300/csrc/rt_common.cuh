@@ -40,6 +40,32 @@ __device__ __forceinline__ double min_image(double d, double L) {
   return L > 0.0 ? __dsub_rn(d, __dmul_rn(L, round(__ddiv_rn(d, L)))) : d;
 }
 
+// Precision conversions on the integer pipe.  GB300's FP64 pipe is its
+// scarcest unit and also executes F2F conversions, so the mixed path moves
+// values between FP32 and FP64 by assembling the bits instead.  Normal
+// numbers convert as the hardware does (double -> float rounds half up on
+// the first dropped bit); results below the FP32 normal range become signed
+// zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned ef = (hi >> 20) & 0x7FFu;
+  const int e = (int)ef - 896;  // rebias 1023 -> 127
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  if (ef == 0x7FFu) return __uint_as_float(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u));
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((((unsigned)e << 23) | m) + ((lo >> 28) & 1u)));
+}
+
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  if (e == 255u) return __hiloint2double((int)(sign | 0x7FF00000u | (m ? 0x80000u : 0u)), 0);
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // Mesh geometry in the sweep precision R, plus FP64 cell data.
 template <class R> struct Geo {
   int C, F, B;

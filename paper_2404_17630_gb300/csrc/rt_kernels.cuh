@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
       add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = (double)hi[q] + (double)lo[q];
+    for (int q = 0; q < 4; ++q) acc[q] = f2d_int(hi[q]) + f2d_int(lo[q]);
   } else {
     acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
     auto add = [&](int e, const R4<R>& v) {
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   u.w -= kfac * acc[3];
   a.rad[t] = u;
   if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
-  if (shadow) shadow[t] = make_float4((float)u.x, (float)u.y, (float)u.z, (float)u.w);
+  if (shadow) shadow[t] = make_float4(d2f_int(u.x), d2f_int(u.y), d2f_int(u.z), d2f_int(u.w));
 }
 
 // Sources and thermochemistry, one thread per cell (Eq. E source term,
@@ -525,8 +525,8 @@ __global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* 
     if (b < B) {
       a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
       if (!isfinite(s.N[b])) bad = true;
-      if (shadow) shadow[(size_t)i * B + b] = make_float4((float)s.N[b], (float)s.f[b][0], (float)s.f[b][1],
-                                                          (float)s.f[b][2]);
+      if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(s.N[b]), d2f_int(s.f[b][0]), d2f_int(s.f[b][1]),
+                                                          d2f_int(s.f[b][2]));
     }
   }
   if (bad) atomicOr(a.status, kStNonFinite);
