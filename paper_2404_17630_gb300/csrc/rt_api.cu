@@ -108,10 +108,12 @@ rt_status check_config(const rt_config* c) {
 
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
-  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64};
+  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
+                     (const d4*)c->hw, (const d4*)c->hx};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
-  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32};
+  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32,
+                    (const float4*)c->hw, (const float4*)c->hx};
 }
 
 ChemParams chem_params(const rt_ctx* ctx) {
@@ -344,6 +346,11 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     e = cudaMalloc(&p, std::max<size_t>((size_t)F * B * 4 * rs, 1));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "flux");
     ctx->allocs.push_back(p); ctx->flux = p;
+    for (void** h : {&ctx->hw, &ctx->hx}) {
+      e = cudaMalloc(&p, std::max<size_t>(2 * (size_t)F * 4 * rs, 1));
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "half-edges");
+      ctx->allocs.push_back(p); *h = p;
+    }
   }
   if (mx) {
     AL(ctx->nA32, F); AL(ctx->rL32, F); AL(ctx->rR32, F); AL(ctx->w32, F); AL(ctx->minv32, 6 * (size_t)C);
@@ -389,6 +396,14 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->w64, ctx->w32);
   }
   if (mx) k_convert<float><<<nblk(6LL * C), kThreads, 0, ctx->stream>>>(6 * C, ctx->minv64, ctx->minv32);
+  if (F > 0) {
+    if (mx)
+      k_build_halfedges<float><<<nblk(2LL * F), kThreads, 0, ctx->stream>>>(
+          2 * F, ctx->csr, ctx->nbr, ctx->w64, ctx->rL64, ctx->rR64, (float4*)ctx->hw, (float4*)ctx->hx);
+    else
+      k_build_halfedges<double><<<nblk(2LL * F), kThreads, 0, ctx->stream>>>(
+          2 * F, ctx->csr, ctx->nbr, ctx->w64, ctx->rL64, ctx->rR64, (d4*)ctx->hw, (d4*)ctx->hx);
+  }
   if ((st = launched(ctx, "geometry kernels"))) return st;
   int h_status = 0;
   CK(cudaMemcpyAsync(&h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
@@ -768,9 +783,8 @@ rt_status adj_subcycle(rt_ctx* ctx, int slot, double dts) {
   const d4* rt_rad = A.tp_rad_trans + slot * C * B;
   // gradients of the recorded state
   k_grad<double><<<nblk(nCB), kThreads, 0, ctx->stream>>>(
-      Geo<double>{ctx->C, ctx->F, ctx->B, ctx->off, ctx->csr, ctx->nbr, ctx->lr, ctx->nA64, ctx->rL64, ctx->rR64,
-                  ctx->w64, ctx->minv64},
-      rt_rad, (double*)ctx->G, ctx->cfg.order, ctx->cfg.limiter, ctx->cfg.lim_eps * ctx->cfg.lim_eps);
+      geo<double>(ctx), rt_rad, (double*)ctx->G, ctx->cfg.order, ctx->cfg.limiter,
+      ctx->cfg.lim_eps * ctx->cfg.lim_eps);
   AdjArgs a = adj_args(ctx, rt_rad, dts);
   k_adj_face<<<nblk(nFB), kThreads, 0, ctx->stream>>>(a);
   k_adj_cellgrad<<<nblk(nCB), kThreads, 0, ctx->stream>>>(a);

@@ -78,6 +78,14 @@ template <class R> struct Geo {
   const R4<R>* rR;        // F: x_f - s_R
   const R4<R>* w;         // F: A d / |d|^2 with d = s_R - s_L
   const R* minv;          // 6C: symmetric inverse of sum A n n^T (xx, xy, xz, yy, yz, zz)
+  const R4<R>* hw;        // 2F half-edges in CSR order: (+-w of the face, sign + for the left cell; neighbour id bits)
+  const R4<R>* hx;        // 2F half-edges in CSR order: x_f - s of this cell's side
 };
+
+// Cell id stored in the fourth lane of a half-edge record (bit copy).
+__device__ __forceinline__ float id_bits(int j, float) { return __int_as_float(j); }
+__device__ __forceinline__ double id_bits(int j, double) { return __longlong_as_double((long long)j); }
+__device__ __forceinline__ int bits_id(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_id(double v) { return (int)__double_as_longlong(v); }
 
 }  // namespace m1rt

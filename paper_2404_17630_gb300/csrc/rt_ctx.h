@@ -22,6 +22,7 @@ struct rt_ctx {
   int32_t *off = nullptr, *csr = nullptr, *nbr = nullptr;
   int2* lr = nullptr;
   d4 *nA64 = nullptr, *rL64 = nullptr, *rR64 = nullptr, *w64 = nullptr;
+  void *hw = nullptr, *hx = nullptr;   // half-edge records in the sweep precision
   double* minv64 = nullptr;
   // FP32 copies (mixed precision)
   float4 *nA32 = nullptr, *rL32 = nullptr, *rR32 = nullptr, *w32 = nullptr;

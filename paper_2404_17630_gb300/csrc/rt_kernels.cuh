@@ -93,6 +93,28 @@ template <class R> __global__ void k_convert4(int n, const d4* __restrict__ in, 
   out[k] = o;
 }
 
+// Half-edge records in CSR order for the gradient kernel: the face's
+// least-squares weight with the sign that makes the contribution
+// w_k (phi_neighbour - phi_cell), the neighbour id, and the face-centre
+// offset from this cell.
+template <class R>
+__global__ void k_build_halfedges(int n, const int32_t* __restrict__ csr, const int32_t* __restrict__ nbr,
+                                  const d4* __restrict__ w, const d4* __restrict__ rL, const d4* __restrict__ rR,
+                                  R4<R>* hw, R4<R>* hx) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int e = csr[k], f = e >> 1;
+  const d4 wf = w[f];
+  const double sg = (e & 1) ? -1.0 : 1.0;
+  R4<R> a;
+  a.x = (R)(sg * wf.x); a.y = (R)(sg * wf.y); a.z = (R)(sg * wf.z); a.w = id_bits(nbr[k], R(0));
+  hw[k] = a;
+  const d4 x = (e & 1) ? rR[f] : rL[f];
+  R4<R> b;
+  b.x = (R)x.x; b.y = (R)x.y; b.z = (R)x.z; b.w = R(0);
+  hx[k] = b;
+}
+
 template <class R> __global__ void k_convert(int n, const double* __restrict__ in, R* out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) out[k] = (R)in[k];
@@ -180,14 +202,15 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     mx[q] = mn[q] = comp<R>(pi, q);
   }
   const int k0 = g.off[i], k1 = g.off[i + 1];
-  auto acc_face = [&](int e, const R4<R>& pj, const R4<R>& w) {
+  // half-edge k: w_k (phi_j - phi_i) is this face's term of the least-squares
+  // right-hand side (w_k carries the side's sign)
+  auto acc_face = [&](const R4<R>& hw, const R4<R>& pj) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      R vj = comp<R>(pj, q), vi = comp<R>(pi, q);
-      R dphi = (e & 1) ? (vi - vj) : (vj - vi);   // phi_R - phi_L of this face
-      r[q][0] += w.x * dphi;
-      r[q][1] += w.y * dphi;
-      r[q][2] += w.z * dphi;
+      const R vj = comp<R>(pj, q), dphi = vj - comp<R>(pi, q);
+      r[q][0] += hw.x * dphi;
+      r[q][1] += hw.y * dphi;
+      r[q][2] += hw.z * dphi;
       mx[q] = vj > mx[q] ? vj : mx[q];
       mn[q] = vj < mn[q] ? vj : mn[q];
     }
@@ -195,19 +218,17 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   int k = k0;
   // batches of four faces, loads first, accumulation in CSR order
   for (; k + 4 <= k1; k += 4) {
-    int e[4], j[4];
+    R4<R> hw[4], pj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { e[u] = __ldg(g.csr + k + u); j[u] = __ldg(g.nbr + k + u); }
-    R4<R> pj[4], w[4];
+    for (int u = 0; u < 4; ++u) hw[u] = ld4<R>(g.hw + k + u);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { pj[u] = ld4<R>(rad + (size_t)j[u] * B + b); w[u] = ld4<R>(g.w + (e[u] >> 1)); }
+    for (int u = 0; u < 4; ++u) pj[u] = ld4<R>(rad + (size_t)bits_id(hw[u].w) * B + b);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc_face(e[u], pj[u], w[u]);
+    for (int u = 0; u < 4; ++u) acc_face(hw[u], pj[u]);
   }
   for (; k < k1; ++k) {
-    const int e = __ldg(g.csr + k);
-    const int j = __ldg(g.nbr + k);
-    acc_face(e, ld4<R>(rad + (size_t)j * B + b), ld4<R>(g.w + (e >> 1)));
+    const R4<R> hw = ld4<R>(g.hw + k);
+    acc_face(hw, ld4<R>(rad + (size_t)bits_id(hw.w) * B + b));
   }
   const R* m = g.minv + 6 * (size_t)i;
   const R m00 = m[0], m01 = m[1], m02 = m[2], m11 = m[3], m12 = m[4], m22 = m[5];
@@ -231,8 +252,7 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = R(0);
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-      const int e = __ldg(g.csr + k), f = e >> 1;
-      const R4<R> x = ld4<R>((e & 1) ? (g.rR + f) : (g.rL + f));
+      const R4<R> x = ld4<R>(g.hx + k);
       const R xx = x.x * x.x + x.y * x.y + x.z * x.z;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
