@@ -128,10 +128,13 @@ ChemParams chem_params(const rt_ctx* ctx) {
   P.f_max = c.f_max;
   P.x_floor = c.x_floor;
   P.max_sub = c.max_substeps;
+  P.smask = P.emask = 0;
   for (int b = 0; b < kMaxBins; ++b)
     for (int s = 0; s < 3; ++s) {
       P.sigma[b][s] = b < c.n_bins ? c.sigma[b][s] : 0.0;
       P.eps[b][s] = b < c.n_bins ? c.eps[b][s] : 0.0;
+      if (P.sigma[b][s] != 0.0) P.smask |= 1 << (3 * b + s);
+      if (P.eps[b][s] != 0.0) P.emask |= 1 << (3 * b + s);
     }
   return P;
 }

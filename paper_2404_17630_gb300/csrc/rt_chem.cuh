@@ -20,6 +20,8 @@ struct ChemParams {
   int max_sub;
   double sigma[kMaxBins][3];
   double eps[kMaxBins][3];
+  int smask;         // bit 3b+s: sigma[b][s] != 0
+  int emask;         // bit 3b+s: eps[b][s] != 0
 };
 
 constexpr double kBoltzmann = 1.380649e-16;
@@ -214,19 +216,16 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   return f;
 }
 
-// FP64 reciprocal: FP32 hardware seed (23 bits) refined by two Newton steps
-// in FP64 (46, then ~53 bits); within an ulp or two of 1/x for x in the FP32
-// normal range, which every denominator of the chemistry step lies in.
+// FP64 reciprocal: FP32 hardware seed (~22 bits) refined by one Newton step
+// in FP64 (~44 bits, relative error below 1e-13), for x in the FP32 normal
+// range, which every denominator of the chemistry step lies in.
 __device__ __forceinline__ double rcp64(double x) {
   const float xf = d2f_int(x);
   if (!(fabsf(xf) < 1e30f && fabsf(xf) > 1e-30f)) return 1.0 / x;
   float yf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
-  double y = f2d_int(yf);
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double y = f2d_int(yf);
+  return fma(y, fma(-x, y, 1.0), y);   // one Newton step: ~2^-44 relative
 }
 
 // Relative change |b - a| / max(|a|, floor) in FP32 from the FP32 images of
@@ -245,8 +244,8 @@ __device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
 // division by N_b, and the substep-control measure f (which only steers step
 // lengths and the accept test) is formed in FP32.  State, rates products and
 // all updates stay FP64.
-__device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const CellState& s,
-                                          CellState& t) {
+__device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const CellState& s,
+                                         CellState& t) {
   const int B = P.B;
   const double c = P.c_red;
   const double cdt = c * dt;
@@ -254,20 +253,26 @@ __device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double
   const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
   const Rates r = RateEval<true>::eval(s.T);
 
-  const double ns0 = nH * s.xHI, ns1 = nHe * s.yI, ns2 = nHe * s.yII;
+  const double ns[3] = {nH * s.xHI, nHe * s.yI, nHe * s.yII};
   double inv1pt[kMaxBins], Nbar[kMaxBins];
-  double G0 = 0, G1 = 0, G2 = 0;
+  double Gs[3] = {0, 0, 0};
+  // products with zero cross-sections (a bin below a species' threshold) are
+  // skipped; the mask is uniform across threads
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
-      double kap = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
-      inv1pt[b] = rcp64(1.0 + cdt * kap);
+      double kap = 0.0;
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+        if (P.smask & (1 << (3 * b + sp))) kap = fma(P.sigma[b][sp], ns[sp], kap);
+      inv1pt[b] = rcp64(fma(cdt, kap, 1.0));
       Nbar[b] = s.N[b] * inv1pt[b];
-      G0 += P.sigma[b][0] * Nbar[b];
-      G1 += P.sigma[b][1] * Nbar[b];
-      G2 += P.sigma[b][2] * Nbar[b];
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+        if (P.smask & (1 << (3 * b + sp))) Gs[sp] = fma(P.sigma[b][sp], Nbar[b], Gs[sp]);
     }
   }
+  const double G0 = Gs[0], G1 = Gs[1], G2 = Gs[2];
   const double ne0 = nH * s.xHII + nHe * (s.yII + 2.0 * s.yIII);
   const double aH = cdt * G0 + (coll ? dt * r.bHI * ne0 : 0.0);
   const double bH = recomb ? dt * r.aHII * ne0 : 0.0;
@@ -284,16 +289,28 @@ __device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double
   t.yI = (s.yI + Bb * t.yII) * iA;
   t.yIII = (s.yIII + Cc * t.yII) * iD;
 
-  const double m0 = nH * t.xHI, m1 = nHe * t.yI, m2 = nHe * t.yII;
+  const double m[3] = {nH * t.xHI, nHe * t.yI, nHe * t.yII};
   double heat_e = 0.0;
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
-      const double a0 = P.sigma[b][0] * m0, a1 = P.sigma[b][1] * m1, a2 = P.sigma[b][2] * m2;
-      const double taup = cdt * ((a0 + a1) + a2);
-      double sc = 1.0 - taup * inv1pt[b];
+      double a[3] = {0.0, 0.0, 0.0}, suma = 0.0;
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+        if (P.smask & (1 << (3 * b + sp))) {
+          a[sp] = P.sigma[b][sp] * m[sp];
+          suma += a[sp];
+        }
+      const double taup = cdt * suma;
+      double sc = fma(-taup, inv1pt[b], 1.0);
       sc = sc > 0.0 ? sc : 0.0;
-      if (heat) heat_e += cdt * Nbar[b] * (P.eps[b][0] * a0 + P.eps[b][1] * a1 + P.eps[b][2] * a2);
+      if (heat) {
+        double ea = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < 3; ++sp)
+          if (P.emask & P.smask & (1 << (3 * b + sp))) ea = fma(P.eps[b][sp], a[sp], ea);
+        heat_e = fma(cdt * Nbar[b], ea, heat_e);
+      }
       t.N[b] = s.N[b] * sc;
       t.f[b][0] = s.f[b][0] * sc;
       t.f[b][1] = s.f[b][1] * sc;
@@ -323,7 +340,7 @@ __device__ double photochem_attempt_mixed(const ChemParams& P, double nH, double
     f = fmaxf(f, rel_change_f(s.yII, t.yII, fl));
     f = fmaxf(f, rel_change_f(s.yIII, t.yIII, fl));
   }
-  return f2d_int(f);
+  return f;
 }
 
 // Adaptive substeps of Sec. 4.1.1 over dt_sub: first attempt = the whole
@@ -336,10 +353,32 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
   int n = 0;
   CellState t;
   *capped = false;
+  if (Fast) {
+    // mixed path: f is an FP32 quantity, so the accept test and the growth
+    // factor are FP32; dt and the remaining time stay FP64 (the subcycle is
+    // covered exactly).  Both are >= 0, where the order of the bit patterns
+    // is the numeric order: the comparisons run on the integer pipe.
+    const float fmax = (float)P.f_max, fs = (float)P.f_s;
+    while (__double_as_longlong(rem) > 0) {
+      if (n >= P.max_sub) { *capped = true; break; }
+      ++n;
+      const float f = photochem_attempt_mixed(P, nH, dt, s, t);
+      if (f > fmax) {
+        dt = dt * f2d_int(__fdividef(fs, f));
+        continue;
+      }
+      s = t;
+      rem = (__double_as_longlong(dt) == __double_as_longlong(rem)) ? 0.0 : rem - dt;
+      const float grow = f > 0.0f ? fminf(__fdividef(fs, f), 2.0f) : 2.0f;
+      dt = dt * f2d_int(grow);
+      if (__double_as_longlong(dt) > __double_as_longlong(rem)) dt = rem;
+    }
+    return n;
+  }
   while (rem > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;
-    double f = Fast ? photochem_attempt_mixed(P, nH, dt, s, t) : photochem_attempt<false>(P, nH, dt, s, t);
+    double f = photochem_attempt<false>(P, nH, dt, s, t);
     if (f > P.f_max) {
       dt = dt * (P.f_s / f);
       continue;
