@@ -53,7 +53,8 @@ enum {
   RT_NONFINITE = 5,     /* a photon density became NaN or Inf */
   RT_OOM = 6,           /* device allocation failed */
   RT_CUDA = 7,          /* other CUDA runtime error */
-  RT_NOT_READY = 8      /* call order: mesh or state missing */
+  RT_NOT_READY = 8,     /* call order: mesh or state missing */
+  RT_TIMEOUT = 9        /* a kernel's bounded wait for its own asynchronous copies gave up */
 };
 
 enum { RT_FP64 = 0, RT_MIXED = 1 };

@@ -108,11 +108,11 @@ rt_status check_config(const rt_config* c) {
 
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
-  return Geo<double>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
+  return Geo<double>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
                      (const d4*)c->hw, (const d4*)c->hx};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
-  return Geo<float>{c->C, c->F, c->B, c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32,
+  return Geo<float>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32,
                     (const float4*)c->hw, (const float4*)c->hx};
 }
 
@@ -141,7 +141,7 @@ ChemParams chem_params(const rt_ctx* ctx) {
 
 CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
   CellArgs a;
-  a.C = ctx->C; a.B = ctx->B; a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.rad = ctx->rad;
+  a.C = ctx->C; a.B = ctx->B; a.divB = make_divb(ctx->B); a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.rad = ctx->rad;
   a.nH = ctx->nH; a.x5 = ctx->x5; a.T = ctx->T; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
   a.nsub = ctx->nsub; a.status = ctx->status;
   a.lam = ctx->cfg.c_red * dt / ctx->cfg.unit_length_cm;
@@ -183,9 +183,22 @@ template <class R> const R4<R>* sweep_rad(rt_ctx* ctx);
 template <> const d4* sweep_rad<double>(rt_ctx* ctx) { return ctx->rad; }
 template <> const float4* sweep_rad<float>(rt_ctx* ctx) { return ctx->shadow; }
 
+constexpr int kGradNB = 8;   // neighbour loads in flight per thread (staged gradients)
+constexpr size_t kGradSmemMax = 160 * 1024;
+
 template <class R> void launch_grad(rt_ctx* ctx) {
   ProfScope ps(ctx, RT_KERNEL_GRAD);
   const R e = (R)ctx->cfg.lim_eps;
+  if constexpr (sizeof(R) == 4) {
+    if (ctx->grad_cap > 0 && ctx->cfg.order >= 2) {
+      const int nb = (ctx->C + kGradCells - 1) / kGradCells;
+      const size_t smem = 2 * (size_t)ctx->grad_cap * sizeof(float4);
+      k_grad_staged<kGradNB><<<nb, kGradCells * ctx->B, smem, ctx->stream>>>(
+          geo<float>(ctx), sweep_rad<float>(ctx), (float*)ctx->G, ctx->cfg.limiter, e * e, ctx->grad_cap,
+          ctx->status);
+      return;
+    }
+  }
   k_grad<R><<<nblk((long long)ctx->C * ctx->B), kThreads, 0, ctx->stream>>>(
       geo<R>(ctx), sweep_rad<R>(ctx), (R*)ctx->G, ctx->cfg.order, ctx->cfg.limiter, e * e);
 }
@@ -328,6 +341,20 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   }
   ctx->max_deg = maxdeg;
   ctx->min_dx_cm = std::cbrt(minV) * ctx->cfg.unit_length_cm;
+  // staged gradients (FP32 sweep): shared memory for the largest block's
+  // half-edge records; a mesh whose blocks need more than kGradSmemMax keeps
+  // the unstaged kernel
+  ctx->grad_cap = 0;
+  if (mixed(ctx)) {
+    int cap = 0;
+    for (int c0 = 0; c0 < C; c0 += kGradCells) cap = std::max(cap, off[std::min(c0 + kGradCells, C)] - off[c0]);
+    const size_t smem = 2 * (size_t)cap * sizeof(float4);
+    if (smem <= kGradSmemMax) {
+      CK(cudaFuncSetAttribute(k_grad_staged<kGradNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+         "staged gradients");
+      ctx->grad_cap = cap;
+    }
+  }
 
   rt_status st;
 #define AL(p, n) if ((st = dalloc(ctx, &(p), (n), #p))) return st
@@ -544,6 +571,7 @@ rt_status rt_sync(rt_ctx* ctx) {
   CK(cudaMemcpyAsync(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "status");
   CK(cudaStreamSynchronize(ctx->stream), "rt_sync");
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  if (h & kStTimeout) return fail(ctx, RT_TIMEOUT, "a device wait for a bulk copy gave up");
   if (h & kStNonFinite) return fail(ctx, RT_NONFINITE, "non-finite photon density");
   if (h & kStChemSubsteps) return fail(ctx, RT_CHEM_SUBSTEPS, "a cell reached max_substeps");
   return RT_OK;

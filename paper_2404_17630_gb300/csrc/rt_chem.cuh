@@ -243,9 +243,17 @@ __device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
 // the photon removal uses N_b' = N_b (1 - tau'_b / (1 + tau_b)) instead of a
 // division by N_b, and the substep-control measure f (which only steers step
 // lengths and the accept test) is formed in FP32.  State, rates products and
-// all updates stay FP64.
-__device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const CellState& s,
-                                         CellState& t) {
+// all updates stay FP64.  The reduced flux does not enter the chemistry: an
+// attempt only reports the factor sc_b that scales bin b's photons (and, by
+// kappa_F = kappa_E, its flux); the caller applies the product of the
+// accepted factors to the flux once.
+struct GasState {
+  double N[kMaxBins];
+  double xHI, xHII, yI, yII, yIII, T;
+};
+
+__device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const GasState& s,
+                                         GasState& t, double sc_out[kMaxBins]) {
   const int B = P.B;
   const double c = P.c_red;
   const double cdt = c * dt;
@@ -312,9 +320,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
         heat_e = fma(cdt * Nbar[b], ea, heat_e);
       }
       t.N[b] = s.N[b] * sc;
-      t.f[b][0] = s.f[b][0] * sc;
-      t.f[b][1] = s.f[b][1] * sc;
-      t.f[b][2] = s.f[b][2] * sc;
+      sc_out[b] = sc;
     }
   }
   const float fl = (float)P.x_floor;
@@ -347,34 +353,48 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 // subcycle; reject if f > f_max and retry with dt f_s / f; after an accepted
 // attempt the next is dt min(f_s / f, 2), clipped to the remaining time.
 // Returns the number of attempts; sets *capped if max_sub was reached.
-template <bool Fast>
+// Mixed path: f is an FP32 quantity, so the accept test and the growth
+// factor are FP32; dt and the remaining time stay FP64 (the subcycle is
+// covered exactly).  Both are >= 0, where the order of the bit patterns is
+// the numeric order: the comparisons run on the integer pipe.  S_b returns
+// the product of the accepted attempts' photon factors (the flux scale).
+__device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, GasState& s,
+                               double S[kMaxBins], bool* capped) {
+  double rem = dt_sub, dt = dt_sub;
+  int n = 0, acc = 0;
+  GasState t;
+  double sc[kMaxBins];
+  *capped = false;
+  const float fmax = (float)P.f_max, fs = (float)P.f_s;
+  while (__double_as_longlong(rem) > 0) {
+    if (n >= P.max_sub) { *capped = true; break; }
+    ++n;
+    const float f = photochem_attempt_mixed(P, nH, dt, s, t, sc);
+    if (f > fmax) {
+      dt = dt * f2d_int(__fdividef(fs, f));
+      continue;
+    }
+    s = t;
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) S[b] = acc ? S[b] * sc[b] : sc[b];
+    ++acc;
+    rem = (__double_as_longlong(dt) == __double_as_longlong(rem)) ? 0.0 : rem - dt;
+    const float grow = f > 0.0f ? fminf(__fdividef(fs, f), 2.0f) : 2.0f;
+    dt = dt * f2d_int(grow);
+    if (__double_as_longlong(dt) > __double_as_longlong(rem)) dt = rem;
+  }
+  if (acc == 0) {
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0;
+  }
+  return n;
+}
+
 __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {
   double rem = dt_sub, dt = dt_sub;
   int n = 0;
   CellState t;
   *capped = false;
-  if (Fast) {
-    // mixed path: f is an FP32 quantity, so the accept test and the growth
-    // factor are FP32; dt and the remaining time stay FP64 (the subcycle is
-    // covered exactly).  Both are >= 0, where the order of the bit patterns
-    // is the numeric order: the comparisons run on the integer pipe.
-    const float fmax = (float)P.f_max, fs = (float)P.f_s;
-    while (__double_as_longlong(rem) > 0) {
-      if (n >= P.max_sub) { *capped = true; break; }
-      ++n;
-      const float f = photochem_attempt_mixed(P, nH, dt, s, t);
-      if (f > fmax) {
-        dt = dt * f2d_int(__fdividef(fs, f));
-        continue;
-      }
-      s = t;
-      rem = (__double_as_longlong(dt) == __double_as_longlong(rem)) ? 0.0 : rem - dt;
-      const float grow = f > 0.0f ? fminf(__fdividef(fs, f), 2.0f) : 2.0f;
-      dt = dt * f2d_int(grow);
-      if (__double_as_longlong(dt) > __double_as_longlong(rem)) dt = rem;
-    }
-    return n;
-  }
   while (rem > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;

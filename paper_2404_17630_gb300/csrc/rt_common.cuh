@@ -11,6 +11,54 @@ constexpr int kMaxBins = 3;
 constexpr int kStChemSubsteps = 1;
 constexpr int kStNonFinite = 2;
 constexpr int kStSingular = 4;
+constexpr int kStTimeout = 8;     // a bounded device wait gave up
+
+// Polls of an mbarrier before a kernel gives up waiting (each poll may
+// suspend the thread for a hardware-chosen interval; the whole wait stays
+// far below a second).
+constexpr uint32_t kWaitPolls = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine, untiled) into shared memory,
+// completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One arrival that also announces `bytes` of asynchronous transfer.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned), counted against the mbarrier's transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the phase with the given parity; false after kWaitPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t n = 0; n < kWaitPolls; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 
 // 32-byte aligned 4-vector of doubles (one 256-bit access).
 using d4 = double4_32a;
@@ -66,9 +114,28 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// n / d for 0 <= n < 2^31 by one wide multiply and a shift.  With
+// L = ceil(log2 d), S = 31 + L and M = ceil(2^S / d) = (2^S + e) / d,
+// 0 <= e < d: n M / 2^S = n / d + n e / (d 2^S) and n e < 2^31 2^L = 2^S,
+// so the excess stays below 1/d and the floor is exact; M < 2^32.
+struct DivB {
+  uint32_t m, s;
+};
+inline DivB make_divb(int d) {
+  uint32_t L = 0;
+  while ((1u << L) < (uint32_t)d) ++L;
+  const uint32_t S = 31 + L;
+  const unsigned long long M = ((1ull << S) + (unsigned long long)d - 1) / (unsigned long long)d;
+  return DivB{(uint32_t)M, S};
+}
+__device__ __forceinline__ int divb(int n, DivB q) {
+  return (int)(((unsigned long long)(unsigned)n * q.m) >> q.s);
+}
+
 // Mesh geometry in the sweep precision R, plus FP64 cell data.
 template <class R> struct Geo {
   int C, F, B;
+  DivB divB;              // division by B
   const int32_t* off;     // C+1 CSR offsets
   const int32_t* csr;     // 2F entries: (face << 1) | side, side 1 = this cell is the right cell
   const int32_t* nbr;     // 2F entries: the other cell of the same face

@@ -16,6 +16,7 @@ struct rt_ctx {
   std::string err;
   bool mesh_ready = false;
   int C = 0, F = 0, B = 0, max_deg = 0;
+  int grad_cap = 0;  // half-edge records of the largest gradient block (0: unstaged gradient kernel)
   double min_dx_cm = 0;
   // FP64 cell and face data
   double *vol = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;

@@ -96,7 +96,9 @@ template <class R> __global__ void k_convert4(int n, const d4* __restrict__ in, 
 // Half-edge records in CSR order for the gradient kernel: the face's
 // least-squares weight with the sign that makes the contribution
 // w_k (phi_neighbour - phi_cell), the neighbour id, and the face-centre
-// offset from this cell.
+// offset x from this cell with, in the fourth lane, |x| (FP32 sweep) or
+// |x|^2 (FP64 sweep, summed in the order of the limiter's definition) for
+// the limiter's regularisation test.
 template <class R>
 __global__ void k_build_halfedges(int n, const int32_t* __restrict__ csr, const int32_t* __restrict__ nbr,
                                   const d4* __restrict__ w, const d4* __restrict__ rL, const d4* __restrict__ rR,
@@ -111,7 +113,9 @@ __global__ void k_build_halfedges(int n, const int32_t* __restrict__ csr, const 
   hw[k] = a;
   const d4 x = (e & 1) ? rR[f] : rL[f];
   R4<R> b;
-  b.x = (R)x.x; b.y = (R)x.y; b.z = (R)x.z; b.w = R(0);
+  const double xx = __dadd_rn(__dadd_rn(__dmul_rn(x.x, x.x), __dmul_rn(x.y, x.y)), __dmul_rn(x.z, x.z));
+  b.x = (R)x.x; b.y = (R)x.y; b.z = (R)x.z;
+  b.w = sizeof(R) == 4 ? (R)sqrt(xx) : (R)xx;
   hx[k] = b;
 }
 
@@ -179,6 +183,17 @@ template <class R> __device__ __forceinline__ R comp(const R4<R>& v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
 
+// max / min of two finite values: one FMNMX in FP32; the FP64 sweep keeps
+// the comparison form of the limiter's definition.
+template <class R> __device__ __forceinline__ R rmax(R a, R b) {
+  if constexpr (sizeof(R) == 4) return fmaxf(a, b);
+  else return b > a ? b : a;
+}
+template <class R> __device__ __forceinline__ R rmin(R a, R b) {
+  if constexpr (sizeof(R) == 4) return fminf(a, b);
+  else return b < a ? b : a;
+}
+
 // G[(i*B + b)*12 + q*3 + d]: limited gradient of component q of bin b.
 template <class R>
 __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict__ rad, R* __restrict__ G,
@@ -186,7 +201,7 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
   if (t >= g.C * B) return;
-  const int i = t / B, b = t % B;
+  const int i = divb(t, g.divB), b = t - i * B;
   R* Go = G + (size_t)t * 12;
   if (order < 2) {
 #pragma unroll
@@ -211,8 +226,8 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
       r[q][0] += hw.x * dphi;
       r[q][1] += hw.y * dphi;
       r[q][2] += hw.z * dphi;
-      mx[q] = vj > mx[q] ? vj : mx[q];
-      mn[q] = vj < mn[q] ? vj : mn[q];
+      mx[q] = rmax<R>(mx[q], vj);
+      mn[q] = rmin<R>(mn[q], vj);
     }
   };
   int k = k0;
@@ -250,16 +265,34 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     R dpos[4], dneg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = R(0);
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-      const R4<R> x = ld4<R>(g.hx + k);
-      const R xx = x.x * x.x + x.y * x.y + x.z * x.z;
+    if constexpr (sizeof(R) == 4) {
+      // |g.x| > eps |g| |x| with |x| from the record: a threshold product,
+      // an abs-compare and a select per component; excluded faces add 0
+      float eg[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-        if (dphi * dphi > lim_eps2 * gg[q] * xx) {
-          dpos[q] = dphi > dpos[q] ? dphi : dpos[q];
-          dneg[q] = dphi < dneg[q] ? dphi : dneg[q];
+      for (int q = 0; q < 4; ++q) eg[q] = sqrtf(lim_eps2 * gg[q]);
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) {
+        const R4<R> x = ld4<R>(g.hx + k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+          const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
+          dpos[q] = fmaxf(dpos[q], dm);
+          dneg[q] = fminf(dneg[q], dm);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) {
+        const R4<R> x = ld4<R>(g.hx + k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+          if (dphi * dphi > lim_eps2 * gg[q] * x.w) {
+            dpos[q] = dphi > dpos[q] ? dphi : dpos[q];
+            dneg[q] = dphi < dneg[q] ? dphi : dneg[q];
+          }
         }
       }
     }
@@ -292,6 +325,119 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   }
 }
 
+// The same gradients and limiter for the FP32 sweep with the half-edge
+// records staged in shared memory.  A block owns kGradCells consecutive
+// cells, whose records are one contiguous range of the CSR arrays: one
+// thread issues two bulk copies (TMA engine) of that range into shared
+// memory, completed on an mbarrier, while every thread loads its own cell
+// state; afterwards the only global loads left per face are the neighbour
+// states, issued NB at a time.  `cap` is the largest record count of any
+// block (the dynamic shared memory holds 2 cap records).
+constexpr int kGradCells = 64;
+
+template <int NB>
+__global__ void __launch_bounds__(kGradCells* kMaxBins)
+    k_grad_staged(Geo<float> g, const float4* __restrict__ rad, float* __restrict__ G, int limiter, float lim_eps2,
+                  int cap, int* status) {
+  extern __shared__ float4 sm[];  // [cap] weight records, then [cap] offset records
+  __shared__ __align__(8) uint64_t bar;
+  const int B = g.B;
+  const int c0 = blockIdx.x * kGradCells;
+  const int c1 = min(c0 + kGradCells, g.C);
+  const int kb0 = __ldg(g.off + c0), kb1 = __ldg(g.off + c1);
+  const int lt = threadIdx.x;
+  const int cl = divb(lt, g.divB), b = lt - cl * B;
+  const int i = c0 + cl;
+  const bool active = i < c1;
+  if (lt == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (lt == 0) {
+    const uint32_t bytes = (uint32_t)(kb1 - kb0) * (uint32_t)sizeof(float4);
+    mbar_arrive_expect_tx(&bar, 2 * bytes);
+    bulk_g2s(sm, g.hw + kb0, bytes, &bar);
+    bulk_g2s(sm + cap, g.hx + kb0, bytes, &bar);
+  }
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+  int k0 = 0, k1 = 0;
+  float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+  if (active) {
+    pi = __ldg(rad + (size_t)i * B + b);
+    k0 = __ldg(g.off + i) - kb0;
+    k1 = __ldg(g.off + i + 1) - kb0;
+    const float* m = g.minv + 6 * (size_t)i;
+    m00 = __ldg(m); m01 = __ldg(m + 1); m02 = __ldg(m + 2); m11 = __ldg(m + 3); m12 = __ldg(m + 4);
+    m22 = __ldg(m + 5);
+  }
+  if (!mbar_wait(&bar, 0)) {
+    if (lt == 0) atomicOr(status, kStTimeout);
+    return;
+  }
+  if (!active) return;
+  const float4* shw = sm;
+  const float4* shx = sm + cap;
+  float r[4][3], mx[4], mn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    r[q][0] = r[q][1] = r[q][2] = 0.f;
+    mx[q] = mn[q] = comp<float>(pi, q);
+  }
+  auto acc_face = [&](const float4& hw, const float4& pj) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float vj = comp<float>(pj, q), dphi = vj - comp<float>(pi, q);
+      r[q][0] += hw.x * dphi;
+      r[q][1] += hw.y * dphi;
+      r[q][2] += hw.z * dphi;
+      mx[q] = fmaxf(mx[q], vj);
+      mn[q] = fminf(mn[q], vj);
+    }
+  };
+  int k = k0;
+  for (; k + NB <= k1; k += NB) {
+    float4 pj[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) pj[u] = __ldg(rad + (size_t)bits_id(shw[k + u].w) * B + b);
+#pragma unroll
+    for (int u = 0; u < NB; ++u) acc_face(shw[k + u], pj[u]);
+  }
+  for (; k < k1; ++k) acc_face(shw[k], __ldg(rad + (size_t)bits_id(shw[k].w) * B + b));
+  float gr[4][3], psi[4], eg[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    gr[q][0] = m00 * r[q][0] + m01 * r[q][1] + m02 * r[q][2];
+    gr[q][1] = m01 * r[q][0] + m11 * r[q][1] + m12 * r[q][2];
+    gr[q][2] = m02 * r[q][0] + m12 * r[q][1] + m22 * r[q][2];
+    eg[q] = sqrtf(lim_eps2 * (gr[q][0] * gr[q][0] + gr[q][1] * gr[q][1] + gr[q][2] * gr[q][2]));
+    psi[q] = 1.f;
+  }
+  if (limiter) {
+    float dpos[4], dneg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.f;
+#pragma unroll 4
+    for (int kk = k0; kk < k1; ++kk) {
+      const float4 x = shx[kk];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+        const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
+        dpos[q] = fmaxf(dpos[q], dm);
+        dneg[q] = fminf(dneg[q], dm);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float vi = comp<float>(pi, q);
+      if (dpos[q] > 0.f) psi[q] = fminf(psi[q], (mx[q] - vi) / dpos[q]);
+      if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
+    }
+  }
+  float4* G4 = reinterpret_cast<float4*>(G + ((size_t)i * B + b) * 12);
+  G4[0] = make_float4(gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0], gr[1][0] * psi[1]);
+  G4[1] = make_float4(gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
+  G4[2] = make_float4(gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3], gr[3][2] * psi[3]);
+}
+
 // ---------------------------------------------------------------------------
 // face flux
 // ---------------------------------------------------------------------------
@@ -311,7 +457,8 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
   }
   if (v[0] < R(0)) v[0] = R(0);
   if constexpr (sizeof(R) == 4) {
-    // FP32 sweep: |F| <= c N tested on squares, scale by rsqrt
+    // FP32 sweep: |F| <= c N tested on squares, scale by rsqrt (a branch:
+    // the clamp is rare and the rsqrt and products are then skipped)
     const float fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
     if (fl2 > v[0] * v[0]) {
       const float s = v[0] * rsqrtf(fl2);
@@ -326,26 +473,33 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
   }
 }
 
+// Hardware reciprocal approximation (MUFU; relative error ~1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // N D n with the Levermore M1 Eddington tensor.
 template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0, R n1, R n2, R P[3]) {
   if constexpr (sizeof(R) == 4) {
-    // FP32 sweep: one rsqrt for |F|, fast reciprocals
+    // FP32 sweep, without branches, from hardware approximations (rsqrt,
+    // reciprocal; sqrt(t) = t rsqrt(t) on t in [1, 4]).  Where F = 0 (which
+    // the face-state clamp also makes of N = 0), f = 0 and u = 0 give
+    // chi = 1/3 and D n = n / 3: the isotropic case needs no branch.
     const float fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-    if (v[0] > 0.0f && fl2 > 0.0f) {
-      const float ifl = rsqrtf(fl2);
-      float f = fl2 * ifl * __frcp_rn(v[0]);
-      f = f > 1.0f ? 1.0f : f;
-      const float chi = __fdividef(3.0f + 4.0f * f * f, 5.0f + 2.0f * sqrtf(4.0f - 3.0f * f * f));
-      const float u0 = v[1] * ifl, u1 = v[2] * ifl, u2 = v[3] * ifl;
-      const float un = u0 * n0 + u1 * n1 + u2 * n2;
-      const float a = 0.5f * (1.0f - chi), bb = 0.5f * (3.0f * chi - 1.0f) * un;
-      P[0] = v[0] * (a * n0 + bb * u0);
-      P[1] = v[0] * (a * n1 + bb * u1);
-      P[2] = v[0] * (a * n2 + bb * u2);
-    } else {
-      const float t = v[0] * (1.0f / 3.0f);
-      P[0] = t * n0; P[1] = t * n1; P[2] = t * n2;
-    }
+    const bool has_f = fl2 > 0.0f;
+    const float ifl = has_f ? rsqrtf(fl2) : 0.0f;
+    const float f = has_f ? fminf(fl2 * ifl * rcp_approx(v[0]), 1.0f) : 0.0f;
+    const float f2 = f * f;
+    const float t = 4.0f - 3.0f * f2;
+    const float chi = (3.0f + 4.0f * f2) * rcp_approx(5.0f + 2.0f * (t * rsqrtf(t)));
+    const float u0 = v[1] * ifl, u1 = v[2] * ifl, u2 = v[3] * ifl;
+    const float un = u0 * n0 + u1 * n1 + u2 * n2;
+    const float a = 0.5f * (1.0f - chi), bb = 0.5f * (3.0f * chi - 1.0f) * un;
+    P[0] = v[0] * (a * n0 + bb * u0);
+    P[1] = v[0] * (a * n1 + bb * u1);
+    P[2] = v[0] * (a * n2 + bb * u2);
     return;
   }
   R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
@@ -373,7 +527,7 @@ __global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict_
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
   if (t >= g.F * B) return;
-  const int f = t / B, b = t % B;
+  const int f = divb(t, g.divB), b = t - f * B;
   const int2 c = __ldg(g.lr + f);
   const R4<R> nA = ld4<R>(g.nA + f);
   R vL[4], vR[4], PL[3], PR[3];
@@ -403,6 +557,7 @@ __global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict_
 
 struct CellArgs {
   int C, B;
+  DivB divB;               // division by B
   const int32_t* off;
   const int32_t* csr;
   const double* vol;       // V_i (L_u^3)
@@ -439,7 +594,7 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = a.B;
   if (t >= a.C * B) return;
-  const int i = t / B, b = t % B;
+  const int i = divb(t, a.divB), b = t - i * B;
   const int k0 = a.off[i], k1 = a.off[i + 1];
   double acc[4];
   if (Comp) {
@@ -506,50 +661,95 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
 
 // Sources and thermochemistry, one thread per cell (Eq. E source term,
 // Sec. 2.3.1, 4.1.1).  Writes the FP32 shadow of the radiation if given.
+// Fast (mixed precision): the attempts carry N and the gas only; the flux is
+// read at the end and scaled by the product of the accepted photon factors.
 template <bool Fast>
 __global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* __restrict__ shadow) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.C) return;
   const int B = a.B;
-  CellState s;
+  const size_t C = a.C;
+  if constexpr (Fast) {
+    GasState s;
+    double S[kMaxBins];
 #pragma unroll
-  for (int b = 0; b < kMaxBins; ++b) {
-    if (b < B) {
-      d4 v = a.rad[(size_t)i * B + b];
-      s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
+    for (int b = 0; b < kMaxBins; ++b) {
+      S[b] = 1.0;
+      if (b < B) s.N[b] = a.rad[(size_t)i * B + b].x;
     }
-  }
-  if (a.do_inject) {
-    const int si = a.src_idx[i];
-    if (si >= 0) {
-      const double vcm3 = a.vol[i] * a.lu3;
+    if (a.do_inject) {
+      const int si = a.src_idx[i];
+      if (si >= 0) {
+        const double vcm3 = a.vol[i] * a.lu3;
 #pragma unroll
-      for (int b = 0; b < kMaxBins; ++b)
-        if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+        for (int b = 0; b < kMaxBins; ++b)
+          if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+      }
     }
-  }
-  if (a.do_chem) {
-    const size_t C = a.C;
-    s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
-    s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
-    bool capped;
-    int n = chemistry<Fast>(P, a.nH[i], a.dt, s, &capped);
-    a.nsub[i] = n;
-    if (capped) atomicOr(a.status, kStChemSubsteps);
-    a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
-    a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
-  }
-  bool bad = false;
+    if (a.do_chem) {
+      s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+      s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+      bool capped;
+      const int n = chemistry_mixed(P, a.nH[i], a.dt, s, S, &capped);
+      a.nsub[i] = n;
+      if (capped) atomicOr(a.status, kStChemSubsteps);
+      a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
+      a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+    }
+    bool bad = false;
 #pragma unroll
-  for (int b = 0; b < kMaxBins; ++b) {
-    if (b < B) {
-      a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
-      if (!isfinite(s.N[b])) bad = true;
-      if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(s.N[b]), d2f_int(s.f[b][0]), d2f_int(s.f[b][1]),
-                                                          d2f_int(s.f[b][2]));
+    for (int b = 0; b < kMaxBins; ++b) {
+      if (b < B) {
+        d4* r = a.rad + (size_t)i * B + b;
+        const d4 u = *r;
+        const d4 o = make_d4(s.N[b], u.y * S[b], u.z * S[b], u.w * S[b]);
+        *r = o;
+        if (!isfinite(o.x)) bad = true;
+        if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(o.x), d2f_int(o.y), d2f_int(o.z), d2f_int(o.w));
+      }
     }
+    if (bad) atomicOr(a.status, kStNonFinite);
+    return;
+  } else {
+    CellState s;
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) {
+      if (b < B) {
+        d4 v = a.rad[(size_t)i * B + b];
+        s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
+      }
+    }
+    if (a.do_inject) {
+      const int si = a.src_idx[i];
+      if (si >= 0) {
+        const double vcm3 = a.vol[i] * a.lu3;
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b)
+          if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+      }
+    }
+    if (a.do_chem) {
+      s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+      s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+      bool capped;
+      const int n = chemistry(P, a.nH[i], a.dt, s, &capped);
+      a.nsub[i] = n;
+      if (capped) atomicOr(a.status, kStChemSubsteps);
+      a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
+      a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int b = 0; b < kMaxBins; ++b) {
+      if (b < B) {
+        a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
+        if (!isfinite(s.N[b])) bad = true;
+        if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(s.N[b]), d2f_int(s.f[b][0]), d2f_int(s.f[b][1]),
+                                                            d2f_int(s.f[b][2]));
+      }
+    }
+    if (bad) atomicOr(a.status, kStNonFinite);
   }
-  if (bad) atomicOr(a.status, kStNonFinite);
 }
 
 }  // namespace m1rt

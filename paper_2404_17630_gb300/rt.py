@@ -17,12 +17,14 @@ import numpy as np
 
 from . import _build
 
-RT_OK, RT_INVALID_ARG, RT_BAD_MESH, RT_CFL, RT_CHEM_SUBSTEPS, RT_NONFINITE, RT_OOM, RT_CUDA, RT_NOT_READY = range(9)
+RT_OK, RT_INVALID_ARG, RT_BAD_MESH, RT_CFL, RT_CHEM_SUBSTEPS, RT_NONFINITE, RT_OOM, RT_CUDA, RT_NOT_READY, RT_TIMEOUT = \
+    range(10)
 RT_FP64, RT_MIXED = 0, 1
 RT_FIELD_N, RT_FIELD_F, RT_FIELD_X, RT_FIELD_T, RT_FIELD_NSUB = 1, 2, 4, 8, 16
 
 STATUS_NAMES = {0: "RT_OK", 1: "RT_INVALID_ARG", 2: "RT_BAD_MESH", 3: "RT_CFL", 4: "RT_CHEM_SUBSTEPS",
-                5: "RT_NONFINITE", 6: "RT_OOM", 7: "RT_CUDA", 8: "RT_NOT_READY"}
+                5: "RT_NONFINITE", 6: "RT_OOM", 7: "RT_CUDA", 8: "RT_NOT_READY",
+                9: "RT_TIMEOUT"}
 
 
 class RTError(RuntimeError):
