@@ -109,11 +109,12 @@ rt_status check_config(const rt_config* c) {
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
   return Geo<double>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
-                     (const d4*)c->hw, (const d4*)c->hx};
+                     (const d4*)c->hw, (const d4*)c->hx, nullptr, nullptr, c->B};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
-  return Geo<float>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA32, c->rL32, c->rR32, c->w32, c->minv32,
-                    (const float4*)c->hw, (const float4*)c->hx};
+  // the FP32 sweep reads faces through fa / fb; no per-array face copies
+  return Geo<float>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, nullptr, nullptr, nullptr, nullptr,
+                    c->minv32, (const float4*)c->hw, (const float4*)c->hx, c->fa32, c->fb32, pad_bins(c->B)};
 }
 
 ChemParams chem_params(const rt_ctx* ctx) {
@@ -141,7 +142,7 @@ ChemParams chem_params(const rt_ctx* ctx) {
 
 CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
   CellArgs a;
-  a.C = ctx->C; a.B = ctx->B; a.divB = make_divb(ctx->B); a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.rad = ctx->rad;
+  a.C = ctx->C; a.B = ctx->B; a.divB = make_divb(ctx->B); a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.ivol = ctx->ivol; a.rad = ctx->rad;
   a.nH = ctx->nH; a.x5 = ctx->x5; a.T = ctx->T; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
   a.nsub = ctx->nsub; a.status = ctx->status;
   a.lam = ctx->cfg.c_red * dt / ctx->cfg.unit_length_cm;
@@ -370,7 +371,8 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   const size_t rs = mx ? 4 : 8;
   {
     void* p;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>((size_t)C * B * 12 * rs, 1));
+    const size_t gbytes = mx ? (size_t)C * 4 * pad_bins(B) * sizeof(float4) : (size_t)C * B * 12 * sizeof(double);
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(gbytes, 1));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "G");
     ctx->allocs.push_back(p); ctx->G = p;
     e = cudaMalloc(&p, std::max<size_t>((size_t)F * B * 4 * rs, 1));
@@ -383,7 +385,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     }
   }
   if (mx) {
-    AL(ctx->nA32, F); AL(ctx->rL32, F); AL(ctx->rR32, F); AL(ctx->w32, F); AL(ctx->minv32, 6 * (size_t)C);
+    AL(ctx->fa32, F); AL(ctx->fb32, F); AL(ctx->minv32, 6 * (size_t)C); AL(ctx->ivol, C);
     AL(ctx->shadow, (size_t)C * B);
   }
 #undef AL
@@ -420,12 +422,13 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   k_geometry_cells<<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->cfg.box, ctx->off, ctx->csr, ctx->lr, ctx->cx,
                                                           ctx->cy, ctx->cz, sA, ctx->minv64, ctx->status);
   if (mx && F > 0) {
-    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->nA64, ctx->nA32);
-    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->rL64, ctx->rL32);
-    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->rR64, ctx->rR32);
-    k_convert4<float><<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->w64, ctx->w32);
+    k_build_facerecs<<<nblk(F), kThreads, 0, ctx->stream>>>(F, ctx->lr, ctx->nA64, ctx->rL64, ctx->rR64, ctx->fa32,
+                                                            ctx->fb32);
   }
-  if (mx) k_convert<float><<<nblk(6LL * C), kThreads, 0, ctx->stream>>>(6 * C, ctx->minv64, ctx->minv32);
+  if (mx) {
+    k_convert<float><<<nblk(6LL * C), kThreads, 0, ctx->stream>>>(6 * C, ctx->minv64, ctx->minv32);
+    k_reciprocal<<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->vol, ctx->ivol);
+  }
   if (F > 0) {
     if (mx)
       k_build_halfedges<float><<<nblk(2LL * F), kThreads, 0, ctx->stream>>>(
@@ -629,11 +632,20 @@ rt_status rt_stage_gradients(rt_ctx* ctx, double* G) {
   if (!G) return RT_OK;
   const size_t n = (size_t)ctx->C * ctx->B * 12;
   if (mixed(ctx)) {
-    // widen in a host buffer
-    std::vector<float> h(n);
-    CK(cudaMemcpyAsync(h.data(), ctx->G, n * 4, cudaMemcpyDeviceToHost, ctx->stream), "gradients");
+    // widen the gradient groups of the cell-major records in a host buffer
+    const int Bp = pad_bins(ctx->B);
+    std::vector<float4> h((size_t)ctx->C * 4 * Bp);
+    CK(cudaMemcpyAsync(h.data(), ctx->G, h.size() * sizeof(float4), cudaMemcpyDeviceToHost, ctx->stream),
+       "gradients");
     CK(cudaStreamSynchronize(ctx->stream), "gradients");
-    std::vector<double> d(h.begin(), h.end());
+    std::vector<double> d(n);
+    for (int i = 0; i < ctx->C; ++i)
+      for (int b = 0; b < ctx->B; ++b)
+        for (int v = 0; v < 3; ++v) {
+          const float4 q = h[grec(i, v, b, Bp)];
+          double* o = d.data() + ((size_t)i * ctx->B + b) * 12 + 4 * v;
+          o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+        }
     if (is_device_ptr(G)) {
       CK(cudaMemcpy(G, d.data(), n * 8, cudaMemcpyHostToDevice), "gradients");
     } else {
@@ -650,10 +662,23 @@ rt_status rt_stage_fluxes(rt_ctx* ctx, const double* G, double* flux) {
   const size_t nG = (size_t)ctx->C * ctx->B * 12, nF = (size_t)ctx->F * ctx->B * 4;
   if (G) {
     if (mixed(ctx)) {
+      // cell-major records: the given gradients, then the FP32 cell state
+      const size_t nr = (size_t)ctx->C * ctx->B;
+      const int Bp = pad_bins(ctx->B);
       std::vector<double> d(nG);
       CK(cudaMemcpy(d.data(), G, nG * 8, is_device_ptr(G) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "G");
-      std::vector<float> h(d.begin(), d.end());
-      CK(cudaMemcpy(ctx->G, h.data(), nG * 4, cudaMemcpyHostToDevice), "G");
+      std::vector<float4> sh(nr);
+      CK(cudaMemcpy(sh.data(), ctx->shadow, nr * sizeof(float4), cudaMemcpyDeviceToHost), "G");
+      std::vector<float4> h((size_t)ctx->C * 4 * Bp, make_float4(0.f, 0.f, 0.f, 0.f));
+      for (int i = 0; i < ctx->C; ++i)
+        for (int b = 0; b < ctx->B; ++b) {
+          const double* q = d.data() + ((size_t)i * ctx->B + b) * 12;
+          for (int v = 0; v < 3; ++v)
+            h[grec(i, v, b, Bp)] = make_float4((float)q[4 * v], (float)q[4 * v + 1], (float)q[4 * v + 2],
+                                               (float)q[4 * v + 3]);
+          h[grec(i, 3, b, Bp)] = sh[(size_t)i * ctx->B + b];
+        }
+      CK(cudaMemcpy(ctx->G, h.data(), h.size() * sizeof(float4), cudaMemcpyHostToDevice), "G");
     } else if ((st = copy_in(ctx, ctx->G, G, nG * 8))) {
       return st;
     }

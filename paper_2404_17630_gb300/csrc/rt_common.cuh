@@ -132,6 +132,34 @@ __device__ __forceinline__ int divb(int n, DivB q) {
   return (int)(((unsigned long long)(unsigned)n * q.m) >> q.s);
 }
 
+// Eight floats in one 32-byte aligned record, moved by one 256-bit access.
+struct __align__(32) f8 {
+  float v[8];
+};
+__device__ __forceinline__ f8 ld8(const f8* p) {
+  f8 r;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+        "=f"(r.v[7])
+      : "l"(p));
+  return r;
+}
+__device__ __forceinline__ void st8(f8* p, float a0, float a1, float a2, float a3, float a4, float a5, float a6,
+                                    float a7) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2),
+               "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+               : "memory");
+}
+
+// Gradient records.  FP64 sweep: 12 words per (cell, bin), component q's
+// gradient at q*3 + d.  FP32 sweep, cell-major: per cell four groups -- the
+// 12 gradient words as three float4, then the cell state (N, f) the
+// gradients were taken of -- each group holding the bins side by side, with
+// 3 bins padded to 4 so that a group is one aligned 64-byte block: a face
+// kernel load then touches one cache line per cell.
+__host__ __device__ constexpr int pad_bins(int B) { return B == 3 ? 4 : B; }
+__host__ __device__ inline size_t grec(int i, int g, int b, int Bp) { return ((size_t)i * 4 + g) * Bp + b; }
+
 // Mesh geometry in the sweep precision R, plus FP64 cell data.
 template <class R> struct Geo {
   int C, F, B;
@@ -147,6 +175,9 @@ template <class R> struct Geo {
   const R* minv;          // 6C: symmetric inverse of sum A n n^T (xx, xy, xz, yy, yz, zz)
   const R4<R>* hw;        // 2F half-edges in CSR order: (+-w of the face, sign + for the left cell; neighbour id bits)
   const R4<R>* hx;        // 2F half-edges in CSR order: x_f - s of this cell's side
+  const f8* fa;           // FP32 sweep, F: (n, A, x_f - s_L, left id bits)
+  const float4* fb;       // FP32 sweep, F: (x_f - s_R, right id bits)
+  int Bp;                 // FP32 gradient records: bins per group (pad_bins(B))
 };
 
 // Cell id stored in the fourth lane of a half-edge record (bit copy).

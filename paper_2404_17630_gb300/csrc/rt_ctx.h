@@ -8,6 +8,7 @@
 #include "rt_common.cuh"
 
 using m1rt::d4;
+using m1rt::f8;
 
 struct rt_ctx {
   rt_config cfg{};
@@ -26,7 +27,8 @@ struct rt_ctx {
   void *hw = nullptr, *hx = nullptr;   // half-edge records in the sweep precision
   double* minv64 = nullptr;
   // FP32 copies (mixed precision)
-  float4 *nA32 = nullptr, *rL32 = nullptr, *rR32 = nullptr, *w32 = nullptr;
+  f8* fa32 = nullptr;          // FP32 face records (n, A, x_f - s_L, left)
+  float4* fb32 = nullptr;      // FP32 face records (x_f - s_R, right)
   float* minv32 = nullptr;
   // state
   d4* rad = nullptr;      // master [C][B]
@@ -36,6 +38,7 @@ struct rt_ctx {
   double* src_rate = nullptr;
   int n_src_cells = 0, src_cap = 0;
   int32_t* nsub = nullptr;
+  double* ivol = nullptr;      // 1 / V (mixed-precision flux application)
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision
   void* flux = nullptr;        // [F][B] 4-vectors in sweep precision

@@ -119,6 +119,21 @@ __global__ void k_build_halfedges(int n, const int32_t* __restrict__ csr, const 
   hx[k] = b;
 }
 
+// Face records of the FP32 sweep: (n, A, x_f - s_L, left id) in 32 bytes
+// and (x_f - s_R, right id) in 16 bytes.
+__global__ void k_build_facerecs(int F, const int2* __restrict__ lr, const d4* __restrict__ nA,
+                                 const d4* __restrict__ rL, const d4* __restrict__ rR, f8* fa, float4* fb) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const int2 c = lr[f];
+  const d4 n = nA[f], a = rL[f], b = rR[f];
+  f8 o;
+  o.v[0] = (float)n.x; o.v[1] = (float)n.y; o.v[2] = (float)n.z; o.v[3] = (float)n.w;
+  o.v[4] = (float)a.x; o.v[5] = (float)a.y; o.v[6] = (float)a.z; o.v[7] = __int_as_float(c.x);
+  fa[f] = o;
+  fb[f] = make_float4((float)b.x, (float)b.y, (float)b.z, __int_as_float(c.y));
+}
+
 template <class R> __global__ void k_convert(int n, const double* __restrict__ in, R* out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) out[k] = (R)in[k];
@@ -202,13 +217,19 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   const int B = g.B;
   if (t >= g.C * B) return;
   const int i = divb(t, g.divB), b = t - i * B;
-  R* Go = G + (size_t)t * 12;
+  const R4<R> pi = ld4<R>(rad + t);
   if (order < 2) {
+    if constexpr (sizeof(R) == 4) {
+      float4* G4 = reinterpret_cast<float4*>(G);
+      for (int v = 0; v < 3; ++v) G4[grec(i, v, b, g.Bp)] = make_float4(0.f, 0.f, 0.f, 0.f);
+      G4[grec(i, 3, b, g.Bp)] = pi;
+    } else {
+      R* Go = G + (size_t)t * 12;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) Go[k] = R(0);
+      for (int k = 0; k < 12; ++k) Go[k] = R(0);
+    }
     return;
   }
-  const R4<R> pi = ld4<R>(rad + t);
   R r[4][3];
   R mx[4], mn[4];
 #pragma unroll
@@ -316,12 +337,20 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     o[3 * q + 1] = gr[q][1] * psi[q];
     o[3 * q + 2] = gr[q][2] * psi[q];
   }
-  R4<R>* G4 = reinterpret_cast<R4<R>*>(Go);
+  if constexpr (sizeof(R) == 4) {
+    float4* G4 = reinterpret_cast<float4*>(G);
+    G4[grec(i, 0, b, g.Bp)] = make_float4(o[0], o[1], o[2], o[3]);
+    G4[grec(i, 1, b, g.Bp)] = make_float4(o[4], o[5], o[6], o[7]);
+    G4[grec(i, 2, b, g.Bp)] = make_float4(o[8], o[9], o[10], o[11]);
+    G4[grec(i, 3, b, g.Bp)] = pi;
+  } else {
+    R4<R>* G4 = reinterpret_cast<R4<R>*>(G + (size_t)t * 12);
 #pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    R4<R> w;
-    w.x = o[4 * v]; w.y = o[4 * v + 1]; w.z = o[4 * v + 2]; w.w = o[4 * v + 3];
-    G4[v] = w;
+    for (int v = 0; v < 3; ++v) {
+      R4<R> w;
+      w.x = o[4 * v]; w.y = o[4 * v + 1]; w.z = o[4 * v + 2]; w.w = o[4 * v + 3];
+      G4[v] = w;
+    }
   }
 }
 
@@ -432,10 +461,11 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
       if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
     }
   }
-  float4* G4 = reinterpret_cast<float4*>(G + ((size_t)i * B + b) * 12);
-  G4[0] = make_float4(gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0], gr[1][0] * psi[1]);
-  G4[1] = make_float4(gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
-  G4[2] = make_float4(gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3], gr[3][2] * psi[3]);
+  float4* G4 = reinterpret_cast<float4*>(G);
+  G4[grec(i, 0, b, g.Bp)] = make_float4(gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0], gr[1][0] * psi[1]);
+  G4[grec(i, 1, b, g.Bp)] = make_float4(gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
+  G4[grec(i, 2, b, g.Bp)] = make_float4(gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3], gr[3][2] * psi[3]);
+  G4[grec(i, 3, b, g.Bp)] = pi;
 }
 
 // ---------------------------------------------------------------------------
@@ -470,6 +500,21 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
       R s = fl > R(0) ? v[0] / fl : R(0);
       v[1] *= s; v[2] *= s; v[3] *= s;
     }
+  }
+}
+
+// The same extrapolation from the four groups of an FP32 gradient record:
+// component q's gradient at words 3q..3q+2, the cell state at words 12..15.
+__device__ __forceinline__ void face_state_rec(const float4 r[4], float x0, float x1, float x2, float v[4]) {
+  const float w[16] = {r[0].x, r[0].y, r[0].z, r[0].w, r[1].x, r[1].y, r[1].z, r[1].w,
+                       r[2].x, r[2].y, r[2].z, r[2].w, r[3].x, r[3].y, r[3].z, r[3].w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = w[12 + q] + (w[3 * q] * x0 + w[3 * q + 1] * x1 + w[3 * q + 2] * x2);
+  if (v[0] < 0.0f) v[0] = 0.0f;
+  const float fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (fl2 > v[0] * v[0]) {
+    const float s = v[0] * rsqrtf(fl2);
+    v[1] *= s; v[2] *= s; v[3] *= s;
   }
 }
 
@@ -528,6 +573,34 @@ __global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict_
   const int B = g.B;
   if (t >= g.F * B) return;
   const int f = divb(t, g.divB), b = t - f * B;
+  if constexpr (sizeof(R) == 4) {
+    // FP32 sweep: one 32-byte and one 16-byte face record, then the four
+    // groups (gradients, state) of each side's cell-major record
+    const f8 a = ld8(g.fa + f);
+    const float4 xr = __ldg(g.fb + f);
+    const float4* G4 = reinterpret_cast<const float4*>(G);
+    const int cL = __float_as_int(a.v[7]), cR = __float_as_int(xr.w), Bp = g.Bp;
+    float4 l[4], r[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) l[v] = __ldg(G4 + grec(cL, v, b, Bp));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) r[v] = __ldg(G4 + grec(cR, v, b, Bp));
+    float vL[4], vR[4], PL[3], PR[3];
+    face_state_rec(l, a.v[4], a.v[5], a.v[6], vL);
+    face_state_rec(r, xr.x, xr.y, xr.z, vR);
+    const float n0 = a.v[0], n1 = a.v[1], n2 = a.v[2], A = a.v[3];
+    m1_normal<float>(vL, n0, n1, n2, PL);
+    m1_normal<float>(vR, n0, n1, n2, PR);
+    const float h = 0.5f;
+    const float fn = h * ((vL[1] + vR[1]) * n0 + (vL[2] + vR[2]) * n1 + (vL[3] + vR[3]) * n2);
+    float4 o;
+    o.x = A * (fn - h * (vR[0] - vL[0]));
+    o.y = A * (h * (PL[0] + PR[0]) - h * (vR[1] - vL[1]));
+    o.z = A * (h * (PL[1] + PR[1]) - h * (vR[2] - vL[2]));
+    o.w = A * (h * (PL[2] + PR[2]) - h * (vR[3] - vL[3]));
+    flux[t] = o;
+    return;
+  }
   const int2 c = __ldg(g.lr + f);
   const R4<R> nA = ld4<R>(g.nA + f);
   R vL[4], vR[4], PL[3], PR[3];
@@ -561,6 +634,7 @@ struct CellArgs {
   const int32_t* off;
   const int32_t* csr;
   const double* vol;       // V_i (L_u^3)
+  const double* ivol;      // 1 / V_i (mixed precision only)
   d4* rad;            // master radiation (FP64)
   double* nH;
   double* x5;              // 5*C
@@ -648,7 +722,9 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
       add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
     }
   }
-  const double kfac = a.lam / a.vol[i];
+  // FP32 sweep: lam (1/V) with 1/V formed once per mesh (one FP64 multiply
+  // instead of a division per subcycle); the FP64 sweep divides as defined
+  const double kfac = sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
   d4 u = a.rad[t];
   u.x -= kfac * acc[0];
   u.y -= kfac * acc[1];
@@ -657,6 +733,11 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   a.rad[t] = u;
   if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
   if (shadow) shadow[t] = make_float4(d2f_int(u.x), d2f_int(u.y), d2f_int(u.z), d2f_int(u.w));
+}
+
+__global__ void k_reciprocal(int n, const double* __restrict__ in, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = 1.0 / in[k];
 }
 
 // Sources and thermochemistry, one thread per cell (Eq. E source term,
