@@ -39,28 +39,10 @@ L2_BYTES = 129e6
 
 
 def thesan_like(n=128, seed=4, n_peaks=4096):
-    """THESAN-like box: Voronoi mesh of an n^3 jittered lattice in a periodic
-    box of 3.58 Mpc (physical, 23.3 cMpc at z = 5.5), n_H = exp(GRF) with
-    P(k) ~ k^-2, sigma 1.5, mean 2e-4 cm^-3 (128^3 FFT grid, nearest node),
-    sources at the n_peaks highest density maxima with Q = 1e49 rho/rho_min
-    clipped to 1e52 photons/s, c_red = 0.2 c."""
+    """THESAN-like box (the recipe is synth.thesan_like): 128^3 jittered
+    lattice, 3.58 Mpc, exp(GRF) density, 4096 peak sources, c_red = 0.2 c."""
     import synth
-    L = 3580.0  # kpc
-    mesh = synth.voronoi_mesh(n, L, 0.3, seed=seed)
-    C = mesh.n_cells
-    nH, rho = synth.grf_density(mesh.gen, L, 128, 1.5, 2e-4, seed + 1)
-    peaks = synth.density_peaks(rho, n_peaks)
-    pos = (peaks + 0.5) * (L / 128)
-    cells = synth.locate_cells(mesh, pos).astype(np.int64)
-    rp = rho[tuple(peaks.T)]
-    Qtot = np.minimum(1e49 * rp / rp.min(), 1e52)
-    Q = np.outer(Qtot, synth.SPECTRAL_SPLIT_E4)
-    x5 = np.zeros((5, C)); x5[0] = 1.0; x5[2] = 1.0
-    cfg = dict(n_bins=3, c_red=0.2 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L, cfl=0.3, chem_mode=2,
-               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
-               max_substeps=10000, y_he=synth.helium_ratio(0.24), sigma=synth.GREY_SIGMA, eps=synth.GREY_EPS)
-    state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q)
-    return mesh, cfg, state
+    return synth.thesan_like(n, seed, n_peaks)
 
 
 def differentiable(n=64, seed=7, n_src=8):
@@ -332,7 +314,7 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
 # FP64 work of one chemistry attempt of the mixed path (2 x DFMA + DMUL + DADD
 # thread instructions, from ncu on the 2e5-cell workload in steady state,
 # one attempt per cell): the unit count behind k_chem's ALU roofline.
-FP64_FLOP_PER_ATTEMPT = {"mixed": 292.0, "fp64": None}  # re-measured after each change of k_chem
+FP64_FLOP_PER_ATTEMPT = {"mixed": 250.0, "fp64": None}  # re-measured after each change of k_chem
 # GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
 # clock per SM (ncu: 16 cycles per warp instruction on the FP64 pipe) x 2 FLOP
 # x 2.07 GHz = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s.
@@ -434,8 +416,24 @@ def measure_large(steps, warmup, dev):
     peaks, kind = measured_peaks()
     f = rt.fields()
     rf, kern, rf_mem = roofline(res, "mixed", peaks, kind, attempts=float(f["nsub"].sum()))
+    # per-field error of the mixed path against the FP64 path: one step of
+    # n_sub subcycles of each from the initial state
+    fields = {}
+    for prec in ("mixed", "fp64"):
+        r2 = RT(make_config(precision=prec, gather_sum=1, **cfg), mesh, stream=stream)
+        r2.set_gas(state["nH"], state["x5"], state["T"])
+        r2.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+        r2.set_sources(state["cells"], state["Q"])
+        r2.step(dt, n_sub)
+        r2.sync()
+        fields[prec] = r2.fields()
+        del r2
+    a, b = fields["mixed"], fields["fp64"]
+    err = {k: float(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300)) for k in ("N", "F", "x5", "T")}
     return {"workload": f"THESAN-like voronoi 128^3 ({C} cells, {F} faces), GRF n_H, 4096 peak sources, "
-                        f"c_red 0.2c, {n_sub} subcycles/step, mixed", "value": C * n_sub * steps / (ms / 1e3),
+                        f"c_red 0.2c, {n_sub} subcycles/step, mixed",
+            "mixed_vs_fp64_after_one_step": {"metric": "max|mixed - fp64| / max|fp64| per field", **err},
+            "value": C * n_sub * steps / (ms / 1e3),
             "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "roofline": rf,
             "roofline_memory_kernel": rf_mem,
             "kernels": kern, "mesh_build_s": round(build_s, 1), "x_HII_mean": float(f["x5"][1].mean())}

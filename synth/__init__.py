@@ -296,3 +296,30 @@ def locate_cells(mesh: Mesh, pos: np.ndarray) -> np.ndarray:
                 better = d2 < bestd
                 best[better], bestd[better] = q[better], d2[better]
     return best
+
+
+def thesan_like(n: int = 128, seed: int = 4, n_peaks: int = 4096, L: float = 3580.0, ng: int = 128):
+    """THESAN-like reionisation box: Voronoi mesh of an n^3 jittered lattice in a
+    periodic box of L kpc (3.58 Mpc physical = 23.3 cMpc at z = 5.5 for the
+    full box), n_H = exp(GRF) with P(k) ~ k^-2, sigma 1.5, mean 2e-4 cm^-3 (ng^3
+    FFT grid, nearest node), sources at the n_peaks highest density maxima with
+    Q = 1e49 rho / rho_min clipped to 1e52 photons/s split over 3 bins, c_red =
+    0.2 c, neutral gas at 1e4 K, no radiation.  The 1/8 sub-box instance is
+    n = 64, L = 1790, ng = 64, n_peaks = 512.  Returns (mesh, cfg, state)."""
+    mesh = voronoi_mesh(n, L, 0.3, seed=seed)
+    C = mesh.n_cells
+    nH, rho = grf_density(mesh.gen, L, ng, 1.5, 2e-4, seed + 1)
+    peaks = density_peaks(rho, n_peaks)
+    pos = (peaks + 0.5) * (L / ng)
+    cells = locate_cells(mesh, pos).astype(np.int64)
+    rp = rho[tuple(peaks.T)]
+    Qtot = np.minimum(1e49 * rp / rp.min(), 1e52)
+    Q = np.outer(Qtot, SPECTRAL_SPLIT_E4)
+    x5 = np.zeros((5, C))
+    x5[0] = 1.0
+    x5[2] = 1.0
+    cfg = dict(n_bins=3, c_red=0.2 * C_LIGHT, unit_length_cm=KPC_CM, box=L, cfl=0.3, chem_mode=2,
+               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
+               max_substeps=10000, y_he=helium_ratio(0.24), sigma=GREY_SIGMA, eps=GREY_EPS)
+    state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q)
+    return mesh, cfg, state
