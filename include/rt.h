@@ -91,6 +91,12 @@ typedef struct {
   double eps[3][3];       /* heat per photoionisation [bin][species], erg */
   int gather_sum;         /* RT_MIXED only: 0 = each FP32 face flux widened and summed in FP64;
                              1 = compensated FP32 pair (error-free two_sum), widened to FP64 once per cell */
+  int splitting;          /* 0 = Lie (sources + chemistry over the subcycle, then transport; the order of
+                             Fig. overview_subcycling); 1 = Strang (sources + chemistry over half the subcycle
+                             on each side of the transport step; the symmetric split of Sec. 2.3) */
+  int time_order;         /* 1 = forward-Euler transport (no time extrapolation, Sec. 2.3.3);
+                             2 = Heun's method in SSP form: U1 = U + dt L(U), U2 = U1 + dt L(U1),
+                             U' = U/2 + U2/2 (second order in time, positive under the same CFL) */
 } rt_config;
 
 /* Cells of the static mesh (structure of arrays, n entries each). */
@@ -160,14 +166,17 @@ rt_status rt_mesh_info(rt_ctx *ctx, int64_t *n_cells, int64_t *n_faces, int32_t 
  *    G[((i*B + b)*4 + q)*3 + d] (q: N, F_x/c, F_y/c, F_z/c; d: x, y, z), per L_u;
  *  rt_stage_fluxes: from G (or, if G is NULL, from freshly computed
  *    gradients) the face fluxes A_f * Phi / c_red into flux[(f*B + b)*4 + q];
- *  rt_stage_transport: gradients, fluxes and their application over dt;
+ *  rt_stage_transport: gradients, fluxes and their application over dt
+ *    (both Heun stages when time_order is 2);
  *  rt_stage_chemistry: source injection and thermochemistry over dt. */
 rt_status rt_stage_gradients(rt_ctx *ctx, double *G);
 rt_status rt_stage_fluxes(rt_ctx *ctx, const double *G, double *flux);
 rt_status rt_stage_transport(rt_ctx *ctx, double dt);
 rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
 
-/* Reverse mode of rt_step(dt, n_sub), FP64 precision, chem_mode 0 or 1.
+/* Reverse mode of rt_step(dt, n_sub), FP64 precision, chem_mode 0 or 1,
+ * Lie splitting and forward-Euler transport (other configurations return
+ * RT_INVALID_ARG).
  * The paper has no adjoint; this is the exact derivative of the discrete
  * forward map (sources, every chemistry attempt with the substep controller
  * of Sec. 4.1.1, gradients and limiter on their active branch, M1 face

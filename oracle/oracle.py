@@ -34,6 +34,8 @@ class OracleConfig(ctypes.Structure):
         ("y_he", ctypes.c_double),
         ("sigma", (ctypes.c_double * 3) * 3),
         ("eps", (ctypes.c_double * 3) * 3),
+        ("splitting", ctypes.c_int),
+        ("time_order", ctypes.c_int),
     ]
 
 
@@ -56,6 +58,8 @@ def default_config(**kw) -> OracleConfig:
     c.x_floor = 1e-4
     c.max_substeps = 10000
     c.y_he = 0.0
+    c.splitting = 0
+    c.time_order = 1
     for k, v in kw.items():
         if k in ("sigma", "eps"):
             arr = getattr(c, k)

@@ -60,6 +60,8 @@ typedef struct {
   double y_he;             /* n_He / n_H */
   double sigma[ORC_MAXB][3]; /* cross-sections [bin][HI, HeI, HeII], cm^2 */
   double eps[ORC_MAXB][3];   /* heat per photoionisation [bin][species], erg */
+  int splitting;           /* 0: Lie (chemistry, then transport); 1: Strang (half chemistry, transport, half chemistry) */
+  int time_order;          /* 1: forward Euler transport; 2: Heun (two-stage SSP Runge-Kutta) */
 } orc_config;
 
 typedef struct {
@@ -676,15 +678,48 @@ double orc_max_dt(const orc_t *o) {
  * (overview_subcycling): thermochemistry (with the source term), gradients,
  * fluxes, application.  Returns 0, ST_CFL (nothing done), ST_CHEM (a cell hit
  * the substep cap) or ST_NONFINITE. */
+/* Transport over dt with the configured time integrator.  Order 1: one
+ * forward-Euler stage (Sec. 2.3.3 disables time extrapolation, so the
+ * reconstruction is from the cell values at the start).  Order 2: Heun's
+ * method in its strong-stability-preserving form, U1 = U + dt L(U),
+ * U2 = U1 + dt L(U1), U' = U/2 + U2/2, a convex combination of Euler
+ * stages and so positive under the same Courant limit. */
+static void transport_step(orc_t *o, double dt) {
+  if (o->cfg.time_order != 2) {
+    orc_transport(o, dt);
+    return;
+  }
+  const int64_t nN = (int64_t)o->cfg.n_bins * o->C, nF = 3 * nN;
+  double *N0 = malloc(nN * sizeof(double)), *F0 = malloc(nF * sizeof(double));
+  memcpy(N0, o->N, nN * sizeof(double));
+  memcpy(F0, o->fr, nF * sizeof(double));
+  orc_transport(o, dt);
+  orc_transport(o, dt);
+  for (int64_t k = 0; k < nN; ++k) o->N[k] = 0.5 * N0[k] + 0.5 * o->N[k];
+  for (int64_t k = 0; k < nF; ++k) o->fr[k] = 0.5 * F0[k] + 0.5 * o->fr[k];
+  free(N0);
+  free(F0);
+}
+
 int orc_step(orc_t *o, double dt, int n_sub) {
   if (n_sub < 1) return 1;
   double dts = dt / n_sub;
   if (dts > orc_max_dt(o) * (1.0 + 1e-12)) return ST_CFL;  /* ulp slack for dt = n * dt_max / n */
   int st = ST_OK;
   for (int s = 0; s < n_sub; ++s) {
-    int c = thermochemistry(o, dts);
-    if (c) st = c;
-    orc_transport(o, dts);
+    if (o->cfg.splitting == 1) {
+      /* Strang: sources and thermochemistry over dt/2 on each side of the
+       * transport step (the paper's symmetric operator split) */
+      int c = thermochemistry(o, 0.5 * dts);
+      if (c) st = c;
+      transport_step(o, dts);
+      c = thermochemistry(o, 0.5 * dts);
+      if (c) st = c;
+    } else {
+      int c = thermochemistry(o, dts);
+      if (c) st = c;
+      transport_step(o, dts);
+    }
   }
   for (int64_t k = 0; k < 4 * o->cfg.n_bins * o->C; ++k) {
     double v = k < o->cfg.n_bins * o->C ? o->N[k] : o->fr[k - o->cfg.n_bins * o->C];
@@ -1157,7 +1192,8 @@ static int chemistry_cell_vjp(orc_t *o, int64_t i, double dt_sub, const double *
  */
 int orc_adjoint(orc_t *o, double dt, int n_sub, double *lN, double *lfr, double *lx5, double *lT, double *g_src,
                 double *g_nH) {
-  if (n_sub < 1 || o->cfg.chem_mode == 2) return 1;
+  /* reverse mode of the Lie / forward-Euler subcycle with the isothermal network */
+  if (n_sub < 1 || o->cfg.chem_mode == 2 || o->cfg.splitting != 0 || o->cfg.time_order == 2) return 1;
   const double dts = dt / n_sub;
   if (dts > orc_max_dt(o) * (1.0 + 1e-12)) return ST_CFL;
   const int B = o->cfg.n_bins, nv = 4 * B + 6;

@@ -103,6 +103,8 @@ rt_status check_config(const rt_config* c) {
     return fail(nullptr, RT_INVALID_ARG, "bad substep parameters");
   if (c->y_he < 0 || c->lim_eps < 0) return fail(nullptr, RT_INVALID_ARG, "y_he and lim_eps must be >= 0");
   if (c->gather_sum < 0 || c->gather_sum > 1) return fail(nullptr, RT_INVALID_ARG, "gather_sum must be 0 or 1");
+  if (c->splitting < 0 || c->splitting > 1) return fail(nullptr, RT_INVALID_ARG, "splitting must be 0 or 1");
+  if (c->time_order < 1 || c->time_order > 2) return fail(nullptr, RT_INVALID_ARG, "time_order must be 1 or 2");
   return RT_OK;
 }
 
@@ -152,6 +154,8 @@ CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
   a.do_gather = gather;
   a.do_inject = inject && ctx->n_src_cells > 0;
   a.do_chem = chem && ctx->cfg.chem_mode > 0;
+  a.rad0 = nullptr;
+  a.heun = 0;
   return a;
 }
 
@@ -210,9 +214,13 @@ template <class R> void launch_flux(rt_ctx* ctx) {
                                                                             (const R*)ctx->G, (R4<R>*)ctx->flux);
 }
 
-void launch_gather(rt_ctx* ctx, double dt) {
+// stage: 0 plain update; 1 also keeps the input state in rad0 (first Heun
+// stage); 2 forms U/2 + U2/2 with the state kept in rad0 (second stage)
+void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
   ProfScope ps(ctx, RT_KERNEL_GATHER);
   CellArgs a = cell_args(ctx, dt, 1, 0, 0);
+  a.rad0 = ctx->rad0;
+  a.heun = stage;
   const long long n = (long long)ctx->C * ctx->B;
   if (mixed(ctx) && comp_sum(ctx))
     k_gather<float, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
@@ -233,6 +241,20 @@ void launch_chem(rt_ctx* ctx, double dt) {
 
 void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
 void launch_flux_any(rt_ctx* ctx) { mixed(ctx) ? launch_flux<float>(ctx) : launch_flux<double>(ctx); }
+
+// Transport over dt with the configured integrator: one forward-Euler
+// stage, or Heun's two stages with the combination fused into the second
+// flux application.
+void transport(rt_ctx* ctx, double dt) {
+  const bool heun = ctx->cfg.time_order == 2;
+  launch_grad_any(ctx);
+  launch_flux_any(ctx);
+  launch_gather(ctx, dt, heun ? 1 : 0);
+  if (!heun) return;
+  launch_grad_any(ctx);
+  launch_flux_any(ctx);
+  launch_gather(ctx, dt, 2);
+}
 
 void refresh_shadow(rt_ctx* ctx) {
   if (!mixed(ctx)) return;
@@ -362,6 +384,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   AL(ctx->vol, C); AL(ctx->cx, C); AL(ctx->cy, C); AL(ctx->cz, C);
   AL(ctx->off, C + 1); AL(ctx->csr, 2 * (size_t)F); AL(ctx->nbr, 2 * (size_t)F); AL(ctx->lr, F);
   AL(ctx->nA64, F); AL(ctx->rL64, F); AL(ctx->rR64, F); AL(ctx->w64, F); AL(ctx->minv64, 6 * (size_t)C);
+  if (ctx->cfg.time_order == 2) AL(ctx->rad0, (size_t)C * B);
   AL(ctx->rad, (size_t)C * B); AL(ctx->nH, C); AL(ctx->x5, 5 * (size_t)C); AL(ctx->T, C);
   AL(ctx->src_idx, C); AL(ctx->nsub, C); AL(ctx->status, 1);
   ctx->stage_n = std::max<size_t>(4 * (size_t)B * C, 7 * (size_t)F);
@@ -557,12 +580,13 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   const double dmax = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
   if (dts > dmax * (1.0 + 1e-12))
     return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
-  // Subcycle: sources + chemistry, gradients, fluxes, application.
+  // Subcycle: sources + chemistry, gradients, fluxes, application (Lie);
+  // Strang puts half the chemistry on each side of the transport.
+  const bool strang = ctx->cfg.splitting == 1;
   for (int s = 0; s < n_sub; ++s) {
-    launch_chem(ctx, dts);
-    launch_grad_any(ctx);
-    launch_flux_any(ctx);
-    launch_gather(ctx, dts);
+    launch_chem(ctx, strang ? 0.5 * dts : dts);
+    transport(ctx, dts);
+    if (strang) launch_chem(ctx, 0.5 * dts);
   }
   return launched(ctx, "rt_step");
 }
@@ -704,9 +728,7 @@ rt_status rt_stage_transport(rt_ctx* ctx, double dt) {
   rt_status st = need_mesh(ctx);
   if (st) return st;
   if (!(dt >= 0)) return fail(ctx, RT_INVALID_ARG, "dt must be >= 0");
-  launch_grad_any(ctx);
-  launch_flux_any(ctx);
-  launch_gather(ctx, dt);
+  transport(ctx, dt);
   return launched(ctx, "transport");
 }
 
@@ -892,8 +914,9 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
                      double* dL_dnH, double* lam0_N, double* lam0_F, double* lam0_x5, double* lam0_T) {
   rt_status st = need_mesh(ctx);
   if (st) return st;
-  if (mixed(ctx) || ctx->cfg.chem_mode == 2)
-    return fail(ctx, RT_INVALID_ARG, "rt_adjoint supports FP64 precision with chem_mode 0 or 1");
+  if (mixed(ctx) || ctx->cfg.chem_mode == 2 || ctx->cfg.splitting != 0 || ctx->cfg.time_order != 1)
+    return fail(ctx, RT_INVALID_ARG,
+                "rt_adjoint supports FP64 precision, chem_mode 0 or 1, Lie splitting and forward-Euler transport");
   if (n_sub < 1 || !(dt > 0) || !std::isfinite(dt) || checkpoint_every < 1)
     return fail(ctx, RT_INVALID_ARG, "need dt > 0, n_sub >= 1, checkpoint_every >= 1");
   const double dts = dt / n_sub;

@@ -38,6 +38,7 @@ struct rt_ctx {
   double* src_rate = nullptr;
   int n_src_cells = 0, src_cap = 0;
   int32_t* nsub = nullptr;
+  d4* rad0 = nullptr;          // state at the start of a Heun transport step (time_order 2)
   double* ivol = nullptr;      // 1 / V (mixed-precision flux application)
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision

@@ -643,6 +643,8 @@ struct CellArgs {
   const double* src_rate;  // [n_src_cells][B] photons/s
   int32_t* nsub;           // C
   int* status;
+  d4* rad0;                // Heun: the state at the start of the transport step
+  int heun;                // 0 plain; 1 keep the input in rad0; 2 write rad0/2 + (updated)/2
   double lam;              // c_red dt / unit_length_cm
   double dt;
   double lu3;              // unit_length_cm^3
@@ -726,10 +728,18 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   // instead of a division per subcycle); the FP64 sweep divides as defined
   const double kfac = sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
   d4 u = a.rad[t];
+  if (a.heun == 1) a.rad0[t] = u;
   u.x -= kfac * acc[0];
   u.y -= kfac * acc[1];
   u.z -= kfac * acc[2];
   u.w -= kfac * acc[3];
+  if (a.heun == 2) {
+    const d4 u0 = a.rad0[t];
+    u.x = 0.5 * u0.x + 0.5 * u.x;
+    u.y = 0.5 * u0.y + 0.5 * u.y;
+    u.z = 0.5 * u0.z + 0.5 * u.z;
+    u.w = 0.5 * u0.w + 0.5 * u.w;
+  }
   a.rad[t] = u;
   if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
   if (shadow) shadow[t] = make_float4(d2f_int(u.x), d2f_int(u.y), d2f_int(u.z), d2f_int(u.w));

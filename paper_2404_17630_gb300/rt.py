@@ -54,6 +54,8 @@ class rt_config(ctypes.Structure):
         ("sigma", (ctypes.c_double * 3) * 3),
         ("eps", (ctypes.c_double * 3) * 3),
         ("gather_sum", ctypes.c_int),
+        ("splitting", ctypes.c_int),
+        ("time_order", ctypes.c_int),
     ]
 
 
@@ -72,7 +74,8 @@ def make_config(**kw) -> rt_config:
     c = rt_config()
     defaults = dict(n_bins=3, precision=RT_FP64, c_red=0.01 * 2.99792458e10, unit_length_cm=3.0856775814913673e21,
                     box=0.0, cfl=0.3, chem_mode=2, chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05,
-                    f_max=0.1, x_floor=1e-4, max_substeps=10000, y_he=0.0, gather_sum=0)
+                    f_max=0.1, x_floor=1e-4, max_substeps=10000, y_he=0.0, gather_sum=0,
+                    splitting=0, time_order=1)
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("sigma", "eps"):

@@ -151,9 +151,33 @@ def test_voronoi_2e5_one_subcycle_fp64():
     compare_state(rt, o, TOL64)
 
 
+@pytest.mark.parametrize("splitting,time_order", [(1, 1), (0, 2), (1, 2)])
+def test_step_variants_fp64(splitting, time_order):
+    """Strang splitting and Heun transport (second order in time), with
+    sources and the full thermal network: whole steps at 1e-12."""
+    mesh, cfg, st = voronoi_case(n=12, n_src=4, splitting=splitting, time_order=time_order)
+    o, rt = make_oracle(mesh, cfg, st), make_gpu(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.step(3 * dt, 3) == 0
+    rt.step(3 * dt, 3)
+    assert rt.sync() == 0
+    compare_state(rt, o, TOL64)
+
+
 # ---------------------------------------------------------------------------
 # mixed precision
 # ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("splitting,time_order", [(1, 1), (0, 2), (1, 2)])
+def test_step_variants_mixed(splitting, time_order):
+    mesh, cfg, st = voronoi_case(n=12, n_src=4, splitting=splitting, time_order=time_order)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1)
+    dt = o.max_dt()
+    assert o.step(3 * dt, 3) == 0
+    rt.step(3 * dt, 3)
+    assert rt.sync() == 0
+    compare_state(rt, o, 1e-4)
 
 @pytest.mark.parametrize("gather_sum", [0, 1])
 def test_mixed_step_errors(gather_sum):

@@ -265,6 +265,82 @@ def test_photon_conservation_with_absorption_no_recombination():
     np.testing.assert_allclose(x5[2] + x5[3] + x5[4], 1, atol=1e-14)
 
 
+@pytest.mark.parametrize("splitting,time_order", [(0, 1), (1, 1), (0, 2), (1, 2)])
+def test_photon_budget_with_sources(splitting, time_order):
+    """Sources on, absorption on, recombination and collisional ionisation
+    off: every photon injected (Q dt per source, Eq. E) is either still in
+    flight or has made one free electron, so sum_i V_i (sum_b N_b + n_e)
+    grows by exactly sum_k Q_k t, for the Lie and Strang splits and for both
+    transport integrators.  A half step applied twice, or a stage weight
+    off in Heun's combination, breaks the budget."""
+    mesh, cfg, st = voronoi_case(n=10, chem_mode=1, chem_flags=0, splitting=splitting, time_order=time_order)
+    o = make_oracle(mesh, cfg, st)
+    V = mesh.volume * cfg["unit_length_cm"] ** 3
+    nH, yhe = st["nH"], cfg["y_he"]
+
+    def total():
+        N, _ = o.radiation()
+        x5, _ = o.gas()
+        ne = nH * (x5[1] + yhe * (x5[3] + 2 * x5[4]))
+        return ((N.sum(0) + ne) * V).sum()
+
+    t0 = total()
+    dt = o.max_dt()
+    assert o.step(4 * dt, 4) == 0
+    t1 = total()
+    injected = st["Q"].sum() * 4 * dt
+    assert injected > 1e-3 * t0
+    assert abs((t1 - t0) / injected - 1) < 1e-10
+
+
+def test_heun_conserves_photons_and_flux():
+    """Heun's two-stage transport keeps the antisymmetric gather's exact
+    conservation of sum N V and sum F V (its result is a convex combination
+    of conservative stages)."""
+    mesh, cfg, st = voronoi_case(n=12, chem_mode=0, time_order=2, n_src=0)
+    o = make_oracle(mesh, cfg, st)
+    V = mesh.volume
+    N0, fr0 = o.radiation()
+    dt = o.max_dt()
+    assert o.step(5 * dt, 5) == 0
+    N1, fr1 = o.radiation()
+    np.testing.assert_allclose((N1 * V).sum(1), (N0 * V).sum(1), rtol=1e-13)
+    assert np.abs((fr1 * V).sum(2) - (fr0 * V).sum(2)).max() <= 1e-13 * np.abs(fr0 * V).sum()
+    assert np.abs(N1 - N0).max() > 1e-3 * N0.max()
+
+
+def _smooth_wave_error_ratio(time_order, n0=4):
+    """Temporal convergence on a fixed mesh (limiter off, smooth field):
+    states at t = n0 dt_max from n0, 2 n0 and 4 n0 subcycles; the spatial
+    error is common to all three, so |U(n0) - U(2n0)| / |U(2n0) - U(4n0)|
+    tends to 2^p for a method of order p in time."""
+    mesh = synth.voronoi_mesh(10, 1.0, 0.2, seed=5)
+    C = mesh.n_cells
+    ph = 2 * np.pi * mesh.centroids()[:, 0]
+    N = 1.0 + 0.01 * np.sin(ph)
+    fr = np.zeros((1, 3, C))
+    fr[0, 0] = 0.5 * N
+    cfg = base_config(box=1.0, n_bins=1, c_red=1.0, unit_length_cm=1.0, chem_mode=0, limiter=0,
+                      time_order=time_order)
+    gas = dict(zip(("nH", "x5", "T"), neutral_gas(C, 1e-3)))
+    out = []
+    for k in (1, 2, 4):
+        o = make_oracle(mesh, cfg, dict(N=N[None], fr=fr, **gas))
+        t_end = n0 * o.max_dt()
+        assert o.step(t_end, n0 * k) == 0
+        out.append(o.radiation()[0][0])
+    return np.abs(out[0] - out[1]).max() / np.abs(out[1] - out[2]).max()
+
+
+def test_heun_is_second_order_in_time():
+    """Forward Euler halves its temporal error with the step (ratio 2);
+    Heun's method quarters it (ratio 4)."""
+    r1 = _smooth_wave_error_ratio(1)
+    r2 = _smooth_wave_error_ratio(2)
+    assert 1.7 < r1 < 2.4, r1
+    assert 3.4 < r2 < 4.6, r2
+
+
 # ---------------------------------------------------------------------------
 # wave and beam: transport speed c_red (Sec. 4.2.1)
 # ---------------------------------------------------------------------------
