@@ -439,6 +439,41 @@ def measure_large(steps, warmup, dev):
             "kernels": kern, "mesh_build_s": round(build_s, 1), "x_HII_mean": float(f["x5"][1].mean())}
 
 
+def measure_hii(steps, warmup, dev, n=64, n_sub=64):
+    """Mixed precision on the expanding-HII-region workload: staggered 2 x n^3
+    grid (truncated octahedra), 3 bins, 64 subcycles per step."""
+    import synth
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
+    mesh, cfg, state = synth.hii_region(n)
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision="mixed", gather_sum=1, **cfg), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dt = rt.max_dt() * n_sub
+    for _ in range(warmup):
+        rt.step(dt, n_sub)
+    rt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(steps):
+        rt.step(dt, n_sub)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    rt.sync()
+    C, F, _ = rt.mesh_info()
+    f = rt.fields()
+    return {"workload": f"expanding HII region, staggered 2x{n}^3 grid ({C} cells, {F} faces, 7 faces/cell), "
+                        f"r^-2 density, 3 bins, c_red 1e-3 c, {n_sub} subcycles/step, mixed",
+            "value": C * n_sub * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "t_Myr": (warmup + steps) * dt / 3.15576e13,
+            "ionised_volume_fraction": float((f["x5"][1] * mesh.volume).sum() / mesh.volume.sum())}
+
+
 def measure_adjoint(dev, n=64, n_sub=50, k=10):
     """FP64 forward and reverse mode on the 262k-cell differentiable workload."""
     import torch
@@ -493,6 +528,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2.1M-cell THESAN-like run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode run")
+    ap.add_argument("--no-hii", action="store_true", help="skip the expanding-HII-region run")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -534,6 +570,7 @@ def main():
     e2e = None if args.no_e2e else e2e_measure("mixed", mesh, cfg, state, max(2, args.steps // 2), args.warmup, dev)
     large = None if args.no_large else measure_large(3, 1, dev)
     adjoint = None if args.no_adjoint else measure_adjoint(dev)
+    hii = None if args.no_hii else measure_hii(3, 1, dev)
     if rank != 0:
         return
     C, F = res["C"], res["F"]
@@ -556,7 +593,7 @@ def main():
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "mixed_fp64_sums": fp64sum,
         "e2e": e2e, "cpu_baseline": cpu,
-        "thesan_like_2M": large, "adjoint": adjoint,
+        "thesan_like_2M": large, "adjoint": adjoint, "hii_region": hii,
         "gpu_launches": res["launches"], "clocks": cl,
     }
     print(json.dumps(out))

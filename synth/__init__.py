@@ -125,6 +125,71 @@ def cartesian_mesh(n: int, L: float) -> Mesh:
 
 
 # ----------------------------------------------------------------------------
+# Staggered (body-centred cubic) grid
+# ----------------------------------------------------------------------------
+
+def bcc_mesh(n: int, L: float) -> Mesh:
+    """Voronoi mesh of the staggered 2 x n^3 grid in a periodic box of side L:
+    generators on the corners (i, j, k) h and the body centres (i+1/2, j+1/2,
+    k+1/2) h of an n^3 lattice, h = L / n.  Every cell is the same truncated
+    octahedron of volume h^3 / 2: eight hexagonal faces (area 3 sqrt(3) h^2 / 16)
+    towards the nearest generators of the other sublattice at (+-1, +-1, +-1)
+    h / 2, and six square faces (area h^2 / 8) towards the next generators of
+    its own sublattice at h along each axis; each face lies on the bisector
+    plane, centred on the midpoint.  Corner cell (i, j, k) has id i + n(j + nk),
+    body-centre cell n^3 + i + n(j + nk).  Faces: the 8 n^3 hexagons listed
+    from the corner cells (left), then the 6 n^3 squares towards +x, +y, +z
+    from every cell (left)."""
+    h = L / n
+    n3 = n ** 3
+    idx = np.arange(n3, dtype=np.int64)
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+
+    def cid(a, b, c):
+        return (a % n) + n * ((b % n) + n * (c % n))
+
+    pos_a = np.stack([i * h, j * h, k * h], axis=1).astype(np.float64)
+    pos_b = pos_a + 0.5 * h
+    pos = np.concatenate([pos_a, pos_b])
+    left, right, nrm, area = [], [], [], []
+    hexa = 3.0 * np.sqrt(3.0) / 16.0 * h * h
+    for sx in (-1, 1):
+        for sy in (-1, 1):
+            for sz in (-1, 1):
+                # body-centre neighbour at (i, j, k) h + (sx, sy, sz) h / 2
+                nb = n3 + cid(i + (sx - 1) // 2, j + (sy - 1) // 2, k + (sz - 1) // 2)
+                left.append(idx)
+                right.append(nb)
+                d = np.array([sx, sy, sz], dtype=np.float64) / np.sqrt(3.0)
+                nrm.append(np.broadcast_to(d, (n3, 3)))
+                area.append(np.full(n3, hexa))
+    sq = h * h / 8.0
+    for base in (0, n3):
+        for ax in range(3):
+            step = [0, 0, 0]
+            step[ax] = 1
+            left.append(base + idx)
+            right.append(base + cid(i + step[0], j + step[1], k + step[2]))
+            d = np.zeros(3)
+            d[ax] = 1.0
+            nrm.append(np.broadcast_to(d, (n3, 3)))
+            area.append(np.full(n3, sq))
+    left = np.concatenate(left)
+    right = np.concatenate(right)
+    nrm = np.concatenate(nrm)
+    area = np.concatenate(area)
+    # face centre: midpoint of the two generators along the minimum image
+    dvec = pos[right] - pos[left]
+    dvec -= L * np.round(dvec / L)
+    fc = np.mod(pos[left] + 0.5 * dvec, L)
+    C = 2 * n3
+    return Mesh(volume=np.full(C, 0.5 * h ** 3), cx=pos[:, 0].copy(), cy=pos[:, 1].copy(), cz=pos[:, 2].copy(),
+                left=left.astype(np.int32), right=right.astype(np.int32), area=area, nx=nrm[:, 0].copy(),
+                ny=nrm[:, 1].copy(), nz=nrm[:, 2].copy(), fx=fc[:, 0].copy(), fy=fc[:, 1].copy(),
+                fz=fc[:, 2].copy(), box=float(L), gen=pos, lattice_n=0)
+
+
+# ----------------------------------------------------------------------------
 # Voronoi mesh of a jittered lattice
 # ----------------------------------------------------------------------------
 
@@ -322,4 +387,35 @@ def thesan_like(n: int = 128, seed: int = 4, n_peaks: int = 4096, L: float = 358
                chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
                max_substeps=10000, y_he=helium_ratio(0.24), sigma=GREY_SIGMA, eps=GREY_EPS)
     state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q)
+    return mesh, cfg, state
+
+
+def hii_region(n: int = 44, n_bins: int = 3, L: float = 1.6, c_frac: float = 1e-3):
+    """Expanding HII region on the staggered 2 x n^3 grid: periodic box of
+    L kpc, neutral gas at 100 K with n_H = n0 inside r0 and n0 (r0 / r)^2
+    outside (n0 = 3.2 cm^-3, r0 = 91.5 pc, r from the box centre), photons
+    injected uniformly by volume into the cells within 0.05 kpc of the centre
+    at 1e50, 5e48, 3e48 photons/s per bin (the first n_bins), c_red = c_frac c,
+    Y = 0.24, full thermal network.  The box centre is a generator, so the
+    setup is mirror-symmetric about it.  Returns (mesh, cfg, state)."""
+    mesh = bcc_mesh(n, L)
+    C = mesh.n_cells
+    c = mesh.centroids() - 0.5 * L
+    c -= L * np.round(c / L)
+    r = np.sqrt((c * c).sum(1))
+    n0, r0 = 3.2, 0.0915
+    nH = n0 * (r0 / np.maximum(r, r0)) ** 2
+    cells = np.nonzero(r < 0.05)[0].astype(np.int64)
+    w = mesh.volume[cells] / mesh.volume[cells].sum()
+    Qb = np.array([1e50, 5e48, 3e48])[:n_bins]
+    Q = np.outer(w, Qb)
+    x5 = np.zeros((5, C))
+    x5[0] = 1.0
+    x5[2] = 1.0
+    cfg = dict(n_bins=n_bins, c_red=c_frac * C_LIGHT, unit_length_cm=KPC_CM, box=L, cfl=0.3, chem_mode=2,
+               chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
+               max_substeps=10000, y_he=helium_ratio(0.24), sigma=[row[:3] for row in GREY_SIGMA[:n_bins]],
+               eps=[row[:3] for row in GREY_EPS[:n_bins]])
+    state = dict(nH=nH, x5=x5, T=np.full(C, 100.0), N=np.zeros((n_bins, C)), fr=np.zeros((n_bins, 3, C)),
+                 cells=cells, Q=Q)
     return mesh, cfg, state

@@ -570,6 +570,40 @@ def test_config1_mirror_and_permutation_symmetry():
     np.testing.assert_allclose(np.flip(fx, 2), -fx, rtol=0, atol=1e-12 * np.abs(fx).max())
 
 
+def test_hii_region_symmetry_on_staggered_grid():
+    """Expanding HII region on the staggered 2 x n^3 grid (truncated
+    octahedra): source sphere and density profile are centred on a
+    generator, so photon density, abundances and temperature are even and
+    each flux component odd under reflection of its axis, and the fields are
+    invariant under exchange of two axes, to round-off."""
+    n = 12
+    mesh, cfg, st = synth.hii_region(n)
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt()
+    assert o.step(6 * dt, 6) == 0
+    N, fr = o.radiation()
+    x5, T = o.gas()
+    L = cfg["box"]
+    q = np.round((mesh.centroids() - 0.5 * L) / (L / n / 2)).astype(np.int64) % (2 * n)
+    index = {tuple(v): i for i, v in enumerate(q)}
+
+    def image(fn):
+        return np.array([index[tuple(fn(v) % (2 * n))] for v in q])
+
+    mirror_x = image(lambda v: np.array([-v[0], v[1], v[2]]))
+    swap_xy = image(lambda v: np.array([v[1], v[0], v[2]]))
+    assert N[0].max() > 0 and x5[1].max() > 1e-3
+    for f in (N[0], N[1], x5[1], x5[3], T):
+        sc = np.abs(f).max()
+        np.testing.assert_allclose(f[mirror_x], f, rtol=0, atol=1e-12 * sc)
+        np.testing.assert_allclose(f[swap_xy], f, rtol=0, atol=1e-12 * sc)
+    fx, fy = fr[0, 0], fr[0, 1]
+    sc = np.abs(fx).max()
+    np.testing.assert_allclose(fx[mirror_x], -fx, rtol=0, atol=1e-12 * sc)
+    np.testing.assert_allclose(fy[mirror_x], fy, rtol=0, atol=1e-12 * sc)
+    np.testing.assert_allclose(fx[swap_xy], fy, rtol=0, atol=1e-12 * sc)
+
+
 @pytest.mark.slow
 def test_config1_early_ionisation_front():
     """H-only, isothermal version of the 32^3 workload: after 100 subcycles

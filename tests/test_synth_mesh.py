@@ -81,6 +81,79 @@ def test_voronoi_matches_qhull():
     assert ours == qpairs
 
 
+def test_bcc_mesh_invariants_and_qhull():
+    """Staggered 2 x n^3 grid: the analytic truncated octahedra close (sum A n
+    = 0), decompose into pyramids (sum_f A (x_f - s).n = 3V), fill the box,
+    face centres are the generator midpoints on the bisector, and volumes,
+    neighbour pairs and face areas equal Qhull's tessellation of the
+    generators plus their 26 periodic images."""
+    spatial = pytest.importorskip("scipy.spatial")
+    n, L = 3, 1.5
+    m = synth.bcc_mesh(n, L)
+    C, h = m.n_cells, L / n
+    assert C == 2 * n ** 3 and m.n_faces == 14 * n ** 3
+    assert abs(m.volume.sum() / L ** 3 - 1) < 1e-14
+    assert np.abs(_closure(m)).max() < 1e-14 * h * h
+    g = m.gen
+    d = g[m.right] - g[m.left]
+    d -= L * np.round(d / L)
+    dn = d / np.linalg.norm(d, axis=1, keepdims=True)
+    np.testing.assert_allclose(np.stack([m.nx, m.ny, m.nz], 1), dn, atol=1e-14)
+    fc = np.stack([m.fx, m.fy, m.fz], 1)
+    off = fc - (g[m.left] + 0.5 * d)
+    off -= L * np.round(off / L)
+    assert np.abs(off).max() < 1e-14 * L
+    pyr = np.zeros(C)
+    for side, sg in ((m.left, 1.0), (m.right, -1.0)):
+        x = fc - g[side]
+        x -= L * np.round(x / L)
+        np.add.at(pyr, side, sg * m.area * (x * np.stack([m.nx, m.ny, m.nz], 1)).sum(1))
+    np.testing.assert_allclose(pyr / 3, m.volume, rtol=1e-13)
+    # Qhull
+    shifts = np.array([(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)], float) * L
+    allp = np.concatenate([g + s for s in shifts])
+    vor = spatial.Voronoi(allp)
+    base = 13 * C
+    for i in range(C):
+        reg = vor.regions[vor.point_region[base + i]]
+        assert -1 not in reg
+        assert abs(spatial.ConvexHull(vor.vertices[reg]).volume / m.volume[i] - 1) < 1e-9
+    qarea = {}
+    for (a, b), rv in zip(vor.ridge_points, vor.ridge_vertices):
+        if (a // C != 13 and b // C != 13) or -1 in rv:
+            continue
+        poly = vor.vertices[rv]
+        c0 = poly.mean(0)
+        area = 0.5 * np.linalg.norm(sum(np.cross(poly[k] - c0, poly[(k + 1) % len(poly)] - c0)
+                                        for k in range(len(poly))))
+        if area > 1e-9 * h * h:
+            qarea[tuple(sorted((a % C, b % C)))] = area
+    ours = {tuple(sorted((int(i), int(j)))): a for i, j, a in zip(m.left, m.right, m.area)}
+    assert set(ours) == set(qarea)
+    for key, a in ours.items():
+        assert abs(qarea[key] / a - 1) < 1e-9
+
+
+def test_hii_region_setup():
+    """The expanding-HII-region workload: density n0 in the core and
+    n0 (r0/r)^2 outside, total source rate per bin as stated, mirror symmetry
+    of the cell set about the box centre."""
+    mesh, cfg, st = synth.hii_region(12)
+    L = cfg["box"]
+    c = mesh.centroids() - 0.5 * L
+    c -= L * np.round(c / L)
+    r = np.linalg.norm(c, axis=1)
+    assert np.allclose(st["nH"][r < 0.0915], 3.2)
+    far = r > 0.2
+    np.testing.assert_allclose(st["nH"][far] * r[far] ** 2, 3.2 * 0.0915 ** 2, rtol=1e-12)
+    np.testing.assert_allclose(st["Q"].sum(0), [1e50, 5e48, 3e48], rtol=1e-12)
+    assert (r[st["cells"]] < 0.05).all() and (np.sort(r)[: len(st["cells"])] < 0.05).all()
+    half = L / 12 / 2
+    q = np.round(c / half).astype(np.int64) % 24
+    key = {tuple(v) for v in q}
+    assert all(tuple((-v) % 24) in key for v in q)
+
+
 def test_cartesian_mesh():
     m = synth.cartesian_mesh(4, 2.0)
     assert m.n_cells == 64 and m.n_faces == 192
