@@ -465,9 +465,19 @@ def measure_hii(steps, warmup, dev, n=64, n_sub=64):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     rt.sync()
+    rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, True)
+    rt.step(dt, n_sub)
+    prof = rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, False)
+    rt.sync()
     C, F, _ = rt.mesh_info()
     f = rt.fields()
-    return {"workload": f"expanding HII region, staggered 2x{n}^3 grid ({C} cells, {F} faces, 7 faces/cell), "
+    nsub = f["nsub"]
+    return {"kernels_ms_per_launch": {k: round(v[0] / max(v[1], 1), 5) for k, v in prof.items()},
+            "chem_attempts_last_subcycle": {"mean": float(nsub.mean()), "max": int(nsub.max()),
+                                            "cells_above_1": int((nsub > 1).sum())},
+            "workload": f"expanding HII region, staggered 2x{n}^3 grid ({C} cells, {F} faces, 7 faces/cell), "
                         f"r^-2 density, 3 bins, c_red 1e-3 c, {n_sub} subcycles/step, mixed",
             "value": C * n_sub * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "warmup": warmup, "t_Myr": (warmup + steps) * dt / 3.15576e13,

@@ -235,8 +235,19 @@ void launch_chem(rt_ctx* ctx, double dt) {
   CellArgs a = cell_args(ctx, dt, 0, 1, 1);
   ChemParams P = chem_params(ctx);
   const int t = 128;
-  if (mixed(ctx)) k_chem<true><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, ctx->shadow);
-  else k_chem<false><<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, nullptr);
+  if (!mixed(ctx)) {
+    k_chem<<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, nullptr);
+    return;
+  }
+  // first attempt of every cell, then the rejected cells (a persistent grid
+  // of one block per SM that takes the worklist 128 entries at a time; the
+  // worklist is short once the gas is near equilibrium)
+  ChemWork w{ctx->work_cell, ctx->work_f1, ctx->work_ctl};
+  k_chem_first<<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
+  if (!a.do_chem) return;
+  ctx->launches++;
+  const int nb = (int)std::min<long long>(nblk(ctx->C, t), ctx->n_sm);
+  k_chem_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
 }
 
 void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
@@ -297,6 +308,11 @@ rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
     delete ctx;
     cudaGetLastError();
     return fail(nullptr, RT_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+      ctx->n_sm < 1) {
+    cudaGetLastError();
+    ctx->n_sm = 1;
   }
   *out = ctx;
   return RT_OK;
@@ -409,6 +425,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
   }
   if (mx) {
     AL(ctx->fa32, F); AL(ctx->fb32, F); AL(ctx->minv32, 6 * (size_t)C); AL(ctx->ivol, C);
+    AL(ctx->work_cell, C); AL(ctx->work_f1, C); AL(ctx->work_ctl, 4);
     AL(ctx->shadow, (size_t)C * B);
   }
 #undef AL
@@ -442,6 +459,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
                                                             sfx, sfy, sfz, sA, ctx->rL64, ctx->rR64, ctx->w64);
   }
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
+  if (mx) CK(cudaMemsetAsync(ctx->work_ctl, 0, 4 * sizeof(int), ctx->stream), "worklist");
   k_geometry_cells<<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->cfg.box, ctx->off, ctx->csr, ctx->lr, ctx->cx,
                                                           ctx->cy, ctx->cz, sA, ctx->minv64, ctx->status);
   if (mx && F > 0) {

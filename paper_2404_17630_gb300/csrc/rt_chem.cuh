@@ -358,10 +358,12 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 // covered exactly).  Both are >= 0, where the order of the bit patterns is
 // the numeric order: the comparisons run on the integer pipe.  S_b returns
 // the product of the accepted attempts' photon factors (the flux scale).
+// The loop can resume after a rejected first attempt (two-pass chemistry):
+// dt0 = the next attempt's length, n0 = attempts already made.
 __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, GasState& s,
-                               double S[kMaxBins], bool* capped) {
-  double rem = dt_sub, dt = dt_sub;
-  int n = 0, acc = 0;
+                               double S[kMaxBins], bool* capped, double dt0, int n0) {
+  double rem = dt_sub, dt = dt0;
+  int n = n0, acc = 0;
   GasState t;
   double sc[kMaxBins];
   *capped = false;
@@ -388,6 +390,23 @@ __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, Ga
     for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0;
   }
   return n;
+}
+
+// First attempt of the mixed chemistry, over the whole subcycle.  Accepted
+// (returns true): s is the end state and S the photon factors.  Rejected:
+// s is unchanged and *f1 holds the attempt's measure, from which the loop
+// resumes with dt_sub * fs / f1 (chemistry_mixed with n0 = 1).
+__device__ bool chemistry_mixed_first(const ChemParams& P, double nH, double dt_sub, GasState& s,
+                                      double S[kMaxBins], float* f1) {
+  GasState t;
+  double sc[kMaxBins];
+  const float f = photochem_attempt_mixed(P, nH, dt_sub, s, t, sc);
+  *f1 = f;
+  if (f > (float)P.f_max) return false;
+  s = t;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) S[b] = sc[b];
+  return true;
 }
 
 __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {

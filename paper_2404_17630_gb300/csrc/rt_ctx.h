@@ -17,6 +17,7 @@ struct rt_ctx {
   std::string err;
   bool mesh_ready = false;
   int C = 0, F = 0, B = 0, max_deg = 0;
+  int n_sm = 1;       // streaming multiprocessors of the device
   int grad_cap = 0;  // half-edge records of the largest gradient block (0: unstaged gradient kernel)
   double min_dx_cm = 0;
   // FP64 cell and face data
@@ -39,7 +40,10 @@ struct rt_ctx {
   int n_src_cells = 0, src_cap = 0;
   int32_t* nsub = nullptr;
   d4* rad0 = nullptr;          // state at the start of a Heun transport step (time_order 2)
-  double* ivol = nullptr;      // 1 / V (mixed-precision flux application)
+  double* ivol = nullptr;
+  int32_t* work_cell = nullptr;  // mixed chemistry worklist (cells whose first attempt was rejected)
+  float* work_f1 = nullptr;
+  int* work_ctl = nullptr;       // entries, next entry, finished blocks (zero between subcycles)      // 1 / V (mixed-precision flux application)
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision
   void* flux = nullptr;        // [F][B] 4-vectors in sweep precision

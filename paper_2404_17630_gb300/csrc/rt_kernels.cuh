@@ -8,8 +8,10 @@
 //                  thread per (face, bin)  (Sec. 2.3.3, 4.1.3)
 //   k_gather<R>    per (cell, bin): deterministic CSR gather of the stored
 //                  face fluxes, FP64 update (Sec. 4.1.3)
-//   k_chem<Fast>   per cell: source injection and thermochemistry (Eq. E,
-//                  Sec. 2.3.1, 4.1.1)
+//   k_chem         per cell: source injection and thermochemistry (Eq. E,
+//                  Sec. 2.3.1, 4.1.1), FP64 sweep
+//   k_chem_first,  the same in two passes for the mixed precision
+//   k_chem_rest    (first attempt of every cell, then the rejected cells)
 //
 // R is the precision of the transport sweep (double, or float in the mixed
 // mode of Sec. 6.2); the master state, the gather sums, the volume divisions
@@ -751,57 +753,136 @@ __global__ void k_reciprocal(int n, const double* __restrict__ in, double* out) 
 }
 
 // Sources and thermochemistry, one thread per cell (Eq. E source term,
-// Sec. 2.3.1, 4.1.1).  Writes the FP32 shadow of the radiation if given.
-// Fast (mixed precision): the attempts carry N and the gas only; the flux is
-// read at the end and scaled by the product of the accepted photon factors.
-template <bool Fast>
+// Sec. 2.3.1, 4.1.1).  FP64 sweep: one kernel, the oracle's arithmetic.
+// Mixed precision: two passes (the remedy Sec. 6.2 proposes for the
+// divergence of the substep loop): k_chem_first makes the first attempt of
+// every cell over the whole subcycle -- one attempt per lane, no divergence
+// -- and finishes the cells it accepts; the cells it rejects go to a
+// worklist that k_chem_rest works through with the adaptive loop.  The
+// attempts of each cell, and so its result, are those of one pass.  The
+// attempts carry N and the gas only; the flux is read at the end and
+// scaled by the product of the accepted photon factors.
+
+// Worklist of the cells whose first attempt was rejected.
+struct ChemWork {
+  int32_t* cell;   // C
+  float* f1;       // C: the rejected first attempt's measure
+  int* ctl;        // [0] entries, [1] next entry to hand out, [2] finished blocks
+};
+
+__device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasState& s, bool inject) {
+  const int B = a.B;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b)
+    if (b < B) s.N[b] = a.rad[(size_t)i * B + b].x;
+  if (inject) {
+    const int si = a.src_idx[i];
+    if (si >= 0) {
+      const double vcm3 = a.vol[i] * a.lu3;
+#pragma unroll
+      for (int b = 0; b < kMaxBins; ++b)
+        if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+    }
+  }
+  const size_t C = a.C;
+  s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+  s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+}
+
+// Final state of a cell: radiation (flux scaled by S), shadow, gas, count.
+__device__ __forceinline__ void chem_store_mixed(const CellArgs& a, int i, const GasState& s,
+                                                 const double S[kMaxBins], int n, bool gas,
+                                                 float4* __restrict__ shadow) {
+  const int B = a.B;
+  bool bad = false;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      d4* r = a.rad + (size_t)i * B + b;
+      const d4 u = *r;
+      const d4 o = make_d4(s.N[b], u.y * S[b], u.z * S[b], u.w * S[b]);
+      *r = o;
+      if (!isfinite(o.x)) bad = true;
+      if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(o.x), d2f_int(o.y), d2f_int(o.z), d2f_int(o.w));
+    }
+  }
+  if (bad) atomicOr(a.status, kStNonFinite);
+  if (gas) {
+    const size_t C = a.C;
+    a.nsub[i] = n;
+    a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
+    a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, float4* __restrict__ shadow,
+                                                    ChemWork w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.C) return;
+  GasState s;
+  double S[kMaxBins];
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0;
+  chem_load_mixed(a, i, s, a.do_inject);
+  if (!a.do_chem) {
+    chem_store_mixed(a, i, s, S, 0, false, shadow);
+    return;
+  }
+  float f1;
+  if (chemistry_mixed_first(P, a.nH[i], a.dt, s, S, &f1)) {
+    chem_store_mixed(a, i, s, S, 1, true, shadow);
+    return;
+  }
+  // rejected: keep the injected photons, hand the cell to the second pass
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b)
+    if (b < a.B) a.rad[(size_t)i * a.B + b].x = s.N[b];
+  const int k = atomicAdd(w.ctl, 1);
+  w.cell[k] = i;
+  w.f1[k] = f1;
+}
+
+__global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, float4* __restrict__ shadow,
+                                                   ChemWork w) {
+  __shared__ int base;
+  const int total = *(volatile int*)w.ctl;
+  for (;;) {
+    if (threadIdx.x == 0) base = atomicAdd(w.ctl + 1, (int)blockDim.x);
+    __syncthreads();
+    const int k = base + (int)threadIdx.x;
+    const bool more = base < total;
+    __syncthreads();
+    if (!more) break;
+    if (k < total) {
+      const int i = w.cell[k];
+      GasState s;
+      double S[kMaxBins];
+      chem_load_mixed(a, i, s, false);
+      bool capped;
+      const double dt0 = a.dt * f2d_int(__fdividef((float)P.f_s, w.f1[k]));
+      const int n = chemistry_mixed(P, a.nH[i], a.dt, s, S, &capped, dt0, 1);
+      if (capped) atomicOr(a.status, kStChemSubsteps);
+      chem_store_mixed(a, i, s, S, n, true, shadow);
+    }
+  }
+  // the last block to finish resets the worklist for the next subcycle
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(w.ctl + 2, 1) == (int)gridDim.x - 1) {
+      w.ctl[0] = 0;
+      w.ctl[1] = 0;
+      w.ctl[2] = 0;
+      __threadfence();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* __restrict__ shadow) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.C) return;
   const int B = a.B;
   const size_t C = a.C;
-  if constexpr (Fast) {
-    GasState s;
-    double S[kMaxBins];
-#pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) {
-      S[b] = 1.0;
-      if (b < B) s.N[b] = a.rad[(size_t)i * B + b].x;
-    }
-    if (a.do_inject) {
-      const int si = a.src_idx[i];
-      if (si >= 0) {
-        const double vcm3 = a.vol[i] * a.lu3;
-#pragma unroll
-        for (int b = 0; b < kMaxBins; ++b)
-          if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
-      }
-    }
-    if (a.do_chem) {
-      s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
-      s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
-      bool capped;
-      const int n = chemistry_mixed(P, a.nH[i], a.dt, s, S, &capped);
-      a.nsub[i] = n;
-      if (capped) atomicOr(a.status, kStChemSubsteps);
-      a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
-      a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
-    }
-    bool bad = false;
-#pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) {
-      if (b < B) {
-        d4* r = a.rad + (size_t)i * B + b;
-        const d4 u = *r;
-        const d4 o = make_d4(s.N[b], u.y * S[b], u.z * S[b], u.w * S[b]);
-        *r = o;
-        if (!isfinite(o.x)) bad = true;
-        if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(o.x), d2f_int(o.y), d2f_int(o.z), d2f_int(o.w));
-      }
-    }
-    if (bad) atomicOr(a.status, kStNonFinite);
-    return;
-  } else {
+  {
     CellState s;
 #pragma unroll
     for (int b = 0; b < kMaxBins; ++b) {
