@@ -48,8 +48,9 @@ def thesan_like(n=128, seed=4, n_peaks=4096):
 def differentiable(n=64, seed=7, n_src=8):
     """Differentiable workload: n^3 jittered-lattice Voronoi mesh (box 10 kpc),
     lognormal n_H (sigma_ln 1), 8 sources with Q ~ U(1e49, 1e50) photons/s,
-    isothermal H+He network, FP64; loss = mass-weighted ionised fraction of
-    the cells whose generators lie in a 16^3-lattice sub-cube."""
+    full H+He network with thermal energy, FP64; loss = mass-weighted ionised
+    fraction of the cells whose generators lie in the 16^3-lattice sub-cube
+    centred on the first source."""
     import synth
     mesh = synth.voronoi_mesh(n, L_BOX, 0.3, seed=seed)
     C = mesh.n_cells
@@ -58,12 +59,13 @@ def differentiable(n=64, seed=7, n_src=8):
     cells = srng.choice(C, size=n_src, replace=False).astype(np.int64)
     Q = np.outer(srng.uniform(1e49, 1e50, n_src), synth.SPECTRAL_SPLIT_E4)
     x5 = np.zeros((5, C)); x5[0] = 1.0; x5[2] = 1.0
-    cfg = dict(n_bins=3, c_red=0.01 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L_BOX, cfl=0.3, chem_mode=1,
+    cfg = dict(n_bins=3, c_red=0.01 * synth.C_LIGHT, unit_length_cm=synth.KPC_CM, box=L_BOX, cfl=0.3, chem_mode=2,
                chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05, f_max=0.1, x_floor=1e-4,
                max_substeps=10000, y_he=synth.helium_ratio(0.24), sigma=synth.GREY_SIGMA, eps=synth.GREY_EPS)
     idx = np.arange(C)
     ijk = np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1)
-    region = np.all(ijk < 16, axis=1)
+    d = (ijk - ijk[cells[0]] + n // 2) % n - n // 2      # periodic lattice offset from the first source
+    region = np.all((d >= -8) & (d < 8), axis=1)
     state = dict(nH=nH, x5=x5, T=np.full(C, 1e4), N=np.zeros((3, C)), fr=np.zeros((3, 3, C)), cells=cells, Q=Q,
                  region=region)
     return mesh, cfg, state
@@ -520,7 +522,7 @@ def measure_adjoint(dev, n=64, n_sub=50, k=10):
     torch.cuda.synchronize(dev)
     adj = time.perf_counter() - t0
     free, total = torch.cuda.mem_get_info(dev)
-    return {"workload": f"voronoi {n}^3 ({C} cells), {n_sub} FP64 subcycles, isothermal H+He, 8 sources, "
+    return {"workload": f"voronoi {n}^3 ({C} cells), {n_sub} FP64 subcycles, H+He with thermal energy, 8 sources, "
                         f"checkpoint every {k}", "forward_value": C * n_sub / fwd, "adjoint_value": C * n_sub / adj,
             "unit": UNIT, "forward_s": round(fwd, 4), "adjoint_s": round(adj, 4),
             "adjoint_over_forward": round(adj / fwd, 2), "dL_dQ": out["dQ"].sum(axis=1).tolist(),

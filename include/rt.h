@@ -174,8 +174,9 @@ rt_status rt_stage_fluxes(rt_ctx *ctx, const double *G, double *flux);
 rt_status rt_stage_transport(rt_ctx *ctx, double dt);
 rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
 
-/* Reverse mode of rt_step(dt, n_sub), FP64 precision, chem_mode 0 or 1,
- * Lie splitting and forward-Euler transport (other configurations return
+/* Reverse mode of rt_step(dt, n_sub): FP64 precision, any chem_mode (the
+ * thermal network included: rate fits and cooling differentiated in T), Lie
+ * splitting and forward-Euler transport (other configurations return
  * RT_INVALID_ARG).
  * The paper has no adjoint; this is the exact derivative of the discrete
  * forward map (sources, every chemistry attempt with the substep controller
@@ -189,7 +190,7 @@ rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
  * Out (NULL = not wanted): dL_dQ[n_src*B] per source of the last
  *   rt_set_sources call (photons/s), dL_dnH[C], and the cotangents of the
  *   initial fields lam0_N, lam0_F, lam0_x5, lam0_T (same layouts).
- * Synchronous.  RT_INVALID_ARG for RT_MIXED or chem_mode 2. */
+ * Synchronous.  RT_INVALID_ARG for RT_MIXED, Strang splitting or Heun. */
 rt_status rt_adjoint(rt_ctx *ctx, double dt, int n_sub, int checkpoint_every, const double *lam_N,
                      const double *lam_F, const double *lam_x5, const double *lam_T, double *dL_dQ,
                      double *dL_dnH, double *lam0_N, double *lam0_F, double *lam0_x5, double *lam0_T);

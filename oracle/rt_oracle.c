@@ -362,6 +362,64 @@ static double cooling(double T, double ne, double nHI, double nHII, double nHeI,
   return ce + ci + rc + br;
 }
 
+/* d/dT of the rate fits above, for the reverse mode of the thermal network:
+ * d[0..5] = d(alpha_HII, alpha_HeII, alpha_HeIII, beta_HI, beta_HeI, beta_HeII)/dT. */
+static double dalpha_hg(double T, double t_tr, double a) {
+  /* a lam^1.5 / (1 + (lam/2.74)^0.407)^2.242 with lam = 2 t_tr / T, dlam/dT = -lam/T */
+  double lam = 2.0 * t_tr / T;
+  double u = pow(lam / 2.740, 0.407);
+  double al = a * pow(lam, 1.5) / pow(1.0 + u, 2.242);
+  return -al * (1.5 - 2.242 * 0.407 * u / (1.0 + u)) / T;
+}
+static double dlog_tfac(double T) { return -tfac(T) * 0.5 / sqrt(1e5 * T); }
+static double ddiel(double T, double a) {
+  /* a T^-1.5 exp(-470000/T) (1 + 0.3 exp(-94000/T)) */
+  double g = a * pow(T, -1.5) * exp(-470000.0 / T), h = 1.0 + 0.3 * exp(-94000.0 / T);
+  return g * (-1.5 / T + 470000.0 / (T * T)) * h + g * 0.3 * exp(-94000.0 / T) * 94000.0 / (T * T);
+}
+static void rate_derivs(double T, double d[6]) {
+  d[0] = dalpha_hg(T, 157807.0, 2.753e-14);
+  d[1] = -0.750 * 1.26e-14 * pow(2.0 * 285335.0 / T, 0.750) / T + ddiel(T, 1.9e-3);
+  d[2] = dalpha_hg(T, 631515.0, 2.0 * 2.753e-14);
+  d[3] = beta_HI(T) * (0.5 / T + 157809.1 / (T * T) + dlog_tfac(T));
+  d[4] = beta_HeI(T) * (0.5 / T + 285335.4 / (T * T) + dlog_tfac(T));
+  d[5] = beta_HeII(T) * (0.5 / T + 631515.0 / (T * T) + dlog_tfac(T));
+}
+
+/* The cooling rate written as n_e sum_t K_t(T) n_(t): K[10] and dK/dT[10],
+ * terms in the order of cooling(): collisional excitation HI, HeII;
+ * collisional ionisation HI, HeI, HeII; recombination HII, HeII, HeIII,
+ * dielectronic HeII; bremsstrahlung (on n_HII + n_HeII + 4 n_HeIII). */
+static void cooling_coeffs(double T, double K[10], double dK[10]) {
+  double sT = sqrt(T), tf = tfac(T), dlt = dlog_tfac(T);
+  K[0] = 7.50e-19 * exp(-118348.0 / T) * tf;
+  dK[0] = K[0] * (118348.0 / (T * T) + dlt);
+  K[1] = 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * tf;
+  dK[1] = K[1] * (-0.397 / T + 473638.0 / (T * T) + dlt);
+  K[2] = 1.27e-21 * sT * exp(-157809.1 / T) * tf;
+  dK[2] = K[2] * (0.5 / T + 157809.1 / (T * T) + dlt);
+  K[3] = 9.38e-22 * sT * exp(-285335.4 / T) * tf;
+  dK[3] = K[3] * (0.5 / T + 285335.4 / (T * T) + dlt);
+  K[4] = 4.95e-22 * sT * exp(-631515.0 / T) * tf;
+  dK[4] = K[4] * (0.5 / T + 631515.0 / (T * T) + dlt);
+  double q = pow(T / 1e6, 0.7);
+  double t3 = pow(T / 1e3, -0.2) / (1.0 + q);
+  double dlt3 = -0.2 / T - 0.7 * q / (T * (1.0 + q));
+  K[5] = 8.70e-27 * sT * t3;
+  dK[5] = K[5] * (0.5 / T + dlt3);
+  K[6] = 1.55e-26 * pow(T, 0.3647);
+  dK[6] = K[6] * 0.3647 / T;
+  K[7] = 3.48e-26 * sT * t3;
+  dK[7] = K[7] * (0.5 / T + dlt3);
+  K[8] = 1.24e-13 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
+  dK[8] = ddiel(T, 1.24e-13);
+  double lg = log10(T), w = exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+  double gff = 1.1 + 0.34 * w;
+  double dgff = 0.34 * w * (2.0 * (5.5 - lg) / 3.0) / (T * log(10.0));
+  K[9] = 1.42e-27 * gff * sT;
+  dK[9] = 1.42e-27 * (dgff * sT + gff * 0.5 / sT);
+}
+
 static double rel_change(double a, double b, double floor_) {
   double m = fabs(a) > floor_ ? fabs(a) : floor_;
   return fabs(b - a) / m;
@@ -738,7 +796,7 @@ double orc_cooling(double T, double ne, double nHI, double nHII, double nHeI, do
 }
 
 /* ======================================================================== */
-/* Adjoint: reverse mode of whole RT steps (isothermal network).            */
+/* Adjoint: reverse mode of whole RT steps (all chemistry modes).           */
 /*                                                                          */
 /* The paper has no adjoint; this is the exact derivative of the discrete   */
 /* forward map above, written stage by stage in reverse: source term,       */
@@ -944,7 +1002,7 @@ typedef struct {
   double lam_nH;
 } chem_cot;
 
-/* VJP of one isothermal photochem_attempt of cell i: given the cotangents
+/* VJP of one photochem_attempt of cell i: given the cotangents
  * of its output state lt[] and of its substep measure lf, accumulate those of
  * its input state, of dt and of n_H into cc. */
 static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const double *s, const double *lt,
@@ -984,22 +1042,65 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
   double m[3] = {nH * xHI1, nHe * yI1, nHe * yII1};
   double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
   const double in_x[5] = {xHI, xHII, yI, yII, yIII};
+  /* thermal energy (full mode): e0 = 3/2 k n_tot T, e1 = e0 + heat - dt Lambda,
+   * T1 = e1 / (3/2 k n_tot1) */
+  const int mode2 = cf->chem_mode == 2, cool = cf->chem_flags & 4, heat = cf->chem_flags & 8;
+  double ntot0 = 0.0, e0 = 0.0, lamc = 0.0, e1 = 0.0, ntot1 = 0.0, T1 = T;
+  double Kc[10], dKc[10];
+  const double nsp0[5] = {nH * xHI, nH * xHII, nHe * yI, nHe * yII, nHe * yIII};
+  if (mode2) {
+    ntot0 = nH * (1.0 + yhe) + ne0;
+    e0 = 1.5 * KB * ntot0 * T;
+    if (cool) {
+      cooling_coeffs(T, Kc, dKc);
+      lamc = ne0 * ((Kc[0] + Kc[2]) * nsp0[0] + (Kc[5] + Kc[9]) * nsp0[1] + Kc[3] * nsp0[2] +
+                    (Kc[1] + Kc[4] + Kc[6] + Kc[8] + Kc[9]) * nsp0[3] + (Kc[7] + 4.0 * Kc[9]) * nsp0[4]);
+    }
+    double heat_e = 0.0;
+    if (heat)
+      for (int b = 0; b < B; ++b)
+        for (int sp = 0; sp < 3; ++sp) heat_e += cf->eps[b][sp] * c * dt * Nbar[b] * cf->sigma[b][sp] * m[sp];
+    e1 = e0 + heat_e - dt * lamc;
+    double ne2 = nH * xHII1 + nHe * (yII1 + 2.0 * yIII1);
+    ntot1 = nH * (1.0 + yhe) + ne2;
+    T1 = e1 / (1.5 * KB * ntot1);
+  }
 
   double *ls = cc->lam_s;
   double lx1[5];
   for (int q = 0; q < 5; ++q) lx1[q] = lt[4 * B + q];
-  ls[4 * B + 5] += lt[4 * B + 5]; /* T passes through (isothermal) */
   double lxin[5] = {0, 0, 0, 0, 0};
-  /* substep measure f = max_k |out_k - in_k| / max(|in_k|, floor) */
+  double lT0 = 0.0, le1 = 0.0, le0 = 0.0, lne0e = 0.0;
+  if (mode2) {
+    const double lT1 = lt[4 * B + 5];
+    le1 = lT1 / (1.5 * KB * ntot1);
+    const double lntot1 = -lT1 * T1 / ntot1;
+    lx1[1] += lntot1 * nH;
+    lx1[3] += lntot1 * nHe;
+    lx1[4] += lntot1 * 2.0 * nHe;
+    cc->lam_nH += lntot1 * ((1.0 + yhe) + xHII1 + yhe * (yII1 + 2.0 * yIII1));
+  } else {
+    lT0 += lt[4 * B + 5]; /* T passes through (isothermal) */
+  }
+  /* substep measure f = max over (energy, full mode) and the abundances of
+   * |out - in| / max(|in|, floor) */
   if (lf != 0.0) {
     int nk = yhe > 0 ? 5 : 2;
     double best = -1.0;
     int kb = -1;
+    if (mode2) {
+      best = rel_change(e0, e1, 0.0);
+      kb = 5;
+    }
     for (int k = 0; k < nk; ++k) {
       double r = rel_change(in_x[k], out_x[k], cf->x_floor);
       if (r > best) { best = r; kb = k; }
     }
-    if (best > 0) {
+    if (best > 0 && kb == 5) {
+      double mm = fabs(e0), sg = e1 > e0 ? 1.0 : -1.0;
+      le1 += lf * sg / mm;
+      le0 += -lf * sg / mm - lf * (fabs(e1 - e0) / mm / mm) * (e0 > 0 ? 1.0 : -1.0);
+    } else if (best > 0) {
       double a = in_x[kb], bo = out_x[kb];
       double mm = fabs(a) > cf->x_floor ? fabs(a) : cf->x_floor;
       double sg = bo > a ? 1.0 : -1.0;
@@ -1007,8 +1108,41 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
       lxin[kb] += -lf * sg / mm - lf * (fabs(bo - a) / mm / mm) * (fabs(a) > cf->x_floor ? (a > 0 ? 1.0 : -1.0) : 0.0);
     }
   }
-  /* photon removal and flux scaling */
   double lNbar[ORC_MAXB] = {0}, lm[3] = {0, 0, 0};
+  if (mode2) {
+    /* e1 = e0 + heat - dt Lambda */
+    le0 += le1;
+    cc->lam_dt -= le1 * lamc;
+    if (heat)
+      for (int b = 0; b < B; ++b) {
+        double ea = 0.0;
+        for (int sp = 0; sp < 3; ++sp) ea += cf->eps[b][sp] * cf->sigma[b][sp] * m[sp];
+        lNbar[b] += le1 * c * dt * ea;
+        cc->lam_dt += le1 * c * Nbar[b] * ea;
+        for (int sp = 0; sp < 3; ++sp) lm[sp] += le1 * c * dt * Nbar[b] * cf->eps[b][sp] * cf->sigma[b][sp];
+      }
+    if (cool) {
+      const double ll = -le1 * dt;
+      double dLdT = ne0 * ((dKc[0] + dKc[2]) * nsp0[0] + (dKc[5] + dKc[9]) * nsp0[1] + dKc[3] * nsp0[2] +
+                           (dKc[1] + dKc[4] + dKc[6] + dKc[8] + dKc[9]) * nsp0[3] + (dKc[7] + 4.0 * dKc[9]) * nsp0[4]);
+      double dn[5] = {ne0 * (Kc[0] + Kc[2]), ne0 * (Kc[5] + Kc[9]), ne0 * Kc[3],
+                      ne0 * (Kc[1] + Kc[4] + Kc[6] + Kc[8] + Kc[9]), ne0 * (Kc[7] + 4.0 * Kc[9])};
+      lT0 += ll * dLdT;
+      lne0e += ll * lamc / ne0;
+      lxin[0] += ll * dn[0] * nH;
+      lxin[1] += ll * dn[1] * nH;
+      lxin[2] += ll * dn[2] * nHe;
+      lxin[3] += ll * dn[3] * nHe;
+      lxin[4] += ll * dn[4] * nHe;
+      cc->lam_nH += ll * (dn[0] * xHI + dn[1] * xHII + yhe * (dn[2] * yI + dn[3] * yII + dn[4] * yIII));
+    }
+    /* e0 = 3/2 k (n_H (1 + y) + n_e0) T */
+    lT0 += le0 * 1.5 * KB * ntot0;
+    const double lntot0 = le0 * 1.5 * KB * T;
+    lne0e += lntot0;
+    cc->lam_nH += lntot0 * (1.0 + yhe);
+  }
+  /* photon removal and flux scaling */
   for (int b = 0; b < B; ++b) {
     double sm = cf->sigma[b][0] * m[0] + cf->sigma[b][1] * m[1] + cf->sigma[b][2] * m[2];
     double rem = c * dt * Nbar[b] * sm;
@@ -1085,6 +1219,18 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
   cc->lam_nH += lne0 * (xHII + yhe * (yII + 2.0 * yIII));
   lxin[3] += lne0 * nHe;
   lxin[4] += lne0 * 2.0 * nHe;
+  /* temperature dependence of the rates, and n_e0 through the energy */
+  {
+    double dR[6];
+    rate_derivs(T, dR);
+    const int recomb = cf->chem_flags & 1, coll = cf->chem_flags & 2;
+    if (coll) lT0 += laH * dt * dR[3] * ne0 + lA * dt * dR[4] * ne1 + lCc * dt * dR[5] * ne1;
+    if (recomb) lT0 += lbH * dt * dR[0] * ne0 + lBb * dt * dR[1] * ne1 + lDd * dt * dR[2] * ne1;
+    lxin[1] += lne0e * nH;
+    lxin[3] += lne0e * nHe;
+    lxin[4] += lne0e * 2.0 * nHe;
+    cc->lam_nH += lne0e * (xHII + yhe * (yII + 2.0 * yIII));
+  }
   /* rates Gamma_sp = sum_b c sigma_bsp Nbar_b; Nbar = N / (1 + c dt kap) */
   double lns[3] = {0, 0, 0};
   for (int b = 0; b < B; ++b) {
@@ -1100,6 +1246,7 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
   lxin[3] += lns[2] * nHe;
   cc->lam_nH += lns[0] * xHI + lns[1] * yhe * yI + lns[2] * yhe * yII;
   for (int q = 0; q < 5; ++q) ls[4 * B + q] += lxin[q];
+  ls[4 * B + 5] += lT0;
 }
 
 typedef struct {
@@ -1181,8 +1328,8 @@ static int chemistry_cell_vjp(orc_t *o, int64_t i, double dt_sub, const double *
 }
 
 /*
- * Reverse mode of orc_step(dt, n_sub) from the current state (isothermal
- * chemistry or transport only).  Runs the forward step, recording the state
+ * Reverse mode of orc_step(dt, n_sub) from the current state (Lie split,
+ * forward-Euler transport, any chemistry mode).  Runs the forward step, recording the state
  * before each chemistry pass and before each transport pass, and leaves the
  * final state in o, as orc_step does.  Inputs: cotangents of the final state
  * (lN [B*C], lfr [3B*C], lx5 [5*C], lT [C]); they are overwritten with the
@@ -1192,8 +1339,8 @@ static int chemistry_cell_vjp(orc_t *o, int64_t i, double dt_sub, const double *
  */
 int orc_adjoint(orc_t *o, double dt, int n_sub, double *lN, double *lfr, double *lx5, double *lT, double *g_src,
                 double *g_nH) {
-  /* reverse mode of the Lie / forward-Euler subcycle with the isothermal network */
-  if (n_sub < 1 || o->cfg.chem_mode == 2 || o->cfg.splitting != 0 || o->cfg.time_order == 2) return 1;
+  /* reverse mode of the Lie / forward-Euler subcycle */
+  if (n_sub < 1 || o->cfg.splitting != 0 || o->cfg.time_order == 2) return 1;
   const double dts = dt / n_sub;
   if (dts > orc_max_dt(o) * (1.0 + 1e-12)) return ST_CFL;
   const int B = o->cfg.n_bins, nv = 4 * B + 6;

@@ -1,5 +1,5 @@
-// Adjoint kernels: reverse mode of the FP64 subcycle (isothermal chemistry
-// or transport only).  The paper has no adjoint; these are the exact
+// Adjoint kernels: reverse mode of the FP64 subcycle (any chemistry mode:
+// transport only, isothermal network, network with thermal energy).  The paper has no adjoint; these are the exact
 // derivatives of the forward kernels, organised as gathers (no atomics):
 //
 //   k_adj_face      per (face, bin): cotangent of the face flux from the two
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_adj_cellsum(AdjArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// chemistry (isothermal network, FP64)
+// chemistry (FP64; isothermal or with thermal energy)
 // ---------------------------------------------------------------------------
 
 constexpr int kNv = 4 * kMaxBins + 6;
@@ -327,9 +327,85 @@ __device__ __forceinline__ void unpack_state(const double* s, int B, CellState& 
   c.T = s[4 * B + 5];
 }
 
-// Reverse of one isothermal attempt (photochem_attempt<false> with mode 1):
-// lt = cotangent of the output state, lf = of the substep measure;
-// accumulates into ls (input state), ldt, lnH.
+// Temperature derivatives of the rate fits (RateEval<false>) for the
+// reverse mode of the thermal network.  The Hui & Gnedin form
+// a lam^1.5 / (1 + (lam/2.74)^0.407)^2.242 with lam = 2 T_tr / T has
+// d ln alpha / d ln T = -(1.5 - 2.242 * 0.407 u / (1 + u)), u = (lam/2.74)^0.407.
+struct RateSlopes {
+  double aHII, aHeII, aHeIII, bHI, bHeI, bHeII;   // d/dT
+};
+
+__device__ __forceinline__ double hg_slope(double T, double t_tr, double coef) {
+  const double lam = 2.0 * t_tr / T;
+  const double u = pow(lam / 2.740, 0.407);
+  const double a = coef * pow(lam, 1.5) / pow(1.0 + u, 2.242);
+  return -a * (1.5 - 2.242 * 0.407 * u / (1.0 + u)) / T;
+}
+// d/dT of c T^-1.5 exp(-470000/T) (1 + 0.3 exp(-94000/T))
+__device__ __forceinline__ double diel_slope(double T, double c) {
+  const double e1 = exp(-470000.0 / T), e2 = exp(-94000.0 / T);
+  const double g = c * pow(T, -1.5) * e1;
+  return g * ((470000.0 / (T * T) - 1.5 / T) * (1.0 + 0.3 * e2) + 0.3 * e2 * 94000.0 / (T * T));
+}
+// d ln(1 / (1 + sqrt(T / 1e5))) / dT
+__device__ __forceinline__ double tf_slope(double T) {
+  const double r = sqrt(T / 1e5);
+  return -0.5 * r / (T * (1.0 + r));
+}
+
+__device__ RateSlopes rate_slopes(double T, const Rates& r) {
+  RateSlopes d;
+  d.aHII = hg_slope(T, 157807.0, 2.753e-14);
+  d.aHeII = -0.75 * 1.26e-14 * pow(2.0 * 285335.0 / T, 0.750) / T + diel_slope(T, 1.9e-3);
+  d.aHeIII = hg_slope(T, 631515.0, 5.506e-14);
+  const double ts = tf_slope(T);
+  d.bHI = r.bHI * (0.5 / T + 157809.1 / (T * T) + ts);
+  d.bHeI = r.bHeI * (0.5 / T + 285335.4 / (T * T) + ts);
+  d.bHeII = r.bHeII * (0.5 / T + 631515.0 / (T * T) + ts);
+  return d;
+}
+
+// The cooling function as n_e (k_HI n_HI + k_HII n_HII + k_HeI n_HeI +
+// k_HeII n_HeII + k_HeIII n_HeIII), per-species coefficients and their T
+// derivatives (the terms of RateEval<false>::cooling grouped by species).
+struct CoolCoef {
+  double k[5], dk[5];   // HI, HII, HeI, HeII, HeIII
+};
+
+__device__ CoolCoef cooling_coef(double T) {
+  const double sT = sqrt(T), tf = 1.0 / (1.0 + sqrt(T / 1e5)), ts = tf_slope(T), iT2 = 1.0 / (T * T);
+  // collisional excitation and ionisation
+  const double ceH = 7.50e-19 * exp(-118348.0 / T) * tf, dceH = ceH * (118348.0 * iT2 + ts);
+  const double ceHe = 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * tf,
+               dceHe = ceHe * (473638.0 * iT2 - 0.397 / T + ts);
+  const double ciH = 1.27e-21 * sT * exp(-157809.1 / T) * tf, dciH = ciH * (0.5 / T + 157809.1 * iT2 + ts);
+  const double ciHe = 9.38e-22 * sT * exp(-285335.4 / T) * tf, dciHe = ciHe * (0.5 / T + 285335.4 * iT2 + ts);
+  const double ciHe2 = 4.95e-22 * sT * exp(-631515.0 / T) * tf, dciHe2 = ciHe2 * (0.5 / T + 631515.0 * iT2 + ts);
+  // recombination
+  const double q = pow(T / 1e6, 0.7);
+  const double t3 = pow(T / 1e3, -0.2) / (1.0 + q), lt3 = -0.2 / T - 0.7 * q / (T * (1.0 + q));
+  const double rH = 8.70e-27 * sT * t3, drH = rH * (0.5 / T + lt3);
+  const double rHe = 1.55e-26 * pow(T, 0.3647), drHe = rHe * 0.3647 / T;
+  const double rHe2 = 3.48e-26 * sT * t3, drHe2 = rHe2 * (0.5 / T + lt3);
+  const double di = 1.24e-13 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
+  const double ddi = diel_slope(T, 1.24e-13);
+  // bremsstrahlung with the Gaunt factor 1.1 + 0.34 exp(-(5.5 - log10 T)^2 / 3)
+  const double lg = log10(T), w = exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+  const double gff = 1.1 + 0.34 * w, dgff = 0.34 * w * (2.0 * (5.5 - lg) / 3.0) / (T * 2.302585092994046);
+  const double br = 1.42e-27 * gff * sT, dbr = 1.42e-27 * (dgff * sT + 0.5 * gff / sT);
+  CoolCoef c;
+  c.k[0] = ceH + ciH;                    c.dk[0] = dceH + dciH;
+  c.k[1] = rH + br;                      c.dk[1] = drH + dbr;
+  c.k[2] = ciHe;                         c.dk[2] = dciHe;
+  c.k[3] = ceHe + ciHe2 + rHe + di + br; c.dk[3] = dceHe + dciHe2 + drHe + ddi + dbr;
+  c.k[4] = rHe2 + 4.0 * br;              c.dk[4] = drHe2 + 4.0 * dbr;
+  return c;
+}
+
+// Reverse of one attempt (photochem_attempt<false>): lt = cotangent of the
+// output state, lf = of the substep measure; accumulates into ls (input
+// state, T included: through the rate fits, and in mode 2 the energy
+// equation), ldt, lnH.
 __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const double* s, const double* lt, double lf,
                             double* ls, double& ldt, double& lnH) {
   const int B = P.B;
@@ -368,19 +444,60 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   const double m0 = nH * xHI1, m1 = nHe * yI1, m2 = nHe * yII1;
   const double in_x[5] = {xHI, xHII, yI, yII, yIII};
   const double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
+  // thermal energy (mode 2): e0 = 3/2 k n_tot0 T, e1 = e0 + heat - dt Lambda,
+  // T1 = e1 / (3/2 k n_tot1)
+  const bool thermal = P.mode == 2, cool = P.flags & 4, heat = P.flags & 8;
+  const double nsp[5] = {nH * xHI, nH * xHII, nHe * yI, nHe * yII, nHe * yIII};
+  double ntot0 = 0.0, e0 = 0.0, lamc = 0.0, e1 = 0.0, ntot1 = 0.0, T1 = T;
+  CoolCoef cc;
+  if (thermal) {
+    ntot0 = nH * (1.0 + yhe) + ne0;
+    e0 = 1.5 * kBoltzmann * ntot0 * T;
+    if (cool) {
+      cc = cooling_coef(T);
+      lamc = ne0 * (cc.k[0] * nsp[0] + cc.k[1] * nsp[1] + cc.k[2] * nsp[2] + cc.k[3] * nsp[3] + cc.k[4] * nsp[4]);
+    }
+    double heat_e = 0.0;
+    if (heat)
+      for (int b = 0; b < B; ++b)
+        heat_e += c * dt * Nbar[b] * (P.eps[b][0] * P.sigma[b][0] * m0 + P.eps[b][1] * P.sigma[b][1] * m1 +
+                                      P.eps[b][2] * P.sigma[b][2] * m2);
+    e1 = e0 + heat_e - dt * lamc;
+    ntot1 = nH * (1.0 + yhe) + nH * xHII1 + nHe * (yII1 + 2.0 * yIII1);
+    T1 = e1 / (1.5 * kBoltzmann * ntot1);
+  }
 
   double lx1[5], lxin[5] = {0, 0, 0, 0, 0};
   for (int q = 0; q < 5; ++q) lx1[q] = lt[4 * B + q];
-  ls[4 * B + 5] += lt[4 * B + 5];
+  double lT0 = 0.0, le0 = 0.0, le1 = 0.0, lne0e = 0.0;
+  if (thermal) {
+    const double lT1 = lt[4 * B + 5];
+    le1 = lT1 / (1.5 * kBoltzmann * ntot1);
+    const double lnt1 = -lT1 * T1 / ntot1;
+    lx1[1] += lnt1 * nH;
+    lx1[3] += lnt1 * nHe;
+    lx1[4] += lnt1 * 2.0 * nHe;
+    lnH += lnt1 * ((1.0 + yhe) + xHII1 + yhe * (yII1 + 2.0 * yIII1));
+  } else {
+    lT0 += lt[4 * B + 5];
+  }
   if (lf != 0.0) {
     const int nk = yhe > 0 ? 5 : 2;
     double best = -1.0;
     int kb = -1;
+    if (thermal) {
+      best = rel_change(e0, e1, 0.0);
+      kb = 5;
+    }
     for (int k = 0; k < nk; ++k) {
       const double r = rel_change(in_x[k], out_x[k], P.x_floor);
       if (r > best) { best = r; kb = k; }
     }
-    if (best > 0) {
+    if (best > 0 && kb == 5) {
+      const double mm = fabs(e0), sg = e1 > e0 ? 1.0 : -1.0;
+      le1 += lf * sg / mm;
+      le0 += -lf * sg / mm - lf * (fabs(e1 - e0) / mm / mm) * (e0 > 0 ? 1.0 : -1.0);
+    } else if (best > 0) {
       const double av = in_x[kb], bo = out_x[kb];
       const double mm = fabs(av) > P.x_floor ? fabs(av) : P.x_floor;
       const double sg = bo > av ? 1.0 : -1.0;
@@ -389,6 +506,39 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
     }
   }
   double lNbar[kMaxBins] = {0, 0, 0}, lm0 = 0, lm1 = 0, lm2 = 0;
+  if (thermal) {
+    le0 += le1;
+    ldt -= le1 * lamc;
+    if (heat)
+      for (int b = 0; b < B; ++b) {
+        const double e_0 = P.eps[b][0] * P.sigma[b][0], e_1 = P.eps[b][1] * P.sigma[b][1],
+                     e_2 = P.eps[b][2] * P.sigma[b][2];
+        const double ea = e_0 * m0 + e_1 * m1 + e_2 * m2;
+        lNbar[b] += le1 * c * dt * ea;
+        ldt += le1 * c * Nbar[b] * ea;
+        const double w = le1 * c * dt * Nbar[b];
+        lm0 += w * e_0;
+        lm1 += w * e_1;
+        lm2 += w * e_2;
+      }
+    if (cool) {
+      const double ll = -le1 * dt;
+      double dLdT = 0.0;
+      for (int q = 0; q < 5; ++q) dLdT += cc.dk[q] * nsp[q];
+      lT0 += ll * ne0 * dLdT;
+      lne0e += ll * lamc / ne0;
+      lxin[0] += ll * ne0 * cc.k[0] * nH;
+      lxin[1] += ll * ne0 * cc.k[1] * nH;
+      lxin[2] += ll * ne0 * cc.k[2] * nHe;
+      lxin[3] += ll * ne0 * cc.k[3] * nHe;
+      lxin[4] += ll * ne0 * cc.k[4] * nHe;
+      lnH += ll * ne0 * (cc.k[0] * xHI + cc.k[1] * xHII + yhe * (cc.k[2] * yI + cc.k[3] * yII + cc.k[4] * yIII));
+    }
+    lT0 += le0 * 1.5 * kBoltzmann * ntot0;
+    const double lnt0 = le0 * 1.5 * kBoltzmann * T;
+    lne0e += lnt0;
+    lnH += lnt0 * (1.0 + yhe);
+  }
   for (int b = 0; b < B; ++b) {
     const double sm = P.sigma[b][0] * m0 + P.sigma[b][1] * m1 + P.sigma[b][2] * m2;
     const double rem = c * dt * Nbar[b] * sm;
@@ -466,6 +616,15 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lnH += lne0 * (xHII + yhe * (yII + 2.0 * yIII));
   lxin[3] += lne0 * nHe;
   lxin[4] += lne0 * 2.0 * nHe;
+  {
+    const RateSlopes d = rate_slopes(T, rt);
+    if (coll) lT0 += laH * dt * d.bHI * ne0 + lA * dt * d.bHeI * ne1 + lCc * dt * d.bHeII * ne1;
+    if (recomb) lT0 += lbH * dt * d.aHII * ne0 + lBb * dt * d.aHeII * ne1 + lDd * dt * d.aHeIII * ne1;
+    lxin[1] += lne0e * nH;
+    lxin[3] += lne0e * nHe;
+    lxin[4] += lne0e * 2.0 * nHe;
+    lnH += lne0e * (xHII + yhe * (yII + 2.0 * yIII));
+  }
   double lns0 = 0, lns1 = 0, lns2 = 0;
   for (int b = 0; b < B; ++b) {
     lNbar[b] += c * (P.sigma[b][0] * lG0 + P.sigma[b][1] * lG1 + P.sigma[b][2] * lG2);
@@ -482,6 +641,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lxin[3] += lns2 * nHe;
   lnH += lns0 * xHI + lns1 * yhe * yI + lns2 * yhe * yII;
   for (int q = 0; q < 5; ++q) ls[4 * B + q] += lxin[q];
+  ls[4 * B + 5] += lT0;
 }
 
 struct ChemAdjArgs {

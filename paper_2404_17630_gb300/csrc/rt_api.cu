@@ -932,9 +932,8 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
                      double* dL_dnH, double* lam0_N, double* lam0_F, double* lam0_x5, double* lam0_T) {
   rt_status st = need_mesh(ctx);
   if (st) return st;
-  if (mixed(ctx) || ctx->cfg.chem_mode == 2 || ctx->cfg.splitting != 0 || ctx->cfg.time_order != 1)
-    return fail(ctx, RT_INVALID_ARG,
-                "rt_adjoint supports FP64 precision, chem_mode 0 or 1, Lie splitting and forward-Euler transport");
+  if (mixed(ctx) || ctx->cfg.splitting != 0 || ctx->cfg.time_order != 1)
+    return fail(ctx, RT_INVALID_ARG, "rt_adjoint supports FP64 precision, Lie splitting and forward-Euler transport");
   if (n_sub < 1 || !(dt > 0) || !std::isfinite(dt) || checkpoint_every < 1)
     return fail(ctx, RT_INVALID_ARG, "need dt > 0, n_sub >= 1, checkpoint_every >= 1");
   const double dts = dt / n_sub;

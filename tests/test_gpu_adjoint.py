@@ -30,19 +30,24 @@ def rel(a, b):
     return np.abs(a - b).max() / (s if s > 0 else 1.0)
 
 
-@pytest.mark.parametrize("chem_mode,k", [(1, 4), (1, 2), (0, 3)])
+@pytest.mark.parametrize("chem_mode,k", [(1, 4), (1, 2), (0, 3), (2, 4), (2, 1)])
 def test_adjoint_matches_oracle(chem_mode, k):
+    """Modes 0-2; in mode 2 the loss also weighs the final temperature, so
+    the energy equation, photoheating, cooling and the rate slopes in T are
+    all on the path."""
     mesh, cfg, st, R = _setup(chem_mode=chem_mode)
     n_sub = 4
     lx = _loss_cot(mesh, st, R)
     lN = np.zeros((3, mesh.n_cells))
     lN[:, R] = mesh.volume[R]
+    lT = lx[1] * 1e-4 if chem_mode == 2 else None
     o = make_oracle(mesh, cfg, st)
     dt = o.max_dt() * n_sub
-    ref = o.adjoint(dt, n_sub, lam_N=lN, lam_x5=lx)
+    ref = o.adjoint(dt, n_sub, lam_N=lN, lam_x5=lx, lam_T=lT)
     assert ref["status"] == 0
     rt = make_gpu(mesh, cfg, st)
-    got = rt.adjoint(dt, n_sub, k, lam_N=lN, lam_x5=lx, n_src=len(st["cells"]))
+    got = rt.adjoint(dt, n_sub, k, lam_N=lN, lam_x5=lx, lam_T=lT, n_src=len(st["cells"]))
+    assert rel(got["T"], ref["lam0"]["T"]) < 1e-9
     gQ_ref = ref["g_src"][:, st["cells"]].T
     assert rel(got["dQ"], gQ_ref) < 1e-9
     assert rel(got["dnH"], ref["g_nH"]) < 1e-9

@@ -61,9 +61,9 @@ def _fd(mesh, cfg, st, R, n_sub, key, idx, h_rel=1e-4):
     return (vals[0] - vals[1]) / (2 * h_rel * st[key][idx]), same
 
 
-@pytest.mark.parametrize("n_sub", [3])
-def test_adjoint_luminosities_and_densities_vs_fd(n_sub):
-    mesh, cfg, st, R = _setup()
+@pytest.mark.parametrize("n_sub,chem_mode", [(3, 1), (3, 2)])
+def test_adjoint_luminosities_and_densities_vs_fd(n_sub, chem_mode):
+    mesh, cfg, st, R = _setup(chem_mode=chem_mode)
     L, g_Q, g_nH = _adjoint(mesh, cfg, st, R, n_sub)
     L0, _ = _run(mesh, cfg, st, R, n_sub)
     assert L == L0
@@ -88,6 +88,68 @@ def test_adjoint_luminosities_and_densities_vs_fd(n_sub):
         assert abs(g_nH[i] - fd) <= 1e-5 * scale, (i, g_nH[i], fd)
         checked += 1
     assert checked >= 10
+
+
+@pytest.mark.parametrize("chem_mode", [1, 2])
+def test_adjoint_temperature_vs_fd(chem_mode):
+    """Mass-weighted temperature of the region R (full thermal network:
+    photoheating, cooling, n_tot through the abundances) and the ionised
+    fraction (isothermal: T enters only through the rate fits),
+    differentiated w.r.t. the initial temperatures and source rates."""
+    mesh, cfg, st, R = _setup(chem_mode=chem_mode)
+    n_sub = 3
+    C = mesh.n_cells
+    m = st["nH"] * mesh.volume
+    w = np.zeros(C)
+    w[R] = m[R] / m[R].sum()
+    key = "T" if chem_mode == 2 else "x5"
+
+    def loss(o):
+        x5, T = o.gas()
+        return float((w * (T if key == "T" else x5[1])).sum())
+
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    if key == "T":
+        out = o.adjoint(dt, n_sub, lam_T=w)
+    else:
+        lx = np.zeros((5, C))
+        lx[1] = w
+        out = o.adjoint(dt, n_sub, lam_x5=lx)
+    assert out["status"] == 0
+    gT = out["lam0"]["T"]
+    gQ = out["g_src"][:, st["cells"]].T
+
+    def fd(arr, idx, rel):
+        vals, pats = [], []
+        for sg in (1, -1):
+            s2 = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in st.items()}
+            s2[arr][idx] *= 1 + sg * rel
+            o2 = make_oracle(mesh, cfg, s2)
+            assert o2.step(dt, n_sub) == 0
+            vals.append(loss(o2))
+            pats.append(o2.substeps().copy())
+        return (vals[0] - vals[1]) / (2 * rel * st[arr][idx]), np.array_equal(pats[0], pats[1])
+
+    rng = np.random.default_rng(3)
+    checked = 0
+    for i in np.concatenate([rng.choice(np.where(R)[0], 6, replace=False), st["cells"]]):
+        f, same = fd("T", i, 1e-4)
+        if not same:
+            continue
+        assert abs(gT[i] - f) <= 1e-5 * max(abs(f), 1e-3 * np.abs(gT).max()), (i, gT[i], f)
+        checked += 1
+    for k in range(len(st["cells"])):
+        for b in range(cfg["n_bins"]):
+            f, same = fd("Q", (k, b), 1e-4)
+            if not same:
+                continue
+            # absolute floor: the finite difference of a loss of order one
+            # cannot resolve components below ~1e-6 of the largest
+            assert abs(gQ[k, b] - f) <= 1e-5 * abs(f) + 1e-6 * np.abs(gQ).max(), (k, b, gQ[k, b], f)
+            checked += 1
+    assert checked >= 6
+    assert np.abs(gT[R]).max() > 0
 
 
 def test_adjoint_transport_only_vs_fd():
