@@ -1128,7 +1128,10 @@ static void photochem_attempt_vjp(const orc_t *o, int64_t i, double dt, const do
       double dn[5] = {ne0 * (Kc[0] + Kc[2]), ne0 * (Kc[5] + Kc[9]), ne0 * Kc[3],
                       ne0 * (Kc[1] + Kc[4] + Kc[6] + Kc[8] + Kc[9]), ne0 * (Kc[7] + 4.0 * Kc[9])};
       lT0 += ll * dLdT;
-      lne0e += ll * lamc / ne0;
+      /* dLambda/dn_e0 = sum_t K_t n_t (Lambda is linear in n_e0; no division,
+       * n_e0 = 0 in a neutral cell) */
+      lne0e += ll * ((Kc[0] + Kc[2]) * nsp0[0] + (Kc[5] + Kc[9]) * nsp0[1] + Kc[3] * nsp0[2] +
+                     (Kc[1] + Kc[4] + Kc[6] + Kc[8] + Kc[9]) * nsp0[3] + (Kc[7] + 4.0 * Kc[9]) * nsp0[4]);
       lxin[0] += ll * dn[0] * nH;
       lxin[1] += ll * dn[1] * nH;
       lxin[2] += ll * dn[2] * nHe;

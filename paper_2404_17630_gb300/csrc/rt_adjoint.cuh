@@ -526,7 +526,11 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
       double dLdT = 0.0;
       for (int q = 0; q < 5; ++q) dLdT += cc.dk[q] * nsp[q];
       lT0 += ll * ne0 * dLdT;
-      lne0e += ll * lamc / ne0;
+      // Lambda is linear in n_e0: its slope needs no division (n_e0 = 0 in a
+      // neutral cell)
+      double kn = 0.0;
+      for (int q = 0; q < 5; ++q) kn += cc.k[q] * nsp[q];
+      lne0e += ll * kn;
       lxin[0] += ll * ne0 * cc.k[0] * nH;
       lxin[1] += ll * ne0 * cc.k[1] * nH;
       lxin[2] += ll * ne0 * cc.k[2] * nHe;

@@ -72,6 +72,21 @@ def test_adjoint_finite_for_tiny_radiation():
         assert np.isfinite(out[k]).all(), k
 
 
+def test_adjoint_finite_from_neutral_thermal():
+    """Neutral start (n_e = 0), no radiation, full thermal network."""
+    mesh, cfg, st, R = _setup(n=6, chem_mode=2)
+    C = mesh.n_cells
+    st["x5"] = np.zeros((5, C))
+    st["x5"][0] = 1.0
+    st["x5"][2] = 1.0
+    st["N"][:] = 0.0
+    st["fr"][:] = 0.0
+    rt = make_gpu(mesh, cfg, st)
+    out = rt.adjoint(rt.max_dt() * 3, 3, 2, lam_x5=_loss_cot(mesh, st, R), n_src=2)
+    for k in ("dQ", "dnH", "N", "F", "x5", "T"):
+        assert np.isfinite(out[k]).all(), k
+
+
 def test_adjoint_checkpointing_is_exact():
     mesh, cfg, st, R = _setup()
     lx = _loss_cot(mesh, st, R)

@@ -216,3 +216,22 @@ def test_adjoint_finite_for_tiny_radiation():
     assert out["status"] == 0
     for a in (out["g_src"], out["g_nH"], out["lam0"]["N"], out["lam0"]["fr"], out["lam0"]["x5"]):
         assert np.isfinite(a).all()
+
+
+def test_adjoint_neutral_start_thermal():
+    """Neutral gas (n_e = 0) and no radiation at the start, full thermal
+    network: the reverse mode stays finite and matches finite differences
+    of the source rates (the cooling slope in n_e needs no division)."""
+    mesh, cfg, st, R = _setup(chem_mode=2)
+    C = mesh.n_cells
+    st["x5"] = np.zeros((5, C))
+    st["x5"][0] = 1.0
+    st["x5"][2] = 1.0
+    st["N"][:] = 0.0
+    st["fr"][:] = 0.0
+    L, g_Q, g_nH = _adjoint(mesh, cfg, st, R, 3)
+    assert np.isfinite(g_Q).all() and np.isfinite(g_nH).all()
+    for k in range(len(st["cells"])):
+        fd, same = _fd(mesh, cfg, st, R, 3, "Q", (k, 0))
+        if same:
+            assert abs(g_Q[k, 0] - fd) <= 1e-5 * abs(fd) + 1e-6 * np.abs(g_Q).max(), (k, g_Q[k, 0], fd)
