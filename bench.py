@@ -486,6 +486,57 @@ def measure_hii(steps, warmup, dev, n=64, n_sub=64):
             "ionised_volume_fraction": float((f["x5"][1] * mesh.volume).sum() / mesh.volume.sum())}
 
 
+def measure_timebins(dev, n_steps=8):
+    """Individual time steps on the 2e5-cell workload (mixed): the cells on a
+    four-level power-of-two hierarchy by density (densest 10% in the
+    shortest bin, then 20%, 30%, 40%); level k is active in steps divisible
+    by 2^k.  Reports active cell-updates/s and the time against all-active
+    steps."""
+    import torch
+    from paper_2404_17630_gb300 import RT, make_config
+    mesh, cfg, state = workload()
+    C = mesh.n_cells
+    order = np.argsort(-state["nH"], kind="stable")
+    level = np.empty(C, np.int64)
+    cuts = np.cumsum([int(0.1 * C), int(0.2 * C), int(0.3 * C)])
+    level[order] = np.searchsorted(cuts, np.arange(C), side="right")
+    stream = torch.cuda.current_stream(dev)
+    rt = RT(make_config(precision="mixed", gather_sum=1, **cfg), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dt = rt.max_dt() * N_SUB
+    for _ in range(2):
+        rt.step(dt, N_SUB)
+    rt.sync()
+    masks = [(level <= max(k for k in range(4) if s % (2 ** k) == 0)) for s in range(n_steps)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_masked = 0.0
+    for m in masks:
+        rt.set_active(m)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        rt.step(dt, N_SUB)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_masked += ev0.elapsed_time(ev1)
+    rt.set_active(None)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(n_steps):
+        rt.step(dt, N_SUB)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_all = ev0.elapsed_time(ev1)
+    rt.sync()
+    active = float(sum(m.sum() for m in masks))
+    return {"workload": f"voronoi {LATTICE}^3, 4-level time-step hierarchy by density (10/20/30/40 %), "
+                        f"{n_steps} steps of {N_SUB} subcycles, mixed",
+            "active_fraction": active / (n_steps * C),
+            "value": active * N_SUB / (ms_masked / 1e3), "unit": "active cell-updates/s",
+            "ms_masked": ms_masked, "ms_all_active": ms_all, "time_ratio": ms_masked / ms_all}
+
+
 def measure_adjoint(dev, n=64, n_sub=50, k=10):
     """FP64 forward and reverse mode on the 262k-cell differentiable workload."""
     import torch
@@ -540,7 +591,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2.1M-cell THESAN-like run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode run")
-    ap.add_argument("--no-hii", action="store_true", help="skip the expanding-HII-region run")
+    ap.add_argument("--no-hii", action="store_true", help="skip the HII-region and time-step-hierarchy runs")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -583,6 +634,7 @@ def main():
     large = None if args.no_large else measure_large(3, 1, dev)
     adjoint = None if args.no_adjoint else measure_adjoint(dev)
     hii = None if args.no_hii else measure_hii(3, 1, dev)
+    timebins = None if args.no_hii else measure_timebins(dev)
     if rank != 0:
         return
     C, F = res["C"], res["F"]
@@ -605,7 +657,7 @@ def main():
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "mixed_fp64_sums": fp64sum,
         "e2e": e2e, "cpu_baseline": cpu,
-        "thesan_like_2M": large, "adjoint": adjoint, "hii_region": hii,
+        "thesan_like_2M": large, "adjoint": adjoint, "hii_region": hii, "individual_timesteps": timebins,
         "gpu_launches": res["launches"], "clocks": cl,
     }
     print(json.dumps(out))

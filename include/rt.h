@@ -143,6 +143,18 @@ rt_status rt_set_radiation(rt_ctx *ctx, const double *N, const double *F);
  * order.  n = 0 removes all sources. */
 rt_status rt_set_sources(rt_ctx *ctx, int64_t n, const int64_t *cell, const double *Q);
 
+/* Individual time steps (Sec. 2.1: cells on a power-of-two time-step
+ * hierarchy, only the active ones integrated in a step).  active[C] (host or
+ * device bytes, nonzero = active) holds for the following rt_step calls;
+ * NULL = every cell active (the default).  In each subcycle only active cells
+ * get sources and thermochemistry; fluxes are computed for the interfaces
+ * with at least one active cell (Sec. 4.1.3) and applied to both of their
+ * cells, so a passive cell changes only through the interfaces it shares
+ * with active cells and the photon number stays conserved.  The work is
+ * proportional to the active cells and their neighbours.  rt_adjoint needs
+ * every cell active (RT_INVALID_ARG otherwise). */
+rt_status rt_set_active(rt_ctx *ctx, const uint8_t *active);
+
 /* Enqueue one RT step of n_sub subcycles of dt/n_sub seconds each.  Host-side
  * checks only (RT_CFL, RT_NOT_READY, RT_INVALID_ARG); see rt_sync. */
 rt_status rt_step(rt_ctx *ctx, double dt, int n_sub);

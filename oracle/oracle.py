@@ -94,6 +94,8 @@ def _lib():
             lib.orc_create.argtypes = [ctypes.POINTER(OracleConfig), i64, i64, dp, dp, dp, dp, ip32, ip32,
                                        dp, dp, dp, dp, dp, dp, dp]
             lib.orc_free.argtypes = [vp]
+            lib.orc_set_active.argtypes = [vp, vp]
+            lib.orc_set_active.restype = None
             lib.orc_set_radiation.argtypes = [vp, dp, dp]
             lib.orc_set_gas.argtypes = [vp, dp, dp, dp]
             lib.orc_set_sources.argtypes = [vp, i64, ip64, dp]
@@ -176,6 +178,15 @@ class Oracle:
                                        _d(Q))
         if st:
             raise ValueError("oracle: source cell out of range")
+
+    def set_active(self, mask):
+        """Individual time steps: mask[C] (nonzero = active) for the following
+        steps; None = every cell active."""
+        if mask is None:
+            self._lib.orc_set_active(self._h, None)
+            return
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        self._lib.orc_set_active(self._h, m.ctypes.data_as(ctypes.c_void_p))
 
     def radiation(self):
         N, fr = np.empty((self.B, self.C)), np.empty((self.B, 3, self.C))

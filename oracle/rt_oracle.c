@@ -84,6 +84,7 @@ typedef struct {
   /* work */
   double *G;               /* [C][B][4][3] limited gradients */
   double *flux;            /* [F][B][4] face flux times area, over c_red */
+  unsigned char *active;   /* [C] individual time steps: 1 = active cell; NULL = all active */
   int64_t *nsub;           /* substep attempts of the last chemistry pass per cell */
   int status;
 } orc_t;
@@ -272,10 +273,21 @@ static void m1_pressure_normal(double N, const double fr[3], const double n[3], 
   }
 }
 
+/* Individual time steps (Sec. 2.1): fluxes are computed for the interfaces
+ * with at least one active cell (Sec. 4.1.3); every other interface carries
+ * no flux in this step, so a passive cell changes only through the fluxes it
+ * shares with active cells. */
+static int cell_active(const orc_t *o, int64_t i) { return o->active ? o->active[i] != 0 : 1; }
+static int face_active(const orc_t *o, int64_t f) { return cell_active(o, o->left[f]) || cell_active(o, o->right[f]); }
+
 static void face_fluxes(orc_t *o) {
   const int B = o->cfg.n_bins;
   for (int64_t f = 0; f < o->F; ++f) {
     double n[3] = {o->nx[f], o->ny[f], o->nz[f]};
+    if (!face_active(o, f)) {
+      for (int k = 0; k < 4 * B; ++k) o->flux[f * B * 4 + k] = 0.0;
+      continue;
+    }
     for (int b = 0; b < B; ++b) {
       double NL, NR, fL[3], fR[3], PL[3], PR[3];
       face_state(o, o->left[f], f, b, &NL, fL);
@@ -573,7 +585,7 @@ static int chemistry_cell(orc_t *o, int64_t i, double dt_sub) {
 static void inject_sources(orc_t *o, double dt) {
   const double lu = o->cfg.unit_length_cm;
   for (int64_t i = 0; i < o->C; ++i)
-    for (int b = 0; b < o->cfg.n_bins; ++b) {
+    for (int b = 0; b < o->cfg.n_bins && cell_active(o, i); ++b) {
       double S = o->src[b * o->C + i];
       if (S != 0.0) o->N[b * o->C + i] += (S * dt) / (o->vol[i] * (lu * lu * lu));
     }
@@ -587,6 +599,10 @@ static int thermochemistry(orc_t *o, double dt) {
     return st;
   }
   for (int64_t i = 0; i < o->C; ++i) {
+    if (!cell_active(o, i)) {   /* passive cells are not integrated this step */
+      o->nsub[i] = 0;
+      continue;
+    }
     int s = chemistry_cell(o, i, dt);
     if (s) st = s;
   }
@@ -603,8 +619,18 @@ void orc_free(orc_t *o) {
                    &o->fz, &o->minv, &o->N, &o->fr, &o->nH, &o->xHI, &o->xHII, &o->yI, &o->yII,
                    &o->yIII, &o->T, &o->src, &o->G, &o->flux};
   for (size_t k = 0; k < sizeof dp / sizeof dp[0]; ++k) free(*dp[k]);
-  free(o->left); free(o->right); free(o->off); free(o->fl); free(o->nsub);
+  free(o->left); free(o->right); free(o->off); free(o->fl); free(o->nsub); free(o->active);
   free(o);
+}
+
+/* Active cells of the following steps (individual time steps, Sec. 2.1):
+ * mask[C] nonzero = active; NULL = every cell active. */
+void orc_set_active(orc_t *o, const unsigned char *mask) {
+  free(o->active);
+  o->active = NULL;
+  if (!mask) return;
+  o->active = (unsigned char *)malloc((size_t)o->C);
+  memcpy(o->active, mask, (size_t)o->C);
 }
 
 /* Copy the mesh, build per-cell face lists (ascending face index), and the
@@ -1343,7 +1369,7 @@ static int chemistry_cell_vjp(orc_t *o, int64_t i, double dt_sub, const double *
 int orc_adjoint(orc_t *o, double dt, int n_sub, double *lN, double *lfr, double *lx5, double *lT, double *g_src,
                 double *g_nH) {
   /* reverse mode of the Lie / forward-Euler subcycle */
-  if (n_sub < 1 || o->cfg.splitting != 0 || o->cfg.time_order == 2) return 1;
+  if (n_sub < 1 || o->cfg.splitting != 0 || o->cfg.time_order == 2 || o->active) return 1;
   const double dts = dt / n_sub;
   if (dts > orc_max_dt(o) * (1.0 + 1e-12)) return ST_CFL;
   const int B = o->cfg.n_bins, nv = 4 * B + 6;

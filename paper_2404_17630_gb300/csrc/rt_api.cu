@@ -59,7 +59,17 @@ template <class T> rt_status dalloc(rt_ctx* ctx, T** p, size_t n, const char* wh
   return RT_OK;
 }
 
+void free_active(rt_ctx* ctx) {
+  for (void* p : ctx->act_allocs) cudaFree(p);
+  ctx->act_allocs.clear();
+  ctx->all_active = true;
+  ctx->act_cells = ctx->touched_cells = ctx->act_faces = ctx->grad_blocks = nullptr;
+  ctx->touched = nullptr;
+  ctx->n_act = ctx->n_touched = ctx->n_act_faces = ctx->n_grad_blocks = 0;
+}
+
 void free_all(rt_ctx* ctx) {
+  free_active(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->mesh_ready = false;
@@ -111,12 +121,15 @@ rt_status check_config(const rt_config* c) {
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
   return Geo<double>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
-                     (const d4*)c->hw, (const d4*)c->hx, nullptr, nullptr, c->B};
+                     (const d4*)c->hw, (const d4*)c->hx, nullptr, nullptr, c->B, c->touched_cells, c->n_touched,
+                     c->grad_blocks, c->n_grad_blocks, c->touched, c->act_faces, c->n_act_faces};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
   // the FP32 sweep reads faces through fa / fb; no per-array face copies
   return Geo<float>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, nullptr, nullptr, nullptr, nullptr,
-                    c->minv32, (const float4*)c->hw, (const float4*)c->hx, c->fa32, c->fb32, pad_bins(c->B)};
+                    c->minv32, (const float4*)c->hw, (const float4*)c->hx, c->fa32, c->fb32, pad_bins(c->B),
+                    c->touched_cells, c->n_touched, c->grad_blocks, c->n_grad_blocks, c->touched, c->act_faces,
+                    c->n_act_faces};
 }
 
 ChemParams chem_params(const rt_ctx* ctx) {
@@ -156,6 +169,10 @@ CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
   a.do_chem = chem && ctx->cfg.chem_mode > 0;
   a.rad0 = nullptr;
   a.heun = 0;
+  // individual time steps: chemistry over the active cells, the flux
+  // application over the cells with an active interface
+  a.list = chem ? ctx->act_cells : ctx->touched_cells;
+  a.n = chem ? ctx->n_act : ctx->n_touched;
   return a;
 }
 
@@ -196,7 +213,8 @@ template <class R> void launch_grad(rt_ctx* ctx) {
   const R e = (R)ctx->cfg.lim_eps;
   if constexpr (sizeof(R) == 4) {
     if (ctx->grad_cap > 0 && ctx->cfg.order >= 2) {
-      const int nb = (ctx->C + kGradCells - 1) / kGradCells;
+      const int nb = ctx->all_active ? (ctx->C + kGradCells - 1) / kGradCells : ctx->n_grad_blocks;
+      if (nb == 0) return;
       const size_t smem = 2 * (size_t)ctx->grad_cap * sizeof(float4);
       k_grad_staged<kGradNB><<<nb, kGradCells * ctx->B, smem, ctx->stream>>>(
           geo<float>(ctx), sweep_rad<float>(ctx), (float*)ctx->G, ctx->cfg.limiter, e * e, ctx->grad_cap,
@@ -204,14 +222,18 @@ template <class R> void launch_grad(rt_ctx* ctx) {
       return;
     }
   }
-  k_grad<R><<<nblk((long long)ctx->C * ctx->B), kThreads, 0, ctx->stream>>>(
-      geo<R>(ctx), sweep_rad<R>(ctx), (R*)ctx->G, ctx->cfg.order, ctx->cfg.limiter, e * e);
+  const long long n = (long long)(ctx->all_active ? ctx->C : ctx->n_touched) * ctx->B;
+  if (n == 0) return;
+  k_grad<R><<<nblk(n), kThreads, 0, ctx->stream>>>(geo<R>(ctx), sweep_rad<R>(ctx), (R*)ctx->G, ctx->cfg.order,
+                                                   ctx->cfg.limiter, e * e);
 }
 
 template <class R> void launch_flux(rt_ctx* ctx) {
   ProfScope ps(ctx, RT_KERNEL_FLUX);
-  k_flux<R><<<nblk((long long)ctx->F * ctx->B), kThreads, 0, ctx->stream>>>(geo<R>(ctx), sweep_rad<R>(ctx),
-                                                                            (const R*)ctx->G, (R4<R>*)ctx->flux);
+  const long long n = (long long)(ctx->all_active ? ctx->F : ctx->n_act_faces) * ctx->B;
+  if (n == 0) return;
+  k_flux<R><<<nblk(n), kThreads, 0, ctx->stream>>>(geo<R>(ctx), sweep_rad<R>(ctx), (const R*)ctx->G,
+                                                   (R4<R>*)ctx->flux);
 }
 
 // stage: 0 plain update; 1 also keeps the input state in rad0 (first Heun
@@ -221,7 +243,8 @@ void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
   CellArgs a = cell_args(ctx, dt, 1, 0, 0);
   a.rad0 = ctx->rad0;
   a.heun = stage;
-  const long long n = (long long)ctx->C * ctx->B;
+  const long long n = (long long)(ctx->all_active ? ctx->C : ctx->n_touched) * ctx->B;
+  if (n == 0) return;
   if (mixed(ctx) && comp_sum(ctx))
     k_gather<float, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
   else if (mixed(ctx))
@@ -235,18 +258,20 @@ void launch_chem(rt_ctx* ctx, double dt) {
   CellArgs a = cell_args(ctx, dt, 0, 1, 1);
   ChemParams P = chem_params(ctx);
   const int t = 128;
+  const int nc = ctx->all_active ? ctx->C : ctx->n_act;
+  if (nc == 0) return;
   if (!mixed(ctx)) {
-    k_chem<<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, nullptr);
+    k_chem<<<nblk(nc, t), t, 0, ctx->stream>>>(a, P, nullptr);
     return;
   }
   // first attempt of every cell, then the rejected cells (a persistent grid
   // of one block per SM that takes the worklist 128 entries at a time; the
   // worklist is short once the gas is near equilibrium)
   ChemWork w{ctx->work_cell, ctx->work_f1, ctx->work_ctl};
-  k_chem_first<<<nblk(ctx->C, t), t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
+  k_chem_first<<<nblk(nc, t), t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
   if (!a.do_chem) return;
   ctx->launches++;
-  const int nb = (int)std::min<long long>(nblk(ctx->C, t), ctx->n_sm);
+  const int nb = (int)std::min<long long>(nblk(nc, t), ctx->n_sm);
   k_chem_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
 }
 
@@ -587,6 +612,70 @@ rt_status rt_mesh_info(rt_ctx* ctx, int64_t* n_cells, int64_t* n_faces, int32_t*
   if (n_cells) *n_cells = ctx->C;
   if (n_faces) *n_faces = ctx->F;
   if (max_degree) *max_degree = ctx->max_deg;
+  return RT_OK;
+}
+
+rt_status rt_set_active(rt_ctx* ctx, const uint8_t* active) {
+  rt_status st = need_mesh(ctx);
+  if (st) return st;
+  // the lists may be in use by work already enqueued
+  CK(cudaStreamSynchronize(ctx->stream), "rt_set_active");
+  free_active(ctx);
+  if (!active) return RT_OK;
+  const int C = ctx->C, F = ctx->F, B = ctx->B;
+  std::vector<uint8_t> m(C);
+  CK(cudaMemcpy(m.data(), active, (size_t)C, is_device_ptr(active) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+     "active mask");
+  bool all = true;
+  for (int i = 0; i < C; ++i) {
+    m[i] = m[i] != 0;
+    all = all && m[i];
+  }
+  if (all) return RT_OK;
+  std::vector<int2> lr(F);
+  if (F > 0) CK(cudaMemcpy(lr.data(), ctx->lr, (size_t)F * sizeof(int2), cudaMemcpyDeviceToHost), "active mask");
+  std::vector<int32_t> ac, tc, af, gb;
+  std::vector<uint8_t> tf(C, 0);
+  for (int i = 0; i < C; ++i)
+    if (m[i]) ac.push_back(i);
+  for (int f = 0; f < F; ++f)
+    if (m[lr[f].x] || m[lr[f].y]) {
+      af.push_back(f);
+      tf[lr[f].x] = tf[lr[f].y] = 1;
+    }
+  for (int i = 0; i < C; ++i)
+    if (tf[i]) tc.push_back(i);
+  for (int c0 = 0; c0 < C; c0 += kGradCells) {
+    bool any = false;
+    for (int i = c0; i < std::min(c0 + kGradCells, C) && !any; ++i) any = tf[i];
+    if (any) gb.push_back(c0 / kGradCells);
+  }
+  auto up = [&](const void* src, size_t bytes, void** dst) -> rt_status {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
+    ctx->act_allocs.push_back(p);
+    if (bytes) {
+      e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
+    }
+    *dst = p;
+    return RT_OK;
+  };
+  if ((st = up(ac.data(), ac.size() * 4, (void**)&ctx->act_cells))) return st;
+  if ((st = up(tc.data(), tc.size() * 4, (void**)&ctx->touched_cells))) return st;
+  if ((st = up(af.data(), af.size() * 4, (void**)&ctx->act_faces))) return st;
+  if ((st = up(gb.data(), gb.size() * 4, (void**)&ctx->grad_blocks))) return st;
+  if ((st = up(tf.data(), tf.size(), (void**)&ctx->touched))) return st;
+  ctx->n_act = (int)ac.size();
+  ctx->n_touched = (int)tc.size();
+  ctx->n_act_faces = (int)af.size();
+  ctx->n_grad_blocks = (int)gb.size();
+  ctx->all_active = false;
+  // the face kernel writes the active interfaces only: the others carry no
+  // flux while this mask holds
+  const size_t rs = mixed(ctx) ? 4 : 8;
+  CK(cudaMemsetAsync(ctx->flux, 0, (size_t)F * B * 4 * rs, ctx->stream), "active mask");
   return RT_OK;
 }
 
@@ -932,8 +1021,9 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
                      double* dL_dnH, double* lam0_N, double* lam0_F, double* lam0_x5, double* lam0_T) {
   rt_status st = need_mesh(ctx);
   if (st) return st;
-  if (mixed(ctx) || ctx->cfg.splitting != 0 || ctx->cfg.time_order != 1)
-    return fail(ctx, RT_INVALID_ARG, "rt_adjoint supports FP64 precision, Lie splitting and forward-Euler transport");
+  if (mixed(ctx) || ctx->cfg.splitting != 0 || ctx->cfg.time_order != 1 || !ctx->all_active)
+    return fail(ctx, RT_INVALID_ARG,
+                "rt_adjoint supports FP64 precision, Lie splitting, forward-Euler transport, every cell active");
   if (n_sub < 1 || !(dt > 0) || !std::isfinite(dt) || checkpoint_every < 1)
     return fail(ctx, RT_INVALID_ARG, "need dt > 0, n_sub >= 1, checkpoint_every >= 1");
   const double dts = dt / n_sub;

@@ -178,6 +178,16 @@ template <class R> struct Geo {
   const f8* fa;           // FP32 sweep, F: (n, A, x_f - s_L, left id bits)
   const float4* fb;       // FP32 sweep, F: (x_f - s_R, right id bits)
   int Bp;                 // FP32 gradient records: bins per group (pad_bins(B))
+  // individual time steps (null = every cell active): the cells with an
+  // active interface (nc of them; staged gradients: the nb blocks holding
+  // them and a per-cell flag) and the nf interfaces with an active cell
+  const int32_t* clist;
+  int nc;
+  const int32_t* blist;
+  int nb;
+  const uint8_t* touched;
+  const int32_t* flist;
+  int nf;
 };
 
 // Cell id stored in the fourth lane of a half-edge record (bit copy).

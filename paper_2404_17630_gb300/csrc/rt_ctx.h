@@ -43,7 +43,16 @@ struct rt_ctx {
   double* ivol = nullptr;
   int32_t* work_cell = nullptr;  // mixed chemistry worklist (cells whose first attempt was rejected)
   float* work_f1 = nullptr;
-  int* work_ctl = nullptr;       // entries, next entry, finished blocks (zero between subcycles)      // 1 / V (mixed-precision flux application)
+  int* work_ctl = nullptr;       // entries, next entry, finished blocks (zero between subcycles)
+  // individual time steps (all null / zero when every cell is active)
+  bool all_active = true;
+  int32_t* act_cells = nullptr;      // active cells
+  int32_t* touched_cells = nullptr;  // cells with an active interface
+  int32_t* act_faces = nullptr;      // interfaces with an active cell
+  int32_t* grad_blocks = nullptr;    // gradient blocks holding a touched cell
+  uint8_t* touched = nullptr;        // per cell: has an active interface
+  int n_act = 0, n_touched = 0, n_act_faces = 0, n_grad_blocks = 0;
+  std::vector<void*> act_allocs;      // 1 / V (mixed-precision flux application)
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision
   void* flux = nullptr;        // [F][B] 4-vectors in sweep precision

@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
                                               int order, int limiter, R lim_eps2) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
-  if (t >= g.C * B) return;
-  const int i = divb(t, g.divB), b = t - i * B;
+  if (t >= (g.clist ? g.nc : g.C) * B) return;
+  const int ii = divb(t, g.divB), b = t - ii * B;
+  const int i = g.clist ? __ldg(g.clist + ii) : ii;
+  t = i * B + b;
   const R4<R> pi = ld4<R>(rad + t);
   if (order < 2) {
     if constexpr (sizeof(R) == 4) {
@@ -373,13 +375,13 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
   extern __shared__ float4 sm[];  // [cap] weight records, then [cap] offset records
   __shared__ __align__(8) uint64_t bar;
   const int B = g.B;
-  const int c0 = blockIdx.x * kGradCells;
+  const int c0 = (g.blist ? __ldg(g.blist + blockIdx.x) : (int)blockIdx.x) * kGradCells;
   const int c1 = min(c0 + kGradCells, g.C);
   const int kb0 = __ldg(g.off + c0), kb1 = __ldg(g.off + c1);
   const int lt = threadIdx.x;
   const int cl = divb(lt, g.divB), b = lt - cl * B;
   const int i = c0 + cl;
-  const bool active = i < c1;
+  const bool active = i < c1 && (!g.touched || __ldg(g.touched + i));
   if (lt == 0) mbar_init(&bar, 1);
   __syncthreads();
   if (lt == 0) {
@@ -573,8 +575,10 @@ __global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict_
                                               R4<R>* __restrict__ flux) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
-  if (t >= g.F * B) return;
-  const int f = divb(t, g.divB), b = t - f * B;
+  if (t >= (g.flist ? g.nf : g.F) * B) return;
+  const int fi = divb(t, g.divB), b = t - fi * B;
+  const int f = g.flist ? __ldg(g.flist + fi) : fi;
+  t = f * B + b;
   if constexpr (sizeof(R) == 4) {
     // FP32 sweep: one 32-byte and one 16-byte face record, then the four
     // groups (gradients, state) of each side's cell-major record
@@ -633,6 +637,8 @@ __global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict_
 struct CellArgs {
   int C, B;
   DivB divB;               // division by B
+  const int32_t* list;     // individual time steps: the n cells to work on (null = all C)
+  int n;
   const int32_t* off;
   const int32_t* csr;
   const double* vol;       // V_i (L_u^3)
@@ -669,10 +675,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 template <class R, bool Comp>
 __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
                                                 float4* __restrict__ shadow) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = a.B;
-  if (t >= a.C * B) return;
-  const int i = divb(t, a.divB), b = t - i * B;
+  if (t >= (a.list ? a.n : a.C) * B) return;
+  const int ii = divb(t, a.divB), b = t - ii * B;
+  const int i = a.list ? __ldg(a.list + ii) : ii;
+  t = i * B + b;
   const int k0 = a.off[i], k1 = a.off[i + 1];
   double acc[4];
   if (Comp) {
@@ -817,8 +825,9 @@ __device__ __forceinline__ void chem_store_mixed(const CellArgs& a, int i, const
 
 __global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, float4* __restrict__ shadow,
                                                     ChemWork w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.C) return;
+  const int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= (a.list ? a.n : a.C)) return;
+  const int i = a.list ? __ldg(a.list + ii) : ii;
   GasState s;
   double S[kMaxBins];
 #pragma unroll
@@ -878,8 +887,9 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
 }
 
 __global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* __restrict__ shadow) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.C) return;
+  const int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= (a.list ? a.n : a.C)) return;
+  const int i = a.list ? __ldg(a.list + ii) : ii;
   const int B = a.B;
   const size_t C = a.C;
   {

@@ -115,6 +115,7 @@ def load():
                 "rt_set_gas": [vp, vp, vp, vp],
                 "rt_set_radiation": [vp, vp, vp],
                 "rt_set_sources": [vp, i64, vp, vp],
+                "rt_set_active": [vp, vp],
                 "rt_step": [vp, dbl, i32],
                 "rt_sync": [vp],
                 "rt_get_fields": [vp, ctypes.c_uint32, ctypes.POINTER(vp)],
@@ -157,7 +158,8 @@ def _ptr(a, dtype, keep: list):
     try:
         import torch
         if isinstance(a, torch.Tensor):
-            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64,
+                   np.uint8: torch.uint8}[dtype]
             t = a.detach()
             if t.dtype != tdt:
                 raise TypeError(f"expected a {tdt} tensor, got {t.dtype}")
@@ -227,6 +229,13 @@ def rt_set_sources(ctx, cells, Q):
     n = 0 if cells is None else len(cells)
     return _check(lib, ctx, lib.rt_set_sources(ctx, n, _ptr(cells, np.int64, keep) if n else None,
                                                _ptr(Q, np.float64, keep) if n else None))
+
+
+def rt_set_active(ctx, active):
+    """Individual time steps: active[C] (nonzero = active; numpy or torch,
+    host or device) for the following steps; None = every cell active."""
+    lib, keep = load(), []
+    return _check(lib, ctx, lib.rt_set_active(ctx, None if active is None else _ptr(active, np.uint8, keep)))
 
 
 def rt_step(ctx, dt, n_sub):
@@ -391,6 +400,9 @@ class RT:
 
     def set_sources(self, cells, Q):
         rt_set_sources(self.ctx, cells, Q)
+
+    def set_active(self, active):
+        rt_set_active(self.ctx, active)
 
     def step(self, dt, n_sub):
         rt_step(self.ctx, dt, n_sub)

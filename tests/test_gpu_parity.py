@@ -169,6 +169,26 @@ def test_hii_region_staggered_grid():
     print("HII region mixed vs oracle", compare_state(g32, o, 1e-4))
 
 
+@pytest.mark.parametrize("precision,time_order", [("fp64", 1), ("fp64", 2), ("mixed", 1)])
+def test_individual_timesteps(precision, time_order):
+    """Individual time steps: 30% of the cells active (a seeded mask), then
+    a second mask, then every cell active again; each against the oracle with
+    the same masks."""
+    mesh, cfg, st = voronoi_case(n=12, n_src=6, time_order=time_order)
+    rng = np.random.default_rng(9)
+    masks = [rng.uniform(size=mesh.n_cells) < 0.3, rng.uniform(size=mesh.n_cells) < 0.6, None]
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    dt = o.max_dt()
+    for m in masks:
+        o.set_active(m)
+        rt.set_active(m)
+        assert o.step(2 * dt, 2) == 0
+        rt.step(2 * dt, 2)
+        assert rt.sync() == 0
+        compare_state(rt, o, TOL64 if precision == "fp64" else 1e-4)
+
+
 @pytest.mark.parametrize("splitting,time_order", [(1, 1), (0, 2), (1, 2)])
 def test_step_variants_fp64(splitting, time_order):
     """Strang splitting and Heun transport (second order in time), with

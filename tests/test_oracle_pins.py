@@ -341,6 +341,83 @@ def test_heun_is_second_order_in_time():
     assert 3.4 < r2 < 4.6, r2
 
 
+def _mask_and_touched(mesh, frac, seed):
+    rng = np.random.default_rng(seed)
+    act = rng.uniform(size=mesh.n_cells) < frac
+    touched = act.copy()
+    fa = act[mesh.left] | act[mesh.right]
+    touched[mesh.left[fa]] = True
+    touched[mesh.right[fa]] = True
+    return act, touched
+
+
+def test_individual_timesteps_locality_and_conservation():
+    """Individual time steps (Sec. 2.1): with 30% of the cells active, the
+    interfaces with an active cell carry flux and no other does (Sec. 4.1.3),
+    so sum N V is still conserved to round-off, a cell without an active
+    interface keeps its radiation bitwise, and passive cells keep their gas
+    (no thermochemistry) while active cells evolve.  With every cell active
+    the result is bitwise that of the unmasked step."""
+    mesh, cfg, st = voronoi_case(n=10, chem_mode=1, n_src=0)
+    act, touched = _mask_and_touched(mesh, 0.3, 4)
+    V = mesh.volume
+    o = make_oracle(mesh, cfg, st)
+    o.set_active(act)
+    dt = o.max_dt()
+    N0, fr0 = o.radiation()
+    assert o.step(3 * dt, 3) == 0
+    N1, fr1 = o.radiation()
+    x5, T = o.gas()
+    # absorption moves photons into electrons: check transport conservation
+    # with absorption off
+    o2 = make_oracle(mesh, dict(cfg, chem_mode=0), st)
+    o2.set_active(act)
+    assert o2.step(3 * dt, 3) == 0
+    N2, fr2 = o2.radiation()
+    np.testing.assert_allclose((N2 * V).sum(1), (N0 * V).sum(1), rtol=1e-13)
+    # no active interface within three subcycles: radiation untouched
+    far = ~touched
+    # cells are touched only through active interfaces, and the active set
+    # is fixed, so untouched cells never change
+    np.testing.assert_array_equal(N2[:, far], N0[:, far])
+    np.testing.assert_array_equal(fr2[:, :, far], fr0[:, :, far])
+    assert np.abs(N2[:, touched] - N0[:, touched]).max() > 0
+    # passive cells: gas unchanged; active cells: gas evolved
+    np.testing.assert_array_equal(x5[:, ~act], st["x5"][:, ~act])
+    np.testing.assert_array_equal(T[~act], st["T"][~act])
+    assert np.abs(x5[:, act] - st["x5"][:, act]).max() > 0
+    # all active = unmasked, bitwise
+    oa, ob = make_oracle(mesh, cfg, st), make_oracle(mesh, cfg, st)
+    oa.set_active(np.ones(mesh.n_cells, bool))
+    assert oa.step(2 * dt, 2) == 0 and ob.step(2 * dt, 2) == 0
+    np.testing.assert_array_equal(oa.radiation()[0], ob.radiation()[0])
+    np.testing.assert_array_equal(oa.gas()[0], ob.gas()[0])
+
+
+def test_individual_timesteps_photon_budget():
+    """Sources, absorption, no recombination, 40% of the cells active: the
+    budget sum V (sum N + n_e) grows by exactly sum over the active source
+    cells of Q t (a source in a passive cell emits nothing this step)."""
+    mesh, cfg, st = voronoi_case(n=10, chem_mode=1, chem_flags=0, n_src=6)
+    act, _ = _mask_and_touched(mesh, 0.4, 7)
+    assert act[st["cells"]].any() and not act[st["cells"]].all()
+    o = make_oracle(mesh, cfg, st)
+    o.set_active(act)
+    Vc = mesh.volume * cfg["unit_length_cm"] ** 3
+    nH, yhe = st["nH"], cfg["y_he"]
+
+    def total():
+        N, _ = o.radiation()
+        x5, _ = o.gas()
+        return ((N.sum(0) + nH * (x5[1] + yhe * (x5[3] + 2 * x5[4]))) * Vc).sum()
+
+    t0 = total()
+    dt = o.max_dt()
+    assert o.step(4 * dt, 4) == 0
+    inj = st["Q"][act[st["cells"]]].sum() * 4 * dt
+    assert abs((total() - t0) / inj - 1) < 1e-10
+
+
 # ---------------------------------------------------------------------------
 # wave and beam: transport speed c_red (Sec. 4.2.1)
 # ---------------------------------------------------------------------------
