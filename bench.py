@@ -488,15 +488,20 @@ def measure_hii(steps, warmup, dev, n=64, n_sub=64):
 
 def measure_timebins(dev, n_steps=8):
     """Individual time steps on the 2e5-cell workload (mixed): the cells on a
-    four-level power-of-two hierarchy by density (densest 10% in the
-    shortest bin, then 20%, 30%, 40%); level k is active in steps divisible
-    by 2^k.  Reports active cell-updates/s and the time against all-active
-    steps."""
+    four-level power-of-two hierarchy (10% in the shortest level, then 20%,
+    30%, 40%), ranked by a spatially correlated field as the time steps of
+    a simulation follow its density structure: a Gaussian random field
+    (P(k) ~ k^-2) on a 16^3 grid, ties of its nearest-node sampling broken by
+    a 64^3 one; level k is active in steps divisible by 2^k.  Reports active
+    cell-updates/s and the time against all-active steps."""
     import torch
+    import synth
     from paper_2404_17630_gb300 import RT, make_config
     mesh, cfg, state = workload()
     C = mesh.n_cells
-    order = np.argsort(-state["nH"], kind="stable")
+    coarse, _ = synth.grf_density(mesh.gen, L_BOX, 16, 1.5, 1.0, 77)
+    fine, _ = synth.grf_density(mesh.gen, L_BOX, 64, 1.5, 1.0, 78)
+    order = np.argsort(-(np.log(coarse) + 0.05 * np.log(fine)), kind="stable")
     level = np.empty(C, np.int64)
     cuts = np.cumsum([int(0.1 * C), int(0.2 * C), int(0.3 * C)])
     level[order] = np.searchsorted(cuts, np.arange(C), side="right")
@@ -530,7 +535,7 @@ def measure_timebins(dev, n_steps=8):
     ms_all = ev0.elapsed_time(ev1)
     rt.sync()
     active = float(sum(m.sum() for m in masks))
-    return {"workload": f"voronoi {LATTICE}^3, 4-level time-step hierarchy by density (10/20/30/40 %), "
+    return {"workload": f"voronoi {LATTICE}^3, 4-level time-step hierarchy (10/20/30/40 %, spatially correlated), "
                         f"{n_steps} steps of {N_SUB} subcycles, mixed",
             "active_fraction": active / (n_steps * C),
             "value": active * N_SUB / (ms_masked / 1e3), "unit": "active cell-updates/s",
