@@ -151,6 +151,7 @@ ChemParams chem_params(const rt_ctx* ctx) {
       P.eps[b][s] = b < c.n_bins ? c.eps[b][s] : 0.0;
       if (P.sigma[b][s] != 0.0) P.smask |= 1 << (3 * b + s);
       if (P.eps[b][s] != 0.0) P.emask |= 1 << (3 * b + s);
+      P.heat_f[b][s] = (float)(P.eps[b][s] * P.sigma[b][s] / kHeatScale);
     }
   return P;
 }

@@ -22,7 +22,13 @@ struct ChemParams {
   double eps[kMaxBins][3];
   int smask;         // bit 3b+s: sigma[b][s] != 0
   int emask;         // bit 3b+s: eps[b][s] != 0
+  float heat_f[kMaxBins][3];   // mixed precision: eps sigma / kHeatScale in FP32
 };
+
+// Scale of the FP32 photoheating products: eps sigma (~1e-29 erg cm^2) is
+// carried as eps sigma / kHeatScale so that eps sigma n_s Nbar stays in the
+// FP32 normal range.
+constexpr double kHeatScale = 1e-30;
 
 constexpr double kBoltzmann = 1.380649e-16;
 
@@ -298,7 +304,14 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   t.yIII = (s.yIII + Cc * t.yII) * iD;
 
   const double m[3] = {nH * t.xHI, nHe * t.yI, nHe * t.yII};
-  double heat_e = 0.0;
+  // photoheating sum_b c dt Nbar_b sum_s eps_bs sigma_bs n_s' in FP32, as the
+  // rate fits (it only enters the energy increment; the photon removal and
+  // the abundances stay FP64): one FP64 product instead of twelve
+  float hsum = 0.0f;
+  float mf[3] = {0.0f, 0.0f, 0.0f};
+  if (heat) {
+    mf[0] = d2f_int(m[0]); mf[1] = d2f_int(m[1]); mf[2] = d2f_int(m[2]);
+  }
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
@@ -313,16 +326,17 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
       double sc = fma(-taup, inv1pt[b], 1.0);
       sc = sc > 0.0 ? sc : 0.0;
       if (heat) {
-        double ea = 0.0;
+        float ea = 0.0f;
 #pragma unroll
         for (int sp = 0; sp < 3; ++sp)
-          if (P.emask & P.smask & (1 << (3 * b + sp))) ea = fma(P.eps[b][sp], a[sp], ea);
-        heat_e = fma(cdt * Nbar[b], ea, heat_e);
+          if (P.emask & P.smask & (1 << (3 * b + sp))) ea = fmaf(P.heat_f[b][sp], mf[sp], ea);
+        hsum = fmaf(d2f_int(Nbar[b]), ea, hsum);
       }
       t.N[b] = s.N[b] * sc;
       sc_out[b] = sc;
     }
   }
+  const double heat_e = heat ? (cdt * kHeatScale) * f2d_int(hsum) : 0.0;
   const float fl = (float)P.x_floor;
   float f = 0.0f;
   if (P.mode == 2) {
