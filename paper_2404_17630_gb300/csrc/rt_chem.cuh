@@ -122,7 +122,32 @@ template <> struct RateEval<true> {
                  c_rH * nHII + c_rHe * nHeII + c_rHe2 * nHeIII + c_di * nHeII +
                  c_br * (nHII + nHeII + 4.0 * nHeIII));
   }
+  // The same cooling rate divided by kCoolScale, entirely in FP32 from the
+  // FP32 images of the densities (the coefficients, ~1e-27..1e-19, times
+  // 1/kCoolScale lie in the FP32 normal range together with the densities'
+  // products); it only enters the energy increment.
+  __device__ static float cooling_scaled(double Td, float ne, float nHI, float nHII, float nHeI, float nHeII,
+                                         float nHeIII) {
+    const float T = d2f_int(Td), iT = __frcp_rn(T);
+    const float sT = sqrtf(T), tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
+    const float ex1 = fexp(-157809.1f * iT), ex2 = fexp(-285335.4f * iT), ex3 = fexp(-631515.0f * iT);
+    // coefficients of the KWH96 fits times 1/kCoolScale = 1e27
+    const float kHI = (7.50e8f * fexp(-118348.0f * iT) + 1.27e6f * sT * ex1) * tf;
+    const float t3 = fpow(T * 1e-3f, -0.2f) / (1.0f + fpow(T * 1e-6f, 0.7f));
+    const float lg = __log10f(T);
+    const float br = 1.42f * (1.1f + 0.34f * fexp(-(5.5f - lg) * (5.5f - lg) * (1.0f / 3.0f))) * sT;
+    const float kHII = 8.70f * sT * t3;
+    const float kHeI = 9.38e5f * sT * ex2 * tf;
+    const float kHeII = (5.54e10f * fpow(T, -0.397f) * fexp(-473638.0f * iT) + 4.95e5f * sT * ex3) * tf +
+                        15.5f * fpow(T, 0.3647f) +
+                        1.24e14f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    const float kHeIII = 34.8f * sT * t3;
+    return ne * (kHI * nHI + (kHII + br) * nHII + kHeI * nHeI + (kHeII + br) * nHeII + (kHeIII + 4.0f * br) * nHeIII);
+  }
 };
+
+// Scale of the FP32 cooling rate (see RateEval<true>::cooling_scaled).
+constexpr double kCoolScale = 1e-27;
 
 // Per-cell state of the photochemistry step.
 struct CellState {
@@ -342,10 +367,13 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   if (P.mode == 2) {
     const double ntot0 = nH * (1.0 + P.y_he) + ne0;
     const double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
-    const double lam = cool ? RateEval<true>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
-                                                      nHe * s.yIII)
-                            : 0.0;
-    const double e1 = e0 + heat_e - dt * lam;
+    float lam_s = 0.0f;
+    if (cool) {
+      const float nHf = d2f_int(nH), nHef = d2f_int(nHe);
+      lam_s = RateEval<true>::cooling_scaled(s.T, d2f_int(ne0), nHf * d2f_int(s.xHI), nHf * d2f_int(s.xHII),
+                                             nHef * d2f_int(s.yI), nHef * d2f_int(s.yII), nHef * d2f_int(s.yIII));
+    }
+    const double e1 = e0 + heat_e - (dt * kCoolScale) * f2d_int(lam_s);
     const double ne2 = nH * t.xHII + nHe * (t.yII + 2.0 * t.yIII);
     const double ntot1 = nH * (1.0 + P.y_he) + ne2;
     t.T = e1 * rcp64(1.5 * kBoltzmann * ntot1);
