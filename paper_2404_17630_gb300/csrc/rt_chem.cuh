@@ -82,7 +82,30 @@ template <> struct RateEval<false> {
 __device__ __forceinline__ float fpow(float x, float p) { return exp2f(p * __log2f(x)); }
 __device__ __forceinline__ float fexp(float x) { return exp2f(x * 1.4426950408889634f); }
 
+struct RatesF {
+  float aHII, aHeII, aHeIII, bHI, bHeI, bHeII;
+};
+
 template <> struct RateEval<true> {
+  // the rate fits in FP32 (RateEval<true>::eval widens them)
+  __device__ static RatesF eval_f(double Td) {
+    const float T = d2f_int(Td);
+    const float iT = __frcp_rn(T);
+    RatesF r;
+    const float lH = 315614.0f * iT;
+    r.aHII = 2.753e-14f * fpow(lH, 1.5f) / fpow(1.0f + fpow(lH * (1.0f / 2.740f), 0.407f), 2.242f);
+    const float lHe = 570670.0f * iT;
+    r.aHeII = 1.26e-14f * fpow(lHe, 0.750f) +
+              1.9e-3f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT));
+    const float lHe2 = 1263030.0f * iT;
+    r.aHeIII = 2.0f * 2.753e-14f * fpow(lHe2, 1.5f) / fpow(1.0f + fpow(lHe2 * (1.0f / 2.740f), 0.407f), 2.242f);
+    const float sT = sqrtf(T);
+    const float tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
+    r.bHI = 5.85e-11f * sT * fexp(-157809.1f * iT) * tf;
+    r.bHeI = 2.38e-11f * sT * fexp(-285335.4f * iT) * tf;
+    r.bHeII = 5.68e-12f * sT * fexp(-631515.0f * iT) * tf;
+    return r;
+  }
   __device__ static Rates eval(double Td) {
     float T = d2f_int(Td);
     float iT = __frcp_rn(T);
@@ -290,7 +313,9 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   const double cdt = c * dt;
   const double nHe = P.y_he * nH;
   const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
-  const Rates r = RateEval<true>::eval(s.T);
+  // rate coefficients and their products with n_e in FP32 (the fits carry
+  // FP32 accuracy already); the photoionisation terms and the updates FP64
+  const RatesF r = RateEval<true>::eval_f(s.T);
 
   const double ns[3] = {nH * s.xHI, nHe * s.yI, nHe * s.yII};
   double inv1pt[kMaxBins], Nbar[kMaxBins];
@@ -313,16 +338,18 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   }
   const double G0 = Gs[0], G1 = Gs[1], G2 = Gs[2];
   const double ne0 = nH * s.xHII + nHe * (s.yII + 2.0 * s.yIII);
-  const double aH = cdt * G0 + (coll ? dt * r.bHI * ne0 : 0.0);
-  const double bH = recomb ? dt * r.aHII * ne0 : 0.0;
+  const float ne0f = d2f_int(ne0);
+  const double aH = coll ? fma(dt, f2d_int(r.bHI * ne0f), cdt * G0) : cdt * G0;
+  const double bH = recomb ? dt * f2d_int(r.aHII * ne0f) : 0.0;
   const double iden = rcp64(1.0 + aH + bH);
   t.xHI = (s.xHI * (1.0 + bH) + bH * s.xHII) * iden;
   t.xHII = (s.xHII * (1.0 + aH) + aH * s.xHI) * iden;
   const double ne1 = nH * t.xHII + nHe * (s.yII + 2.0 * s.yIII);
-  const double A = cdt * G1 + (coll ? dt * r.bHeI * ne1 : 0.0);
-  const double Bb = recomb ? dt * r.aHeII * ne1 : 0.0;
-  const double Cc = cdt * G2 + (coll ? dt * r.bHeII * ne1 : 0.0);
-  const double D = recomb ? dt * r.aHeIII * ne1 : 0.0;
+  const float ne1f = d2f_int(ne1);
+  const double A = coll ? fma(dt, f2d_int(r.bHeI * ne1f), cdt * G1) : cdt * G1;
+  const double Bb = recomb ? dt * f2d_int(r.aHeII * ne1f) : 0.0;
+  const double Cc = coll ? fma(dt, f2d_int(r.bHeII * ne1f), cdt * G2) : cdt * G2;
+  const double D = recomb ? dt * f2d_int(r.aHeIII * ne1f) : 0.0;
   const double iA = rcp64(1.0 + A), iD = rcp64(1.0 + D);
   t.yII = (s.yII + A * s.yI * iA + D * s.yIII * iD) * rcp64(1.0 + Bb * iA + Cc * iD);
   t.yI = (s.yI + Bb * t.yII) * iA;
@@ -361,23 +388,29 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
       sc_out[b] = sc;
     }
   }
-  const double heat_e = heat ? (cdt * kHeatScale) * f2d_int(hsum) : 0.0;
+
   const float fl = (float)P.x_floor;
   float f = 0.0f;
   if (P.mode == 2) {
-    const double ntot0 = nH * (1.0 + P.y_he) + ne0;
-    const double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
+    // thermal energy, explicit: e' = e + heat - dt Lambda with e = 3/2 k n_tot T,
+    // written as T' = T + (de / (3/2 k) - T dn_e) / n_tot' so that only the
+    // change of n_e is FP64 and the increment is formed in FP32
     float lam_s = 0.0f;
     if (cool) {
       const float nHf = d2f_int(nH), nHef = d2f_int(nHe);
-      lam_s = RateEval<true>::cooling_scaled(s.T, d2f_int(ne0), nHf * d2f_int(s.xHI), nHf * d2f_int(s.xHII),
+      lam_s = RateEval<true>::cooling_scaled(s.T, ne0f, nHf * d2f_int(s.xHI), nHf * d2f_int(s.xHII),
                                              nHef * d2f_int(s.yI), nHef * d2f_int(s.yII), nHef * d2f_int(s.yIII));
     }
-    const double e1 = e0 + heat_e - (dt * kCoolScale) * f2d_int(lam_s);
-    const double ne2 = nH * t.xHII + nHe * (t.yII + 2.0 * t.yIII);
-    const double ntot1 = nH * (1.0 + P.y_he) + ne2;
-    t.T = e1 * rcp64(1.5 * kBoltzmann * ntot1);
-    f = rel_change_f(e0, e1, 0.0f);
+    const float de = fmaf(heat ? d2f_int(cdt * kHeatScale) : 0.0f, hsum, -(d2f_int(dt * kCoolScale) * lam_s));
+    const double dne = nH * (t.xHII - s.xHII) + nHe * ((t.yII - s.yII) + 2.0 * (t.yIII - s.yIII));
+    const float dnef = d2f_int(dne);
+    const float T0 = d2f_int(s.T);
+    const float ntot0 = d2f_int(nH) * (1.0f + (float)P.y_he) + ne0f;
+    const float ntot1 = ntot0 + dnef;
+    constexpr float kInv15k = (float)(1.0 / (1.5 * kBoltzmann));
+    t.T = s.T + f2d_int(__fdividef(fmaf(de, kInv15k, -T0 * dnef), ntot1));
+    // the measure |e' - e| / |e| = |de| / (3/2 k n_tot T)
+    f = __fdividef(fabsf(de) * kInv15k, ntot0 * T0);
   } else {
     t.T = s.T;
   }
