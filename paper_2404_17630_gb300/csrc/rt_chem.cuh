@@ -367,13 +367,10 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
-      double a[3] = {0.0, 0.0, 0.0}, suma = 0.0;
+      double suma = 0.0;
 #pragma unroll
       for (int sp = 0; sp < 3; ++sp)
-        if (P.smask & (1 << (3 * b + sp))) {
-          a[sp] = P.sigma[b][sp] * m[sp];
-          suma += a[sp];
-        }
+        if (P.smask & (1 << (3 * b + sp))) suma = fma(P.sigma[b][sp], m[sp], suma);
       const double taup = cdt * suma;
       double sc = fma(-taup, inv1pt[b], 1.0);
       sc = sc > 0.0 ? sc : 0.0;
