@@ -316,7 +316,7 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
 # FP64 work of one chemistry attempt of the mixed path (2 x DFMA + DMUL + DADD
 # thread instructions, from ncu on the 2e5-cell workload in steady state,
 # one attempt per cell): the unit count behind k_chem's ALU roofline.
-FP64_FLOP_PER_ATTEMPT = {"mixed": 250.0, "fp64": None}  # re-measured after each change of k_chem
+FP64_FLOP_PER_ATTEMPT = {"mixed": 176.0, "fp64": None}  # re-measured after each change of k_chem
 # GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
 # clock per SM (ncu: 16 cycles per warp instruction on the FP64 pipe) x 2 FLOP
 # x 2.07 GHz = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s.
