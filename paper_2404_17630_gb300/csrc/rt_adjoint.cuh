@@ -402,7 +402,7 @@ __device__ CoolCoef cooling_coef(double T) {
   return c;
 }
 
-// Reverse of one attempt (photochem_attempt<false>): lt = cotangent of the
+// Reverse of one attempt (photochem_attempt): lt = cotangent of the
 // output state, lf = of the substep measure; accumulates into ls (input
 // state, T included: through the rate fits, and in mode 2 the energy
 // equation), ldt, lnH.
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(128) k_chem_tape(ChemAdjArgs a, ChemParams P) 
       out[n].dt = dt;
       out[n].rem = rem;
     }
-    const double f = photochem_attempt<false>(P, nH, dt, s, t);
+    const double f = photochem_attempt(P, nH, dt, s, t);
     if (out) out[n].f = f;
     ++n;
     if (f > P.f_max) {

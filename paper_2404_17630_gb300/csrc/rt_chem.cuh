@@ -87,7 +87,7 @@ struct RatesF {
 };
 
 template <> struct RateEval<true> {
-  // the rate fits in FP32 (RateEval<true>::eval widens them)
+  // the rate fits in FP32
   __device__ static RatesF eval_f(double Td) {
     const float T = d2f_int(Td);
     const float iT = __frcp_rn(T);
@@ -105,45 +105,6 @@ template <> struct RateEval<true> {
     r.bHeI = 2.38e-11f * sT * fexp(-285335.4f * iT) * tf;
     r.bHeII = 5.68e-12f * sT * fexp(-631515.0f * iT) * tf;
     return r;
-  }
-  __device__ static Rates eval(double Td) {
-    float T = d2f_int(Td);
-    float iT = __frcp_rn(T);
-    Rates r;
-    float lH = 315614.0f * iT;
-    r.aHII = f2d_int(2.753e-14f * fpow(lH, 1.5f) / fpow(1.0f + fpow(lH * (1.0f / 2.740f), 0.407f), 2.242f));
-    float lHe = 570670.0f * iT;
-    r.aHeII = f2d_int(1.26e-14f * fpow(lHe, 0.750f) +
-                      1.9e-3f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT)));
-    float lHe2 = 1263030.0f * iT;
-    r.aHeIII = f2d_int(2.0f * 2.753e-14f * fpow(lHe2, 1.5f) / fpow(1.0f + fpow(lHe2 * (1.0f / 2.740f), 0.407f), 2.242f));
-    float sT = sqrtf(T);
-    float tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
-    r.bHI = f2d_int(5.85e-11f * sT * fexp(-157809.1f * iT) * tf);
-    r.bHeI = f2d_int(2.38e-11f * sT * fexp(-285335.4f * iT) * tf);
-    r.bHeII = f2d_int(5.68e-12f * sT * fexp(-631515.0f * iT) * tf);
-    return r;
-  }
-  __device__ static double cooling(double Td, double ne, double nHI, double nHII, double nHeI, double nHeII,
-                                   double nHeIII) {
-    float T = d2f_int(Td), iT = __frcp_rn(T);
-    float sT = sqrtf(T), tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
-    // coefficients in FP32 (erg cm^3 s^-1 scale fits FP32), densities in FP64
-    const double c_ceH = f2d_int(7.50e-19f * fexp(-118348.0f * iT) * tf);
-    const double c_ceHe = f2d_int(5.54e-17f * fpow(T, -0.397f) * fexp(-473638.0f * iT) * tf);
-    const double c_ciH = f2d_int(1.27e-21f * sT * fexp(-157809.1f * iT) * tf);
-    const double c_ciHe = f2d_int(9.38e-22f * sT * fexp(-285335.4f * iT) * tf);
-    const double c_ciHe2 = f2d_int(4.95e-22f * sT * fexp(-631515.0f * iT) * tf);
-    float t3 = fpow(T * 1e-3f, -0.2f) / (1.0f + fpow(T * 1e-6f, 0.7f));
-    const double c_rH = f2d_int(8.70e-27f * sT * t3);
-    const double c_rHe = f2d_int(1.55e-26f * fpow(T, 0.3647f));
-    const double c_rHe2 = f2d_int(3.48e-26f * sT * t3);
-    const double c_di = f2d_int(1.24e-13f * fpow(T, -1.5f) * fexp(-470000.0f * iT) * (1.0f + 0.3f * fexp(-94000.0f * iT)));
-    float lg = __log10f(T);
-    const double c_br = f2d_int(1.42e-27f * (1.1f + 0.34f * fexp(-(5.5f - lg) * (5.5f - lg) * (1.0f / 3.0f))) * sT);
-    return ne * (c_ceH * nHI + c_ceHe * nHeII + c_ciH * nHI + c_ciHe * nHeI + c_ciHe2 * nHeII +
-                 c_rH * nHII + c_rHe * nHeII + c_rHe2 * nHeIII + c_di * nHeII +
-                 c_br * (nHII + nHeII + 4.0 * nHeIII));
   }
   // The same cooling rate divided by kCoolScale, entirely in FP32 from the
   // FP32 images of the densities (the coefficients, ~1e-27..1e-19, times
@@ -190,13 +151,12 @@ __device__ __forceinline__ double rel_change(double a, double b, double fl) {
 // rates from it; backward Euler for H, then for He with the updated n_e;
 // photons removed = photoionisations credited (absorbers at the end), F scaled
 // alike; thermal energy explicit.
-template <bool Fast>
 __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, const CellState& s, CellState& t) {
   const int B = P.B;
   const double c = P.c_red;
   const double nHe = P.y_he * nH;
   const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
-  const Rates r = RateEval<Fast>::eval(s.T);
+  const Rates r = RateEval<false>::eval(s.T);
 
   double ns0 = nH * s.xHI, ns1 = nHe * s.yI, ns2 = nHe * s.yII;
   double Nbar[kMaxBins];
@@ -249,7 +209,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   if (P.mode == 2) {
     double ntot0 = nH * (1.0 + P.y_he) + ne0;
     double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
-    double lam = cool ? RateEval<Fast>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
+    double lam = cool ? RateEval<false>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
                                                 nHe * s.yIII)
                       : 0.0;
     double e1 = e0 + (heat ? heat_e : 0.0) - dt * lam;
@@ -489,7 +449,7 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
   while (rem > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;
-    double f = photochem_attempt<false>(P, nH, dt, s, t);
+    double f = photochem_attempt(P, nH, dt, s, t);
     if (f > P.f_max) {
       dt = dt * (P.f_s / f);
       continue;

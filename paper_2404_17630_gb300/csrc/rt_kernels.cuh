@@ -86,15 +86,6 @@ __global__ void k_geometry_cells(int C, double box, const int32_t* __restrict__ 
   o[5] = (m00 * m11 - m01 * m01) / det;
 }
 
-template <class R> __global__ void k_convert4(int n, const d4* __restrict__ in, R4<R>* out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  d4 v = in[k];
-  R4<R> o;
-  o.x = (R)v.x; o.y = (R)v.y; o.z = (R)v.z; o.w = (R)v.w;
-  out[k] = o;
-}
-
 // Half-edge records in CSR order for the gradient kernel: the face's
 // least-squares weight with the sign that makes the contribution
 // w_k (phi_neighbour - phi_cell), the neighbour id, and the face-centre
