@@ -68,7 +68,15 @@ void free_active(rt_ctx* ctx) {
   ctx->n_act = ctx->n_touched = ctx->n_act_faces = ctx->n_grad_blocks = 0;
 }
 
+void drop_graph(rt_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->g_gen = 0;
+}
+
 void free_all(rt_ctx* ctx) {
+  drop_graph(ctx);
+  ctx->gen++;
   free_active(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
@@ -347,6 +355,7 @@ rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
 rt_status rt_set_stream(rt_ctx* ctx, void* stream) {
   if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
   ctx->stream = (cudaStream_t)stream;
+  ctx->gen++;
   return RT_OK;
 }
 
@@ -594,6 +603,7 @@ rt_status rt_set_sources(rt_ctx* ctx, int64_t n, const int64_t* cell, const doub
     CK(cudaMemcpyAsync(ctx->src_rate, rate.data(), (size_t)m * B * 8, cudaMemcpyHostToDevice, ctx->stream),
        "sources");
   CK(cudaStreamSynchronize(ctx->stream), "sources");
+  ctx->gen++;   // the source pointer and count are launch arguments
   ctx->n_src_cells = m;
   ctx->src_cells.assign(hc.begin(), hc.end());
   return RT_OK;
@@ -622,6 +632,7 @@ rt_status rt_set_active(rt_ctx* ctx, const uint8_t* active) {
   // the lists may be in use by work already enqueued
   CK(cudaStreamSynchronize(ctx->stream), "rt_set_active");
   free_active(ctx);
+  ctx->gen++;
   if (!active) return RT_OK;
   const int C = ctx->C, F = ctx->F, B = ctx->B;
   std::vector<uint8_t> m(C);
@@ -688,6 +699,38 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   const double dmax = ctx->cfg.cfl * ctx->min_dx_cm / ctx->cfg.c_red;
   if (dts > dmax * (1.0 + 1e-12))
     return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
+  // Replay the captured graph of this step if nothing it depends on changed.
+  if (ctx->gexec && ctx->g_gen == ctx->gen && ctx->g_dt == dt && ctx->g_nsub == n_sub && !ctx->profiling) {
+    CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "rt_step graph");
+    ctx->launches += ctx->g_launches;
+    return RT_OK;
+  }
+  // Otherwise capture the step's launches into a graph -- on an internal
+  // stream, so that any stream of the caller (the legacy default included)
+  // can replay it -- and launch it.  Not while profiling with events, nor
+  // when the caller's stream is itself being captured (the launches then
+  // become part of the caller's graph).
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  bool capture = !ctx->profiling && cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess &&
+                 cs == cudaStreamCaptureStatusNone;
+  cudaGetLastError();
+  if (capture && !ctx->cap_stream &&
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->cap_stream = nullptr;
+    capture = false;
+  }
+  cudaStream_t user = ctx->stream;
+  if (capture) {
+    drop_graph(ctx);
+    ctx->stream = ctx->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      ctx->stream = user;
+      return cuda_fail(ctx, e, "rt_step capture");
+    }
+  }
+  const int64_t l0 = ctx->launches;
   // Subcycle: sources + chemistry, gradients, fluxes, application (Lie);
   // Strang puts half the chemistry on each side of the transport.
   const bool strang = ctx->cfg.splitting == 1;
@@ -696,7 +739,23 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
     transport(ctx, dts);
     if (strang) launch_chem(ctx, 0.5 * dts);
   }
-  return launched(ctx, "rt_step");
+  if (!capture) return launched(ctx, "rt_step");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  ctx->stream = user;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "rt_step capture");
+  e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    ctx->gexec = nullptr;
+    return cuda_fail(ctx, e, "rt_step graph");
+  }
+  ctx->g_gen = ctx->gen;
+  ctx->g_dt = dt;
+  ctx->g_nsub = n_sub;
+  ctx->g_launches = ctx->launches - l0;
+  CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "rt_step graph");
+  return RT_OK;
 }
 
 rt_status rt_sync(rt_ctx* ctx) {
@@ -1118,6 +1177,8 @@ const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : g
 void rt_destroy(rt_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   adj_free(ctx);
   free_all(ctx);

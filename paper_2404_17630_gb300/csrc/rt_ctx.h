@@ -62,6 +62,15 @@ struct rt_ctx {
   std::vector<void*> allocs;
   // profiling: event pairs around launches, per kernel class
   bool profiling = false;
+  // rt_step as a CUDA graph: captured on first use for a (dt, n_sub) and a
+  // generation of the launch arguments (mesh, sources, active lists), then
+  // replayed; gen is bumped by every call that changes kernel arguments
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // internal stream the step is captured on
+  double g_dt = 0.0;
+  int g_nsub = 0;
+  uint64_t gen = 1, g_gen = 0;
+  int64_t g_launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_used;   // (class, index of start event)
   double prof_ms[RT_KERNEL_COUNT] = {};

@@ -169,6 +169,29 @@ def test_hii_region_staggered_grid():
     print("HII region mixed vs oracle", compare_state(g32, o, 1e-4))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_repeated_steps_replay_the_step_graph(precision):
+    """rt_step captures its launches as a CUDA graph and replays it while dt,
+    n_sub and the launch arguments are unchanged: three equal steps, a
+    change of sources (the graph is rebuilt), two more steps; against the
+    oracle after each."""
+    mesh, cfg, st = voronoi_case(n=10, n_src=3)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    dt = 2 * o.max_dt()
+    tol = TOL64 if precision == "fp64" else 1e-4
+    for k in range(5):
+        if k == 3:
+            cells = np.array([5, 77], dtype=np.int64)
+            Q = np.outer([3e50, 1e49], synth.SPECTRAL_SPLIT_E4)
+            o.set_sources(cells, Q)
+            rt.set_sources(cells, Q)
+        assert o.step(dt, 2) == 0
+        rt.step(dt, 2)
+        assert rt.sync() == 0
+        compare_state(rt, o, tol)
+
+
 @pytest.mark.parametrize("precision,time_order", [("fp64", 1), ("fp64", 2), ("mixed", 1)])
 def test_individual_timesteps(precision, time_order):
     """Individual time steps: 30% of the cells active (a seeded mask), then
