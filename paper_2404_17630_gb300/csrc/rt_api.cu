@@ -59,23 +59,48 @@ template <class T> rt_status dalloc(rt_ctx* ctx, T** p, size_t n, const char* wh
   return RT_OK;
 }
 
-void free_active(rt_ctx* ctx) {
-  for (void* p : ctx->act_allocs) cudaFree(p);
-  ctx->act_allocs.clear();
-  ctx->all_active = true;
-  ctx->act_cells = ctx->touched_cells = ctx->act_faces = ctx->grad_blocks = nullptr;
-  ctx->touched = nullptr;
-  ctx->n_act = ctx->n_touched = ctx->n_act_faces = ctx->n_grad_blocks = 0;
+void drop_graph(rt_ctx::GraphSlot& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g = rt_ctx::GraphSlot();
 }
 
-void drop_graph(rt_ctx* ctx) {
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-  ctx->gexec = nullptr;
-  ctx->g_gen = 0;
+void free_set(rt_ctx::ActSet& a) {
+  for (void* p : a.allocs) cudaFree(p);
+  drop_graph(a.graph);
+  a = rt_ctx::ActSet();
+}
+
+rt_ctx::GraphSlot& cur_graph(rt_ctx* ctx) {
+  return ctx->cur_set < 0 ? ctx->all_graph : ctx->sets[ctx->cur_set].graph;
+}
+
+// Make set k (-1: every cell active) the current one: the launchers read
+// its lists through the context's view fields.
+void use_set(rt_ctx* ctx, int k) {
+  ctx->cur_set = k;
+  if (k < 0) {
+    ctx->all_active = true;
+    ctx->act_cells = ctx->touched_cells = ctx->act_faces = ctx->grad_blocks = nullptr;
+    ctx->touched = nullptr;
+    ctx->n_act = ctx->n_touched = ctx->n_act_faces = ctx->n_grad_blocks = 0;
+    return;
+  }
+  rt_ctx::ActSet& a = ctx->sets[k];
+  a.used = ++ctx->use_clock;
+  ctx->all_active = false;
+  ctx->act_cells = a.act_cells; ctx->touched_cells = a.touched_cells; ctx->act_faces = a.act_faces;
+  ctx->grad_blocks = a.grad_blocks; ctx->touched = a.touched;
+  ctx->n_act = a.n_act; ctx->n_touched = a.n_touched; ctx->n_act_faces = a.n_act_faces;
+  ctx->n_grad_blocks = a.n_grad_blocks;
+}
+
+void free_active(rt_ctx* ctx) {
+  for (auto& a : ctx->sets) free_set(a);
+  drop_graph(ctx->all_graph);
+  use_set(ctx, -1);
 }
 
 void free_all(rt_ctx* ctx) {
-  drop_graph(ctx);
   ctx->gen++;
   free_active(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
@@ -631,63 +656,94 @@ rt_status rt_set_active(rt_ctx* ctx, const uint8_t* active) {
   if (st) return st;
   // the lists may be in use by work already enqueued
   CK(cudaStreamSynchronize(ctx->stream), "rt_set_active");
-  free_active(ctx);
-  ctx->gen++;
-  if (!active) return RT_OK;
   const int C = ctx->C, F = ctx->F, B = ctx->B;
-  std::vector<uint8_t> m(C);
-  CK(cudaMemcpy(m.data(), active, (size_t)C, is_device_ptr(active) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
-     "active mask");
+  const int prev = ctx->cur_set;
+  std::vector<uint8_t> m;
   bool all = true;
-  for (int i = 0; i < C; ++i) {
-    m[i] = m[i] != 0;
-    all = all && m[i];
-  }
-  if (all) return RT_OK;
-  std::vector<int2> lr(F);
-  if (F > 0) CK(cudaMemcpy(lr.data(), ctx->lr, (size_t)F * sizeof(int2), cudaMemcpyDeviceToHost), "active mask");
-  std::vector<int32_t> ac, tc, af, gb;
-  std::vector<uint8_t> tf(C, 0);
-  for (int i = 0; i < C; ++i)
-    if (m[i]) ac.push_back(i);
-  for (int f = 0; f < F; ++f)
-    if (m[lr[f].x] || m[lr[f].y]) {
-      af.push_back(f);
-      tf[lr[f].x] = tf[lr[f].y] = 1;
+  if (active) {
+    m.resize(C);
+    CK(cudaMemcpy(m.data(), active, (size_t)C, is_device_ptr(active) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost),
+       "active mask");
+    for (int i = 0; i < C; ++i) {
+      m[i] = m[i] != 0;
+      all = all && m[i];
     }
-  for (int i = 0; i < C; ++i)
-    if (tf[i]) tc.push_back(i);
-  for (int c0 = 0; c0 < C; c0 += kGradCells) {
-    bool any = false;
-    for (int i = c0; i < std::min(c0 + kGradCells, C) && !any; ++i) any = tf[i];
-    if (any) gb.push_back(c0 / kGradCells);
   }
-  auto up = [&](const void* src, size_t bytes, void** dst) -> rt_status {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
-    ctx->act_allocs.push_back(p);
-    if (bytes) {
-      e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
-    }
-    *dst = p;
+  if (all) {
+    use_set(ctx, -1);
     return RT_OK;
-  };
-  if ((st = up(ac.data(), ac.size() * 4, (void**)&ctx->act_cells))) return st;
-  if ((st = up(tc.data(), tc.size() * 4, (void**)&ctx->touched_cells))) return st;
-  if ((st = up(af.data(), af.size() * 4, (void**)&ctx->act_faces))) return st;
-  if ((st = up(gb.data(), gb.size() * 4, (void**)&ctx->grad_blocks))) return st;
-  if ((st = up(tf.data(), tf.size(), (void**)&ctx->touched))) return st;
-  ctx->n_act = (int)ac.size();
-  ctx->n_touched = (int)tc.size();
-  ctx->n_act_faces = (int)af.size();
-  ctx->n_grad_blocks = (int)gb.size();
-  ctx->all_active = false;
-  // the face kernel writes the active interfaces only: the others carry no
-  // flux while this mask holds
-  const size_t rs = mixed(ctx) ? 4 : 8;
-  CK(cudaMemsetAsync(ctx->flux, 0, (size_t)F * B * 4 * rs, ctx->stream), "active mask");
+  }
+  // a mask seen recently keeps its lists and its step graph
+  uint64_t h = 1469598103934665603ull;   // FNV-1a
+  for (uint8_t v : m) h = (h ^ v) * 1099511628211ull;
+  int k = -1;
+  for (int j = 0; j < rt_ctx::kMaxActSets && k < 0; ++j)
+    if (ctx->sets[j].valid && ctx->sets[j].hash == h && ctx->sets[j].mask == m) k = j;
+  if (k < 0) {
+    // a free slot, else the least recently used one
+    for (int j = 0; j < rt_ctx::kMaxActSets && k < 0; ++j)
+      if (!ctx->sets[j].valid) k = j;
+    if (k < 0) {
+      k = 0;
+      for (int j = 1; j < rt_ctx::kMaxActSets; ++j)
+        if (ctx->sets[j].used < ctx->sets[k].used) k = j;
+    }
+    rt_ctx::ActSet& a = ctx->sets[k];
+    free_set(a);
+    std::vector<int2> lr(F);
+    if (F > 0) CK(cudaMemcpy(lr.data(), ctx->lr, (size_t)F * sizeof(int2), cudaMemcpyDeviceToHost), "active mask");
+    std::vector<int32_t> ac, tc, af, gb;
+    std::vector<uint8_t> tf(C, 0);
+    for (int i = 0; i < C; ++i)
+      if (m[i]) ac.push_back(i);
+    for (int f = 0; f < F; ++f)
+      if (m[lr[f].x] || m[lr[f].y]) {
+        af.push_back(f);
+        tf[lr[f].x] = tf[lr[f].y] = 1;
+      }
+    for (int i = 0; i < C; ++i)
+      if (tf[i]) tc.push_back(i);
+    for (int c0 = 0; c0 < C; c0 += kGradCells) {
+      bool any = false;
+      for (int i = c0; i < std::min(c0 + kGradCells, C) && !any; ++i) any = tf[i];
+      if (any) gb.push_back(c0 / kGradCells);
+    }
+    auto up = [&](const void* src, size_t bytes, void** dst) -> rt_status {
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
+      a.allocs.push_back(p);
+      if (bytes) {
+        e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "active lists");
+      }
+      *dst = p;
+      return RT_OK;
+    };
+    if ((st = up(ac.data(), ac.size() * 4, (void**)&a.act_cells)) ||
+        (st = up(tc.data(), tc.size() * 4, (void**)&a.touched_cells)) ||
+        (st = up(af.data(), af.size() * 4, (void**)&a.act_faces)) ||
+        (st = up(gb.data(), gb.size() * 4, (void**)&a.grad_blocks)) ||
+        (st = up(tf.data(), tf.size(), (void**)&a.touched))) {
+      free_set(a);
+      use_set(ctx, -1);
+      return st;
+    }
+    a.n_act = (int)ac.size();
+    a.n_touched = (int)tc.size();
+    a.n_act_faces = (int)af.size();
+    a.n_grad_blocks = (int)gb.size();
+    a.hash = h;
+    a.mask.swap(m);
+    a.valid = true;
+  }
+  use_set(ctx, k);
+  if (k != prev) {
+    // the face kernel writes the active interfaces only: the others must
+    // carry no flux while this set holds
+    const size_t rs = mixed(ctx) ? 4 : 8;
+    CK(cudaMemsetAsync(ctx->flux, 0, (size_t)F * B * 4 * rs, ctx->stream), "active mask");
+  }
   return RT_OK;
 }
 
@@ -700,9 +756,10 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   if (dts > dmax * (1.0 + 1e-12))
     return fail(ctx, RT_CFL, "subcycle %g s exceeds the CFL limit %g s", dts, dmax);
   // Replay the captured graph of this step if nothing it depends on changed.
-  if (ctx->gexec && ctx->g_gen == ctx->gen && ctx->g_dt == dt && ctx->g_nsub == n_sub && !ctx->profiling) {
-    CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "rt_step graph");
-    ctx->launches += ctx->g_launches;
+  rt_ctx::GraphSlot& g = cur_graph(ctx);
+  if (g.exec && g.gen == ctx->gen && g.dt == dt && g.nsub == n_sub && !ctx->profiling) {
+    CK(cudaGraphLaunch(g.exec, ctx->stream), "rt_step graph");
+    ctx->launches += g.launches;
     return RT_OK;
   }
   // Otherwise capture the step's launches into a graph -- on an internal
@@ -722,7 +779,7 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   }
   cudaStream_t user = ctx->stream;
   if (capture) {
-    drop_graph(ctx);
+    drop_graph(g);
     ctx->stream = ctx->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
@@ -744,17 +801,17 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
   ctx->stream = user;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rt_step capture");
-  e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    ctx->gexec = nullptr;
+    g.exec = nullptr;
     return cuda_fail(ctx, e, "rt_step graph");
   }
-  ctx->g_gen = ctx->gen;
-  ctx->g_dt = dt;
-  ctx->g_nsub = n_sub;
-  ctx->g_launches = ctx->launches - l0;
-  CK(cudaGraphLaunch(ctx->gexec, ctx->stream), "rt_step graph");
+  g.gen = ctx->gen;
+  g.dt = dt;
+  g.nsub = n_sub;
+  g.launches = ctx->launches - l0;
+  CK(cudaGraphLaunch(g.exec, ctx->stream), "rt_step graph");
   return RT_OK;
 }
 
@@ -1177,7 +1234,6 @@ const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : g
 void rt_destroy(rt_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   adj_free(ctx);

@@ -44,7 +44,8 @@ struct rt_ctx {
   int32_t* work_cell = nullptr;  // mixed chemistry worklist (cells whose first attempt was rejected)
   float* work_f1 = nullptr;
   int* work_ctl = nullptr;       // entries, next entry, finished blocks (zero between subcycles)
-  // individual time steps (all null / zero when every cell is active)
+  // individual time steps: the lists of the current active set (all null /
+  // zero when every cell is active), a view of one entry of `sets`
   bool all_active = true;
   int32_t* act_cells = nullptr;      // active cells
   int32_t* touched_cells = nullptr;  // cells with an active interface
@@ -52,7 +53,6 @@ struct rt_ctx {
   int32_t* grad_blocks = nullptr;    // gradient blocks holding a touched cell
   uint8_t* touched = nullptr;        // per cell: has an active interface
   int n_act = 0, n_touched = 0, n_act_faces = 0, n_grad_blocks = 0;
-  std::vector<void*> act_allocs;      // 1 / V (mixed-precision flux application)
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision
   void* flux = nullptr;        // [F][B] 4-vectors in sweep precision
@@ -62,15 +62,34 @@ struct rt_ctx {
   std::vector<void*> allocs;
   // profiling: event pairs around launches, per kernel class
   bool profiling = false;
-  // rt_step as a CUDA graph: captured on first use for a (dt, n_sub) and a
-  // generation of the launch arguments (mesh, sources, active lists), then
-  // replayed; gen is bumped by every call that changes kernel arguments
-  cudaGraphExec_t gexec = nullptr;
+  // rt_step as a CUDA graph, one per active set: captured on first use for a
+  // (dt, n_sub) and a generation of the launch arguments (mesh, sources,
+  // stream), then replayed; gen is bumped by every call that changes them
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int nsub = 0;
+    uint64_t gen = 0;
+    int64_t launches = 0;
+  };
+  // the last few active sets of rt_set_active (a time-step hierarchy cycles
+  // through a few masks): their masks, device lists and step graphs
+  struct ActSet {
+    bool valid = false;
+    uint64_t hash = 0, used = 0;
+    std::vector<uint8_t> mask;
+    int32_t *act_cells = nullptr, *touched_cells = nullptr, *act_faces = nullptr, *grad_blocks = nullptr;
+    uint8_t* touched = nullptr;
+    int n_act = 0, n_touched = 0, n_act_faces = 0, n_grad_blocks = 0;
+    std::vector<void*> allocs;
+    GraphSlot graph;
+  };
+  static constexpr int kMaxActSets = 8;
+  ActSet sets[kMaxActSets];
+  int cur_set = -1;                    // -1: every cell active
+  GraphSlot all_graph;                 // the step graph with every cell active
+  uint64_t gen = 1, use_clock = 0;
   cudaStream_t cap_stream = nullptr;   // internal stream the step is captured on
-  double g_dt = 0.0;
-  int g_nsub = 0;
-  uint64_t gen = 1, g_gen = 0;
-  int64_t g_launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_used;   // (class, index of start event)
   double prof_ms[RT_KERNEL_COUNT] = {};

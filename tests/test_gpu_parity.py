@@ -212,6 +212,29 @@ def test_individual_timesteps(precision, time_order):
         compare_state(rt, o, TOL64 if precision == "fp64" else 1e-4)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_time_step_hierarchy_reuses_sets(precision):
+    """A hierarchy cycles through a few masks: the library keeps each
+    mask's lists and step graph and returns to them (the fluxes of the
+    interfaces a set leaves inactive are cleared on every switch); a cycle
+    of masks with repeats and an all-active step, against the oracle."""
+    mesh, cfg, st = voronoi_case(n=10, n_src=4)
+    rng = np.random.default_rng(21)
+    m1 = rng.uniform(size=mesh.n_cells) < 0.25
+    m2 = rng.uniform(size=mesh.n_cells) < 0.5
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    dt = o.max_dt()
+    tol = TOL64 if precision == "fp64" else 1e-4
+    for m in (m1, m2, m1, None, m2, m1, m1):
+        o.set_active(m)
+        rt.set_active(m)
+        assert o.step(2 * dt, 2) == 0
+        rt.step(2 * dt, 2)
+        assert rt.sync() == 0
+        compare_state(rt, o, tol)
+
+
 @pytest.mark.parametrize("splitting,time_order", [(1, 1), (0, 2), (1, 2)])
 def test_step_variants_fp64(splitting, time_order):
     """Strang splitting and Heun transport (second order in time), with
