@@ -553,6 +553,64 @@ def measure_timebins(dev, n_steps=8):
             "ms_masked": ms_masked, "ms_all_active": ms_all, "time_ratio": ms_masked / ms_all}
 
 
+def measure_config5(dev, n=256, n_sub=200, adj_sub=20, k=20):
+    """The large box: Voronoi mesh of a 256^3 jittered lattice (16.8M cells,
+    7.16 Mpc, exp(GRF) density as the THESAN-like box, 32768 peak sources,
+    c_red = 0.2 c).  Mixed forward of one step of n_sub subcycles (after one
+    warm-up step); then the FP64 reverse mode over adj_sub subcycles with a
+    checkpoint every k (the reverse mode over all 200 subcycles takes ~15
+    minutes at the measured rate, beyond a bench run).  Reports cell-updates/s
+    and the device memory in use (cudaMemGetInfo) at the end of each part."""
+    import torch
+    import synth
+    from paper_2404_17630_gb300 import RT, make_config
+    t0 = time.perf_counter()
+    mesh, cfg, state = synth.thesan_like(n, 10, 32768, 7160.0, 256)
+    build_s = time.perf_counter() - t0
+    C = mesh.n_cells
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"voronoi {n}^3 ({C} cells, {mesh.n_faces} faces), GRF n_H, 32768 peak sources, c_red 0.2c",
+           "mesh_build_s": round(build_s, 1)}
+    free0, total = torch.cuda.mem_get_info(dev)
+    rt = RT(make_config(precision="mixed", gather_sum=1, **cfg), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dt = rt.max_dt() * n_sub
+    rt.step(dt, n_sub)
+    rt.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rt.step(dt, n_sub)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    rt.sync()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    out["forward_mixed"] = {"value": C * n_sub / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "n_sub": n_sub,
+                            "device_GB_in_use": round((free0 - free1) / 1e9, 1)}
+    del rt
+    torch.cuda.synchronize(dev)
+    rt = RT(make_config(precision="fp64", **dict(cfg, chem_mode=2)), mesh, stream=stream)
+    rt.set_gas(state["nH"], state["x5"], state["T"])
+    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+    rt.set_sources(state["cells"], state["Q"])
+    dta = rt.max_dt() * adj_sub
+    lx = np.zeros((5, C))
+    lx[1] = state["nH"] * mesh.volume / (state["nH"] * mesh.volume).sum()
+    t1 = time.perf_counter()
+    res = rt.adjoint(dta, adj_sub, k, lam_x5=torch.as_tensor(lx, device=dev), n_src=len(state["cells"]))
+    torch.cuda.synchronize(dev)
+    adj_s = time.perf_counter() - t1
+    free2, _ = torch.cuda.mem_get_info(dev)
+    out["adjoint_fp64"] = {"value": C * adj_sub / adj_s, "unit": UNIT, "seconds": round(adj_s, 2),
+                           "n_sub": adj_sub, "checkpoint_every": k,
+                           "device_GB_in_use": round((free0 - free2) / 1e9, 1),
+                           "dL_dQ_finite": bool(np.isfinite(res["dQ"]).all())}
+    del rt
+    return out
+
+
 def measure_adjoint(dev, n=64, n_sub=50, k=10):
     """FP64 forward and reverse mode on the 262k-cell differentiable workload."""
     import torch
@@ -608,6 +666,8 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 2.1M-cell THESAN-like run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode run")
     ap.add_argument("--no-hii", action="store_true", help="skip the HII-region and time-step-hierarchy runs")
+    ap.add_argument("--config5", action="store_true",
+                    help="also run the 16.8M-cell box (forward and reverse mode; minutes, ~170 GB of device memory)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -650,6 +710,7 @@ def main():
     large = None if args.no_large else measure_large(3, 1, dev)
     adjoint = None if args.no_adjoint else measure_adjoint(dev)
     hii = None if args.no_hii else measure_hii(3, 1, dev)
+    config5 = measure_config5(dev) if args.config5 else None
     timebins = None if args.no_hii else measure_timebins(dev)
     if rank != 0:
         return
@@ -674,6 +735,7 @@ def main():
         "mixed_fp64_sums": fp64sum,
         "e2e": e2e, "cpu_baseline": cpu,
         "thesan_like_2M": large, "adjoint": adjoint, "hii_region": hii, "individual_timesteps": timebins,
+        "box_16M": config5,
         "gpu_launches": res["launches"], "clocks": cl,
     }
     print(json.dumps(out))
