@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
 // state; afterwards the only global loads left per face are the neighbour
 // states, issued NB at a time.  `cap` is the largest record count of any
 // block (the dynamic shared memory holds 2 cap records).
-constexpr int kGradCells = 64;
+constexpr int kGradCells = 32;
 
 template <int NB>
 __global__ void __launch_bounds__(kGradCells* kMaxBins)
@@ -562,7 +562,7 @@ template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0,
 
 // flux[f*B + b] = A (Phi_N, Phi_F) / c_red, global Lax-Friedrichs at c_red.
 template <class R>
-__global__ void __launch_bounds__(256) k_flux(Geo<R> g, const R4<R>* __restrict__ rad, const R* __restrict__ G,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 1) k_flux(Geo<R> g, const R4<R>* __restrict__ rad, const R* __restrict__ G,
                                               R4<R>* __restrict__ flux) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
