@@ -16,7 +16,7 @@ using namespace m1rt;
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 64;
 inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 thread_local std::string g_create_error;
