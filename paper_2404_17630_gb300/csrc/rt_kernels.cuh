@@ -490,9 +490,10 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
       v[1] *= s; v[2] *= s; v[3] *= s;
     }
   } else {
-    R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-    if (fl > v[0]) {
-      R s = fl > R(0) ? v[0] / fl : R(0);
+    // |F| > c N tested on squares; the square root only where it clamps
+    const R fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    if (fl2 > v[0] * v[0]) {
+      const R s = v[0] / sqrt(fl2);
       v[1] *= s; v[2] *= s; v[3] *= s;
     }
   }
@@ -542,17 +543,20 @@ template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0,
     P[2] = v[0] * (a * n2 + bb * u2);
     return;
   }
-  R fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
-  if (v[0] > R(0) && fl > R(0)) {
-    R f = fl / v[0];
-    f = f > R(1) ? R(1) : f;
-    R chi = (R(3) + R(4) * f * f) / (R(5) + R(2) * sqrt(R(4) - R(3) * f * f));
-    R u0 = v[1] / fl, u1 = v[2] / fl, u2 = v[3] / fl;
-    R un = u0 * n0 + u1 * n1 + u2 * n2;
-    R a = R(0.5) * (R(1) - chi), bb = R(0.5) * (R(3) * chi - R(1));
-    P[0] = v[0] * (a * n0 + bb * un * u0);
-    P[1] = v[0] * (a * n1 + bb * un * u1);
-    P[2] = v[0] * (a * n2 + bb * un * u2);
+  // FP64: the same closure written with f^2 and F itself instead of f and
+  // u = F / |F| (D n = (1 - chi)/2 n + (3 chi - 1)/2 (u.n) u), chi = p / q:
+  // three divisions and one square root per state instead of five and two
+  const R fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (v[0] > R(0) && fl2 > R(0)) {
+    R f2 = fl2 / (v[0] * v[0]);
+    f2 = f2 > R(1) ? R(1) : f2;
+    const R p = R(3) + R(4) * f2, q = R(5) + R(2) * sqrt(R(4) - R(3) * f2);
+    const R r = R(0.5) / q;
+    const R a = (q - p) * r;
+    const R bb = (R(3) * p - q) * r * ((v[1] * n0 + v[2] * n1 + v[3] * n2) / fl2);
+    P[0] = v[0] * (a * n0 + bb * v[1]);
+    P[1] = v[0] * (a * n1 + bb * v[2]);
+    P[2] = v[0] * (a * n2 + bb * v[3]);
   } else {
     P[0] = v[0] * n0 / R(3);
     P[1] = v[0] * n1 / R(3);
