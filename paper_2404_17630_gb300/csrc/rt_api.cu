@@ -239,7 +239,7 @@ template <class R> const R4<R>* sweep_rad(rt_ctx* ctx);
 template <> const d4* sweep_rad<double>(rt_ctx* ctx) { return ctx->rad; }
 template <> const float4* sweep_rad<float>(rt_ctx* ctx) { return ctx->shadow; }
 
-constexpr int kGradNB = 8;   // neighbour loads in flight per thread (staged gradients)
+constexpr int kGradNB = 4;   // neighbour loads in flight per thread (staged gradients)
 constexpr size_t kGradSmemMax = 160 * 1024;
 
 template <class R> void launch_grad(rt_ctx* ctx) {

@@ -42,38 +42,67 @@ struct Rates {
 
 template <bool Fast> struct RateEval;
 
+// Functions of T shared by the FP64 rate fits and the cooling rate: every
+// power of T is exp(p (ln c - ln T)) from one logarithm, and the Boltzmann
+// factors that both use are formed once (relative error ~1e-15 against the
+// pow / exp of the definitions).
+struct TFns {
+  double T, iT, sT, tf, lnT, e94, e470, e157, e285, e631;
+};
+
+// natural logarithms of the fits' scale constants, and 1 / ln 10
+constexpr double kLnAH = 11.654317306519307;    // ln(2 x 157807 / 2.740)
+constexpr double kLnAHe2 = 13.041066233619674;  // ln(2 x 631515 / 2.740)
+constexpr double kLnLHe = 13.254566388120152;   // ln(2 x 285335)
+constexpr double kLn1e3 = 6.907755278982137;
+constexpr double kLn1e6 = 13.815510557964274;
+constexpr double kInvLn10 = 0.43429448190325176;
+
+__device__ __forceinline__ TFns tfns(double T) {
+  TFns t;
+  t.T = T;
+  t.iT = 1.0 / T;
+  t.sT = sqrt(T);
+  t.tf = 1.0 / (1.0 + sqrt(T * 1e-5));
+  t.lnT = log(T);
+  t.e94 = exp(-94000.0 * t.iT);
+  t.e470 = exp(-470000.0 * t.iT);
+  t.e157 = exp(-157809.1 * t.iT);
+  t.e285 = exp(-285335.4 * t.iT);
+  t.e631 = exp(-631515.0 * t.iT);
+  return t;
+}
+
 template <> struct RateEval<false> {
-  __device__ static Rates eval(double T) {
+  __device__ static Rates eval(const TFns& t) {
     Rates r;
-    double lH = 2.0 * 157807.0 / T;
-    r.aHII = 2.753e-14 * pow(lH, 1.5) / pow(1.0 + pow(lH / 2.740, 0.407), 2.242);
-    double lHe = 2.0 * 285335.0 / T;
-    r.aHeII = 1.26e-14 * pow(lHe, 0.750) +
-              1.9e-3 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
-    double lHe2 = 2.0 * 631515.0 / T;
-    r.aHeIII = 2.0 * 2.753e-14 * pow(lHe2, 1.5) / pow(1.0 + pow(lHe2 / 2.740, 0.407), 2.242);
-    double tf = 1.0 / (1.0 + sqrt(T / 1e5));
-    double sT = sqrt(T);
-    r.bHI = 5.85e-11 * sT * exp(-157809.1 / T) * tf;
-    r.bHeI = 2.38e-11 * sT * exp(-285335.4 / T) * tf;
-    r.bHeII = 5.68e-12 * sT * exp(-631515.0 / T) * tf;
+    // Hui & Gnedin case B, lambda = 2 T_i / T: a lambda^1.5 / (1 + (lambda / 2.74)^0.407)^2.242
+    const double lH = 315614.0 * t.iT, lHe2 = 1263030.0 * t.iT;
+    const double uH = exp(0.407 * (kLnAH - t.lnT)), uHe2 = exp(0.407 * (kLnAHe2 - t.lnT));
+    r.aHII = 2.753e-14 * (lH * sqrt(lH)) * exp(-2.242 * log(1.0 + uH));
+    r.aHeIII = 2.0 * 2.753e-14 * (lHe2 * sqrt(lHe2)) * exp(-2.242 * log(1.0 + uHe2));
+    const double die = 1.9e-3 * (t.iT / t.sT) * t.e470 * (1.0 + 0.3 * t.e94);
+    r.aHeII = 1.26e-14 * exp(0.750 * (kLnLHe - t.lnT)) + die;
+    r.bHI = 5.85e-11 * t.sT * t.e157 * t.tf;
+    r.bHeI = 2.38e-11 * t.sT * t.e285 * t.tf;
+    r.bHeII = 5.68e-12 * t.sT * t.e631 * t.tf;
     return r;
   }
-  __device__ static double cooling(double T, double ne, double nHI, double nHII, double nHeI, double nHeII,
+  __device__ static Rates eval(double T) { return eval(tfns(T)); }
+  __device__ static double cooling(const TFns& t, double ne, double nHI, double nHII, double nHeI, double nHeII,
                                    double nHeIII) {
-    double sT = sqrt(T), tf = 1.0 / (1.0 + sqrt(T / 1e5));
-    double ce = 7.50e-19 * exp(-118348.0 / T) * tf * ne * nHI +
-                5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * tf * ne * nHeII;
-    double ci = 1.27e-21 * sT * exp(-157809.1 / T) * tf * ne * nHI +
-                9.38e-22 * sT * exp(-285335.4 / T) * tf * ne * nHeI +
-                4.95e-22 * sT * exp(-631515.0 / T) * tf * ne * nHeII;
-    double t3 = pow(T / 1e3, -0.2) / (1.0 + pow(T / 1e6, 0.7));
-    double rc = 8.70e-27 * sT * t3 * ne * nHII + 1.55e-26 * pow(T, 0.3647) * ne * nHeII +
-                3.48e-26 * sT * t3 * ne * nHeIII +
-                1.24e-13 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T)) * ne * nHeII;
-    double lg = log10(T);
-    double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
-    double br = 1.42e-27 * gff * sT * (nHII + nHeII + 4.0 * nHeIII) * ne;
+    const double sT = t.sT, tf = t.tf;
+    const double ce = 7.50e-19 * exp(-118348.0 * t.iT) * tf * ne * nHI +
+                      5.54e-17 * exp(-0.397 * t.lnT) * exp(-473638.0 * t.iT) * tf * ne * nHeII;
+    const double ci = 1.27e-21 * sT * t.e157 * tf * ne * nHI + 9.38e-22 * sT * t.e285 * tf * ne * nHeI +
+                      4.95e-22 * sT * t.e631 * tf * ne * nHeII;
+    const double t3 = exp(-0.2 * (t.lnT - kLn1e3)) / (1.0 + exp(0.7 * (t.lnT - kLn1e6)));
+    const double rc = 8.70e-27 * sT * t3 * ne * nHII + 1.55e-26 * exp(0.3647 * t.lnT) * ne * nHeII +
+                      3.48e-26 * sT * t3 * ne * nHeIII +
+                      1.24e-13 * (t.iT / sT) * t.e470 * (1.0 + 0.3 * t.e94) * ne * nHeII;
+    const double lg = t.lnT * kInvLn10;
+    const double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+    const double br = 1.42e-27 * gff * sT * (nHII + nHeII + 4.0 * nHeIII) * ne;
     return ce + ci + rc + br;
   }
 };
@@ -156,7 +185,8 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   const double c = P.c_red;
   const double nHe = P.y_he * nH;
   const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
-  const Rates r = RateEval<false>::eval(s.T);
+  const TFns tfn = tfns(s.T);
+  const Rates r = RateEval<false>::eval(tfn);
 
   double ns0 = nH * s.xHI, ns1 = nHe * s.yI, ns2 = nHe * s.yII;
   double Nbar[kMaxBins];
@@ -209,7 +239,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   if (P.mode == 2) {
     double ntot0 = nH * (1.0 + P.y_he) + ne0;
     double e0 = 1.5 * kBoltzmann * ntot0 * s.T;
-    double lam = cool ? RateEval<false>::cooling(s.T, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
+    double lam = cool ? RateEval<false>::cooling(tfn, ne0, nH * s.xHI, nH * s.xHII, nHe * s.yI, nHe * s.yII,
                                                 nHe * s.yIII)
                       : 0.0;
     double e1 = e0 + (heat ? heat_e : 0.0) - dt * lam;

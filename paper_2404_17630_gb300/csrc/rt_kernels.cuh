@@ -191,6 +191,24 @@ template <class R> __device__ __forceinline__ R comp(const R4<R>& v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
 
+// Running extremes of FP64 differences on the integer pipe.  The bits of a
+// double x >= +0 order like x as signed 64-bit integers and those of x < 0
+// are negative, so max(bits, bits(d)) keeps the largest d >= 0 (start: +0);
+// the magnitude bits of d < 0 (0 for d >= 0) track the most negative d.
+__device__ __forceinline__ long long max_bits_pos(long long b, double d) {
+  const long long v = __double_as_longlong(d);
+  return v > b ? v : b;
+}
+__device__ __forceinline__ long long max_bits_neg(long long m, double d) {
+  const long long v = __double_as_longlong(d);
+  const long long mag = (v & 0x7FFFFFFFFFFFFFFFLL) & (v >> 63);
+  return mag > m ? mag : m;
+}
+// -magnitude from max_bits_neg, +0 where nothing was negative
+__device__ __forceinline__ double neg_from_bits(long long m) {
+  return __longlong_as_double(m ? (m | (long long)0x8000000000000000ULL) : 0LL);
+}
+
 // max / min of two finite values: one FMNMX in FP32; the FP64 sweep keeps
 // the comparison form of the limiter's definition.
 template <class R> __device__ __forceinline__ R rmax(R a, R b) {
@@ -227,10 +245,17 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   }
   R r[4][3];
   R mx[4], mn[4];
+  // FP64: the neighbour extremes as max_j (phi_j - phi_i) >= 0 and
+  // min_j (phi_j - phi_i) <= 0, kept as bit patterns and compared on the
+  // integer pipe (the FP64 pipe runs 1/64 of the FP32 rate on this part and
+  // is what bounds this kernel).  Rounding is monotone, so max_j fl(phi_j -
+  // phi_i) = fl(max_j phi_j - phi_i): the same values as the definition.
+  long long dmx[4], dmn[4];   // bits of the largest difference, magnitude bits of the most negative
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     r[q][0] = r[q][1] = r[q][2] = R(0);
     mx[q] = mn[q] = comp<R>(pi, q);
+    dmx[q] = dmn[q] = 0;
   }
   const int k0 = g.off[i], k1 = g.off[i + 1];
   // half-edge k: w_k (phi_j - phi_i) is this face's term of the least-squares
@@ -242,8 +267,13 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
       r[q][0] += hw.x * dphi;
       r[q][1] += hw.y * dphi;
       r[q][2] += hw.z * dphi;
-      mx[q] = rmax<R>(mx[q], vj);
-      mn[q] = rmin<R>(mn[q], vj);
+      if constexpr (sizeof(R) == 8) {
+        dmx[q] = max_bits_pos(dmx[q], dphi);
+        dmn[q] = max_bits_neg(dmn[q], dphi);
+      } else {
+        mx[q] = rmax<R>(mx[q], vj);
+        mn[q] = rmin<R>(mn[q], vj);
+      }
     }
   };
   int k = k0;
@@ -299,28 +329,50 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
         }
       }
     } else {
+      // the threshold test compares two non-negative doubles and the
+      // extremes are kept as bits, as above: integer compares throughout
+      long long bpos[4], bneg[4];
+      R thr[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bpos[q] = bneg[q] = 0;
+        thr[q] = lim_eps2 * gg[q];
+      }
 #pragma unroll 4
       for (int k = k0; k < k1; ++k) {
         const R4<R> x = ld4<R>(g.hx + k);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-          if (dphi * dphi > lim_eps2 * gg[q] * x.w) {
-            dpos[q] = dphi > dpos[q] ? dphi : dpos[q];
-            dneg[q] = dphi < dneg[q] ? dphi : dneg[q];
+          const R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+          if (__double_as_longlong(dphi * dphi) > __double_as_longlong(thr[q] * x.w)) {
+            bpos[q] = max_bits_pos(bpos[q], dphi);
+            bneg[q] = max_bits_neg(bneg[q], dphi);
           }
         }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dpos[q] = __longlong_as_double(bpos[q]);
+        dneg[q] = neg_from_bits(bneg[q]);
       }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const R vi = comp<R>(pi, q);
+      R up, dn;   // max_j phi_j - phi_i and min_j phi_j - phi_i
+      if constexpr (sizeof(R) == 8) {
+        up = __longlong_as_double(dmx[q]);
+        dn = neg_from_bits(dmn[q]);
+      } else {
+        up = mx[q] - vi;
+        dn = mn[q] - vi;
+      }
       if (dpos[q] > R(0)) {
-        R lim = (mx[q] - vi) / dpos[q];
+        R lim = up / dpos[q];
         psi[q] = lim < psi[q] ? lim : psi[q];
       }
       if (dneg[q] < R(0)) {
-        R lim = (mn[q] - vi) / dneg[q];
+        R lim = dn / dneg[q];
         psi[q] = lim < psi[q] ? lim : psi[q];
       }
     }
@@ -416,15 +468,17 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
       mn[q] = fminf(mn[q], vj);
     }
   };
-  int k = k0;
-  for (; k + NB <= k1; k += NB) {
+  // neighbour states NB at a time, the last batch predicated (no serial
+  // tail of single loads); the sums still run in CSR order
+  for (int k = k0; k < k1; k += NB) {
     float4 pj[NB];
 #pragma unroll
-    for (int u = 0; u < NB; ++u) pj[u] = __ldg(rad + (size_t)bits_id(shw[k + u].w) * B + b);
+    for (int u = 0; u < NB; ++u)
+      pj[u] = k + u < k1 ? __ldg(rad + (size_t)bits_id(shw[k + u].w) * B + b) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < NB; ++u) acc_face(shw[k + u], pj[u]);
+    for (int u = 0; u < NB; ++u)
+      if (k + u < k1) acc_face(shw[k + u], pj[u]);
   }
-  for (; k < k1; ++k) acc_face(shw[k], __ldg(rad + (size_t)bits_id(shw[k].w) * B + b));
   float gr[4][3], psi[4], eg[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
