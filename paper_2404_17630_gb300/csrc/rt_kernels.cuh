@@ -191,6 +191,29 @@ template <class R> __device__ __forceinline__ R comp(const R4<R>& v, int q) {
   return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
 }
 
+// Hardware reciprocal approximation (MUFU; relative error ~1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// a / b in FP64 without the FP64 division sequence: an FP32 reciprocal seed
+// (relative error below 2^-22), one Newton-Raphson step y <- y + y (1 - b y)
+// (error ~2^-44), the quotient q = a y and one residual correction
+// q <- q + y (a - b q) (the remainder-based refinement of Markstein, IBM J.
+// Res. Dev. 34 (1990)): within 0.51 units in the last place of a / b, so
+// the correctly rounded quotient but for rare ties.  Five FP64 operations.  Divisors outside the FP32 normal range take the
+// IEEE division.
+__device__ __forceinline__ double div_nr(double a, double b) {
+  const float bf = d2f_int(b);
+  if (!(fabsf(bf) < 1e30f && fabsf(bf) > 1e-30f)) return a / b;
+  double y = f2d_int(rcp_approx(bf));
+  y = fma(y, fma(-b, y, 1.0), y);
+  const double q = a * y;
+  return fma(y, fma(-b, q, a), q);
+}
+
 // Running extremes of FP64 differences on the integer pipe.  The bits of a
 // double x >= +0 order like x as signed 64-bit integers and those of x < 0
 // are negative, so max(bits, bits(d)) keeps the largest d >= 0 (start: +0);
@@ -368,11 +391,15 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
         dn = mn[q] - vi;
       }
       if (dpos[q] > R(0)) {
-        R lim = up / dpos[q];
+        R lim;
+        if constexpr (sizeof(R) == 8) lim = div_nr(up, dpos[q]);
+        else lim = up / dpos[q];
         psi[q] = lim < psi[q] ? lim : psi[q];
       }
       if (dneg[q] < R(0)) {
-        R lim = dn / dneg[q];
+        R lim;
+        if constexpr (sizeof(R) == 8) lim = div_nr(dn, dneg[q]);
+        else lim = dn / dneg[q];
         psi[q] = lim < psi[q] ? lim : psi[q];
       }
     }
@@ -568,13 +595,6 @@ __device__ __forceinline__ void face_state_rec(const float4 r[4], float x0, floa
   }
 }
 
-// Hardware reciprocal approximation (MUFU; relative error ~1 ulp).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // N D n with the Levermore M1 Eddington tensor.
 template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0, R n1, R n2, R P[3]) {
   if constexpr (sizeof(R) == 4) {
@@ -599,15 +619,16 @@ template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0,
   }
   // FP64: the same closure written with f^2 and F itself instead of f and
   // u = F / |F| (D n = (1 - chi)/2 n + (3 chi - 1)/2 (u.n) u), chi = p / q:
-  // three divisions and one square root per state instead of five and two
+  // three quotients (div_nr) and one square root per state instead of five
+  // divisions and two square roots
   const R fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
   if (v[0] > R(0) && fl2 > R(0)) {
-    R f2 = fl2 / (v[0] * v[0]);
+    R f2 = div_nr(fl2, v[0] * v[0]);
     f2 = f2 > R(1) ? R(1) : f2;
     const R p = R(3) + R(4) * f2, q = R(5) + R(2) * sqrt(R(4) - R(3) * f2);
-    const R r = R(0.5) / q;
+    const R r = div_nr(0.5, q);
     const R a = (q - p) * r;
-    const R bb = (R(3) * p - q) * r * ((v[1] * n0 + v[2] * n1 + v[3] * n2) / fl2);
+    const R bb = (R(3) * p - q) * r * div_nr(v[1] * n0 + v[2] * n1 + v[3] * n2, fl2);
     P[0] = v[0] * (a * n0 + bb * v[1]);
     P[1] = v[0] * (a * n1 + bb * v[2]);
     P[2] = v[0] * (a * n2 + bb * v[3]);
