@@ -313,24 +313,32 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
                 ms_per_step=1e3 * sec / steps)
 
 
-# FP64 work of one chemistry attempt of the mixed path (2 x DFMA + DMUL + DADD
-# thread instructions, from ncu on the 2e5-cell workload in steady state,
-# one attempt per cell): the unit count behind k_chem's ALU roofline.
-FP64_FLOP_PER_ATTEMPT = {"mixed": 176.0, "fp64": None}  # re-measured after each change of k_chem
+# FP64 work of the kernels the FP64 unit bounds, from ncu on the 2e5-cell
+# workload in steady state (FLOP = 2 x DFMA + DMUL + DADD thread
+# instructions): per chemistry attempt for k_chem (one attempt per cell in
+# steady state), per cell for the FP64 sweep kernels.  The unit counts behind
+# the `alu` rooflines; re-measured after each change of these kernels.
+FP64_FLOP = {
+    "mixed": {"k_chem": (176.0, "attempt")},
+    "fp64": {"k_chem": (1406.0, "attempt"), "k_grad": (3096.8, "cell"), "k_flux": (5627.5, "cell"),
+             "k_gather": (439.4, "cell")},
+}
 # GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
 # clock per SM (ncu: 16 cycles per warp instruction on the FP64 pipe) x 2 FLOP
 # x 2.07 GHz = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_SOURCE = "FP64 units x clock (152 SMs x 2 FMA lanes/clk x 2 x 2.07 GHz)"
 
 
 def roofline(res, precision, peaks, peak_kind, attempts=None):
-    """Roofline of the kernel with the largest time share.  Memory-bound
-    kernels (k_grad, k_flux, k_gather) against the measured HBM copy
-    bandwidth; k_chem (FP64 chemistry) against the FP64 peak when its FP64
-    work per attempt is known."""
+    """Roofline of the kernel with the largest time share.  A kernel whose
+    FP64 work is known (FP64_FLOP) against the FP64 peak (`alu`): the
+    chemistry, and every kernel of the FP64 path; the others against the
+    measured HBM copy bandwidth.  Beside it, the memory-bound kernel with the
+    largest share against HBM."""
     C, F, B = res["C"], res["F"], 3
     w = 4 if precision == "mixed" else 8
-    prof = res["prof"]
+    prof = {k: v for k, v in res["prof"].items() if v[1] > 0}
     total = sum(v[0] for v in prof.values())
     shares = {k: (v[0] / total if total else 0.0) for k, v in prof.items()}
     kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": round(shares[k], 4),
@@ -338,8 +346,15 @@ def roofline(res, precision, peaks, peak_kind, attempts=None):
                 "GBs": algorithmic_bytes(k, C, F, B, w) / (v[0] / 1e3 / max(v[1], 1)) / 1e9 if v[0] else None}
             for k, v in prof.items()}
     peak = float(peaks["hbm_gbs"])
+    units = {"cell": C, "attempt": attempts if attempts else C}
+    flops = FP64_FLOP.get(precision, {})
     for k in kern:
         kern[k]["hbm_frac"] = round(kern[k]["GBs"] / peak, 4) if kern[k]["GBs"] else None
+        if k in flops and kern[k]["ms_per_launch"] > 0:
+            f, u = flops[k]
+            tf = f * units[u] / (kern[k]["ms_per_launch"] / 1e3) / 1e12
+            kern[k]["fp64_tflops"] = round(tf, 4)
+            kern[k]["fp64_frac"] = round(tf / FP64_PEAK_TFLOPS, 4)
 
     def hbm_line(k):
         return {"kernel": k, "bound": "hbm", "achieved": round(kern[k]["GBs"], 1), "peak": peak, "unit": "GB/s",
@@ -349,15 +364,12 @@ def roofline(res, precision, peaks, peak_kind, attempts=None):
     top = max(prof, key=lambda k: prof[k][0])
     mem = [k for k in prof if k != "k_chem"]
     top_mem = max(mem, key=lambda k: prof[k][0])
-    flop = FP64_FLOP_PER_ATTEMPT.get(precision)
-    if top == "k_chem" and flop and attempts:
-        per_launch_s = prof[top][0] / 1e3 / max(prof[top][1], 1)
-        ach = flop * attempts / per_launch_s / 1e12
-        line = {"kernel": "k_chem", "bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "FP64 units x clock (152 SMs x 2 FMA lanes/clk x 2 x 2.07 GHz)",
-                "traffic": ncu_traffic("k_chem", precision),
-                "alg_flop_per_launch": flop * attempts, "attempts_per_launch": attempts}
+    if top in flops:
+        f, u = flops[top]
+        line = {"kernel": top, "bound": "alu", "achieved": kern[top]["fp64_tflops"],
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": kern[top]["fp64_frac"],
+                "peak_source": FP64_PEAK_SOURCE, "traffic": ncu_traffic(top, precision),
+                "alg_flop_per_launch": f * units[u], "flop_per_" + u: f, u + "s_per_launch": units[u]}
     else:
         line = hbm_line(top)
     return line, kern, hbm_line(top_mem)
@@ -696,7 +708,7 @@ def main():
         r64 = run_gpu("fp64", mesh, cfg, state, max(2, args.steps // 5), 1, rank, world, dev, dist)
         fp64 = {"value": world * r64["C"] * N_SUB * max(2, args.steps // 5) / (r64["ms"] / 1e3),
                 "ms_per_step": r64["ms"] / max(2, args.steps // 5), "dtype": "f64"}
-        rf64, k64, rf64m = roofline(r64, "fp64", peaks, peak_kind)
+        rf64, k64, rf64m = roofline(r64, "fp64", peaks, peak_kind, attempts=r64.get("attempts"))
         fp64["roofline"] = rf64
         fp64["roofline_memory_kernel"] = rf64m
         fp64["kernels"] = k64

@@ -784,12 +784,15 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
     for (int q = 0; q < 4; ++q) acc[q] = f2d_int(hi[q]) + f2d_int(lo[q]);
   } else {
     acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+    // acc +- v as one fused multiply-add by +-1 (exact product, one
+    // rounding: the same sum as the add or subtract, without predicated
+    // copies of both)
     auto add = [&](int e, const R4<R>& v) {
-      if (e & 1) {
-        acc[0] -= (double)v.x; acc[1] -= (double)v.y; acc[2] -= (double)v.z; acc[3] -= (double)v.w;
-      } else {
-        acc[0] += (double)v.x; acc[1] += (double)v.y; acc[2] += (double)v.z; acc[3] += (double)v.w;
-      }
+      const double sg = (e & 1) ? -1.0 : 1.0;
+      acc[0] = fma(sg, (double)v.x, acc[0]);
+      acc[1] = fma(sg, (double)v.y, acc[1]);
+      acc[2] = fma(sg, (double)v.z, acc[2]);
+      acc[3] = fma(sg, (double)v.w, acc[3]);
     };
     int k = k0;
     for (; k + 4 <= k1; k += 4) {
