@@ -127,9 +127,11 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, precision):
+def ncu_traffic(kernel, precision, cells):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    from the current kernel sources; else None."""
+    from the current kernel sources on a mesh of this many cells; else None
+    (traffic does not scale in proportion between meshes that do and do not
+    fit in L2)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -137,7 +139,7 @@ def ncu_traffic(kernel, precision):
     except (OSError, ValueError):
         return None
     ent = d.get(f"{precision}:{kernel}")
-    if not ent or ent.get("source_sha") != source_hash():
+    if not ent or ent.get("source_sha") != source_hash() or ent.get("cells") != cells:
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -359,7 +361,7 @@ def roofline(res, precision, peaks, peak_kind, attempts=None):
     def hbm_line(k):
         return {"kernel": k, "bound": "hbm", "achieved": round(kern[k]["GBs"], 1), "peak": peak, "unit": "GB/s",
                 "frac": kern[k]["hbm_frac"], "peak_source": f"hbm_gbs of {peak_kind}",
-                "traffic": ncu_traffic(k, precision), "alg_bytes_per_launch": kern[k]["alg_bytes_per_launch"]}
+                "traffic": ncu_traffic(k, precision, C), "alg_bytes_per_launch": kern[k]["alg_bytes_per_launch"]}
 
     top = max(prof, key=lambda k: prof[k][0])
     mem = [k for k in prof if k != "k_chem"]
@@ -368,7 +370,7 @@ def roofline(res, precision, peaks, peak_kind, attempts=None):
         f, u = flops[top]
         line = {"kernel": top, "bound": "alu", "achieved": kern[top]["fp64_tflops"],
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": kern[top]["fp64_frac"],
-                "peak_source": FP64_PEAK_SOURCE, "traffic": ncu_traffic(top, precision),
+                "peak_source": FP64_PEAK_SOURCE, "traffic": ncu_traffic(top, precision, C),
                 "alg_flop_per_launch": f * units[u], "flop_per_" + u: f, u + "s_per_launch": units[u]}
     else:
         line = hbm_line(top)

@@ -61,9 +61,9 @@ constexpr double kInvLn10 = 0.43429448190325176;
 __device__ __forceinline__ TFns tfns(double T) {
   TFns t;
   t.T = T;
-  t.iT = 1.0 / T;
+  t.iT = div_nr(1.0, T);
   t.sT = sqrt(T);
-  t.tf = 1.0 / (1.0 + sqrt(T * 1e-5));
+  t.tf = div_nr(1.0, 1.0 + sqrt(T * 1e-5));
   t.lnT = log(T);
   t.e94 = exp(-94000.0 * t.iT);
   t.e470 = exp(-470000.0 * t.iT);
@@ -81,7 +81,7 @@ template <> struct RateEval<false> {
     const double uH = exp(0.407 * (kLnAH - t.lnT)), uHe2 = exp(0.407 * (kLnAHe2 - t.lnT));
     r.aHII = 2.753e-14 * (lH * sqrt(lH)) * exp(-2.242 * log(1.0 + uH));
     r.aHeIII = 2.0 * 2.753e-14 * (lHe2 * sqrt(lHe2)) * exp(-2.242 * log(1.0 + uHe2));
-    const double die = 1.9e-3 * (t.iT / t.sT) * t.e470 * (1.0 + 0.3 * t.e94);
+    const double die = 1.9e-3 * div_nr(t.iT, t.sT) * t.e470 * (1.0 + 0.3 * t.e94);
     r.aHeII = 1.26e-14 * exp(0.750 * (kLnLHe - t.lnT)) + die;
     r.bHI = 5.85e-11 * t.sT * t.e157 * t.tf;
     r.bHeI = 2.38e-11 * t.sT * t.e285 * t.tf;
@@ -96,12 +96,12 @@ template <> struct RateEval<false> {
                       5.54e-17 * exp(-0.397 * t.lnT) * exp(-473638.0 * t.iT) * tf * ne * nHeII;
     const double ci = 1.27e-21 * sT * t.e157 * tf * ne * nHI + 9.38e-22 * sT * t.e285 * tf * ne * nHeI +
                       4.95e-22 * sT * t.e631 * tf * ne * nHeII;
-    const double t3 = exp(-0.2 * (t.lnT - kLn1e3)) / (1.0 + exp(0.7 * (t.lnT - kLn1e6)));
+    const double t3 = div_nr(exp(-0.2 * (t.lnT - kLn1e3)), 1.0 + exp(0.7 * (t.lnT - kLn1e6)));
     const double rc = 8.70e-27 * sT * t3 * ne * nHII + 1.55e-26 * exp(0.3647 * t.lnT) * ne * nHeII +
                       3.48e-26 * sT * t3 * ne * nHeIII +
-                      1.24e-13 * (t.iT / sT) * t.e470 * (1.0 + 0.3 * t.e94) * ne * nHeII;
+                      1.24e-13 * div_nr(t.iT, sT) * t.e470 * (1.0 + 0.3 * t.e94) * ne * nHeII;
     const double lg = t.lnT * kInvLn10;
-    const double gff = 1.1 + 0.34 * exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
+    const double gff = 1.1 + 0.34 * exp(div_nr(-(5.5 - lg) * (5.5 - lg), 3.0));
     const double br = 1.42e-27 * gff * sT * (nHII + nHeII + 4.0 * nHeIII) * ne;
     return ce + ci + rc + br;
   }
@@ -171,7 +171,7 @@ struct CellState {
 
 __device__ __forceinline__ double rel_change(double a, double b, double fl) {
   double m = fabs(a) > fl ? fabs(a) : fl;
-  return fabs(b - a) / m;
+  return div_nr(fabs(b - a), m);
 }
 
 // One semi-implicit photochemistry attempt over dt from s into t; returns the
@@ -195,7 +195,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
       double kap = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
-      Nbar[b] = s.N[b] / (1.0 + c * dt * kap);
+      Nbar[b] = div_nr(s.N[b], 1.0 + c * dt * kap);
       G0 += c * P.sigma[b][0] * Nbar[b];
       G1 += c * P.sigma[b][1] * Nbar[b];
       G2 += c * P.sigma[b][2] * Nbar[b];
@@ -205,17 +205,17 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
   double aH = dt * (G0 + (coll ? r.bHI * ne0 : 0.0));
   double bH = recomb ? dt * r.aHII * ne0 : 0.0;
   double den = 1.0 + aH + bH;
-  t.xHI = (s.xHI * (1.0 + bH) + bH * s.xHII) / den;
-  t.xHII = (s.xHII * (1.0 + aH) + aH * s.xHI) / den;
+  t.xHI = div_nr(s.xHI * (1.0 + bH) + bH * s.xHII, den);
+  t.xHII = div_nr(s.xHII * (1.0 + aH) + aH * s.xHI, den);
   double ne1 = nH * t.xHII + nHe * (s.yII + 2.0 * s.yIII);
   double A = dt * (G1 + (coll ? r.bHeI * ne1 : 0.0));
   double Bb = recomb ? dt * r.aHeII * ne1 : 0.0;
   double Cc = dt * (G2 + (coll ? r.bHeII * ne1 : 0.0));
   double D = recomb ? dt * r.aHeIII * ne1 : 0.0;
   double opA = 1.0 + A, opD = 1.0 + D;
-  t.yII = (s.yII + A * s.yI / opA + D * s.yIII / opD) / (1.0 + Bb / opA + Cc / opD);
-  t.yI = (s.yI + Bb * t.yII) / opA;
-  t.yIII = (s.yIII + Cc * t.yII) / opD;
+  t.yII = div_nr(s.yII + div_nr(A * s.yI, opA) + div_nr(D * s.yIII, opD), 1.0 + div_nr(Bb, opA) + div_nr(Cc, opD));
+  t.yI = div_nr(s.yI + Bb * t.yII, opA);
+  t.yIII = div_nr(s.yIII + Cc * t.yII, opD);
 
   double m0 = nH * t.xHI, m1 = nHe * t.yI, m2 = nHe * t.yII;
   double heat_e = 0.0;
@@ -228,7 +228,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
       heat_e += P.eps[b][0] * i0 + P.eps[b][1] * i1 + P.eps[b][2] * i2;
       double N1 = s.N[b] - ((i0 + i1) + i2);
       if (N1 < 0) N1 = 0;
-      double sc = s.N[b] > 0 ? N1 / s.N[b] : 0.0;
+      double sc = s.N[b] > 0 ? div_nr(N1, s.N[b]) : 0.0;
       t.N[b] = N1;
       t.f[b][0] = s.f[b][0] * sc;
       t.f[b][1] = s.f[b][1] * sc;
@@ -245,7 +245,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
     double e1 = e0 + (heat ? heat_e : 0.0) - dt * lam;
     double ne2 = nH * t.xHII + nHe * (t.yII + 2.0 * t.yIII);
     double ntot1 = nH * (1.0 + P.y_he) + ne2;
-    t.T = e1 / (1.5 * kBoltzmann * ntot1);
+    t.T = div_nr(e1, 1.5 * kBoltzmann * ntot1);
     f = rel_change(e0, e1, 0.0);
   } else {
     t.T = s.T;
@@ -266,9 +266,7 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
 __device__ __forceinline__ double rcp64(double x) {
   const float xf = d2f_int(x);
   if (!(fabsf(xf) < 1e30f && fabsf(xf) > 1e-30f)) return 1.0 / x;
-  float yf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
-  const double y = f2d_int(yf);
+  const double y = f2d_int(rcp_approx(xf));
   return fma(y, fma(-x, y, 1.0), y);   // one Newton step: ~2^-44 relative
 }
 
@@ -481,12 +479,12 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
     ++n;
     double f = photochem_attempt(P, nH, dt, s, t);
     if (f > P.f_max) {
-      dt = dt * (P.f_s / f);
+      dt = dt * div_nr(P.f_s, f);
       continue;
     }
     s = t;
     rem = (dt == rem) ? 0.0 : rem - dt;
-    double grow = (f > 0) ? P.f_s / f : 2.0;
+    double grow = (f > 0) ? div_nr(P.f_s, f) : 2.0;
     if (grow > 2.0) grow = 2.0;
     dt = dt * grow;
     if (dt > rem) dt = rem;

@@ -114,6 +114,29 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// Hardware reciprocal approximation (MUFU; relative error ~1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// a / b in FP64 without the FP64 division sequence: an FP32 reciprocal seed
+// (relative error below 2^-22), one Newton-Raphson step y <- y + y (1 - b y)
+// (error ~2^-44), the quotient q = a y and one residual correction
+// q <- q + y (a - b q) (the remainder-based refinement of Markstein, IBM J.
+// Res. Dev. 34 (1990)): within 0.51 units in the last place of a / b, so
+// the correctly rounded quotient but for rare ties.  Five FP64 operations.  Divisors outside the FP32 normal range take the
+// IEEE division.
+__device__ __forceinline__ double div_nr(double a, double b) {
+  const float bf = d2f_int(b);
+  if (!(fabsf(bf) < 1e30f && fabsf(bf) > 1e-30f)) return a / b;
+  double y = f2d_int(rcp_approx(bf));
+  y = fma(y, fma(-b, y, 1.0), y);
+  const double q = a * y;
+  return fma(y, fma(-b, q, a), q);
+}
+
 // n / d for 0 <= n < 2^31 by one wide multiply and a shift.  With
 // L = ceil(log2 d), S = 31 + L and M = ceil(2^S / d) = (2^S + e) / d,
 // 0 <= e < d: n M / 2^S = n / d + n e / (d 2^S) and n e < 2^31 2^L = 2^S,
