@@ -277,16 +277,9 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     }
   };
   int k = k0;
-  // batches of four faces, loads first, accumulation in CSR order
-  for (; k + 4 <= k1; k += 4) {
-    R4<R> hw[4], pj[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) hw[u] = ld4<R>(g.hw + k + u);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) pj[u] = ld4<R>(rad + (size_t)bits_id(hw[u].w) * B + b);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc_face(hw[u], pj[u]);
-  }
+  // one face at a time, not unrolled (batches of four with a serial tail
+  // were measured slower in the FP64 sweep)
+#pragma unroll 1
   for (; k < k1; ++k) {
     const R4<R> hw = ld4<R>(g.hw + k);
     acc_face(hw, ld4<R>(rad + (size_t)bits_id(hw.w) * B + b));
@@ -338,7 +331,7 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
         bpos[q] = bneg[q] = 0;
         thr[q] = lim_eps2 * gg[q];
       }
-#pragma unroll 4
+#pragma unroll 1
       for (int k = k0; k < k1; ++k) {
         const R4<R> x = ld4<R>(g.hx + k);
 #pragma unroll
