@@ -285,6 +285,49 @@ def test_step_equals_separate_stages(splitting, time_order, gather_sum):
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("n_bins", [1, 2])
+def test_mixed_step_fewer_bins(n_bins):
+    """One and two frequency bins in the mixed path (gradient records with
+    one and two bins per group; three bins are padded to four): whole steps
+    with sources and chemistry against the oracle, on a ragged 11^3 mesh."""
+    mesh, cfg, st = voronoi_case(n=11, n_bins=n_bins)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1)
+    dt = o.max_dt()
+    assert o.step(3 * dt, 3) == 0
+    rt.step(3 * dt, 3)
+    assert rt.sync() == 0
+    compare_state(rt, o, 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_no_cell_active(precision):
+    """A mask with no active cell: no sources, no chemistry, no interface
+    carries a flux, so a step leaves every field as it was (the oracle
+    agrees); then all cells active again."""
+    mesh, cfg, st = voronoi_case(n=10, n_src=3)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    before = rt.fields()
+    none = np.zeros(mesh.n_cells, dtype=bool)
+    o.set_active(none)
+    rt.set_active(none)
+    dt = o.max_dt()
+    assert o.step(2 * dt, 2) == 0
+    rt.step(2 * dt, 2)
+    assert rt.sync() == 0
+    after = rt.fields()
+    for k in ("N", "F", "x5", "T"):
+        assert np.array_equal(after[k], before[k]), k
+    compare_state(rt, o, TOL64 if precision == "fp64" else 1e-4)
+    o.set_active(None)
+    rt.set_active(None)
+    assert o.step(2 * dt, 2) == 0
+    rt.step(2 * dt, 2)
+    assert rt.sync() == 0
+    compare_state(rt, o, TOL64 if precision == "fp64" else 1e-4)
+
+
 @pytest.mark.parametrize("gather_sum", [0, 1])
 def test_mixed_step_errors(gather_sum):
     """FP32 sweep: per-field error against the FP64 oracle after a few
