@@ -83,6 +83,7 @@ void use_set(rt_ctx* ctx, int k) {
     ctx->act_cells = ctx->touched_cells = ctx->act_faces = ctx->grad_blocks = nullptr;
     ctx->touched = nullptr;
     ctx->n_act = ctx->n_touched = ctx->n_act_faces = ctx->n_grad_blocks = 0;
+    ctx->grad_cap_list = 0;
     return;
   }
   rt_ctx::ActSet& a = ctx->sets[k];
@@ -92,6 +93,7 @@ void use_set(rt_ctx* ctx, int k) {
   ctx->grad_blocks = a.grad_blocks; ctx->touched = a.touched;
   ctx->n_act = a.n_act; ctx->n_touched = a.n_touched; ctx->n_act_faces = a.n_act_faces;
   ctx->n_grad_blocks = a.n_grad_blocks;
+  ctx->grad_cap_list = a.grad_cap_list;
 }
 
 void free_active(rt_ctx* ctx) {
@@ -240,6 +242,11 @@ template <> const d4* sweep_rad<double>(rt_ctx* ctx) { return ctx->rad; }
 template <> const float4* sweep_rad<float>(rt_ctx* ctx) { return ctx->shadow; }
 
 constexpr int kGradNB = 4;   // neighbour loads in flight per thread (staged gradients)
+// An active set's gradients run over its touched-cell list when fewer than
+// this fraction of the cells of the blocks it touches are touched, else over
+// those blocks (measured on the 2e5-cell hierarchy: the list form is faster
+// at 32 % and 61 %, slower at 87 %)
+constexpr double kGradListDensity = 0.75;
 constexpr size_t kGradSmemMax = 160 * 1024;
 
 template <class R> void launch_grad(rt_ctx* ctx) {
@@ -247,12 +254,20 @@ template <class R> void launch_grad(rt_ctx* ctx) {
   const R e = (R)ctx->cfg.lim_eps;
   if constexpr (sizeof(R) == 4) {
     if (ctx->grad_cap > 0 && ctx->cfg.order >= 2) {
-      const int nb = ctx->all_active ? (ctx->C + kGradCells - 1) / kGradCells : ctx->n_grad_blocks;
+      // every cell active: blocks of consecutive cells; an active set: blocks
+      // of consecutive entries of its touched-cell list (no work for the
+      // untouched cells of a block)
+      const bool list = !ctx->all_active && ctx->grad_cap_list > 0 &&
+                        (double)ctx->n_touched < kGradListDensity * kGradCells * (double)ctx->n_grad_blocks;
+      const int cap = list ? ctx->grad_cap_list : ctx->grad_cap;
+      const int nb = ctx->all_active ? (ctx->C + kGradCells - 1) / kGradCells
+                     : list          ? (ctx->n_touched + kGradCells - 1) / kGradCells
+                                     : ctx->n_grad_blocks;
       if (nb == 0) return;
-      const size_t smem = 2 * (size_t)ctx->grad_cap * sizeof(float4);
+      const size_t smem = 2 * (size_t)cap * sizeof(float4);
       k_grad_staged<kGradNB><<<nb, kGradCells * ctx->B, smem, ctx->stream>>>(
-          geo<float>(ctx), sweep_rad<float>(ctx), (float*)ctx->G, ctx->cfg.limiter, e * e, ctx->grad_cap,
-          ctx->status);
+          geo<float>(ctx), sweep_rad<float>(ctx), (float*)ctx->G, ctx->cfg.limiter, e * e, cap, ctx->status,
+          list ? 1 : 0);
       return;
     }
   }
@@ -452,6 +467,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
       CK(cudaFuncSetAttribute(k_grad_staged<kGradNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
          "staged gradients");
       ctx->grad_cap = cap;
+      ctx->grad_smem_attr = (int)smem;
     }
   }
 
@@ -708,6 +724,29 @@ rt_status rt_set_active(rt_ctx* ctx, const uint8_t* active) {
       for (int i = c0; i < std::min(c0 + kGradCells, C) && !any; ++i) any = tf[i];
       if (any) gb.push_back(c0 / kGradCells);
     }
+    // staged gradients over the touched list: the face records of the
+    // largest block of kGradCells list entries must fit in shared memory
+    int cap_list = 0;
+    if (mixed(ctx) && ctx->grad_cap > 0) {
+      std::vector<int32_t> deg(C, 0);
+      for (int f = 0; f < F; ++f) {
+        deg[lr[f].x]++;
+        deg[lr[f].y]++;
+      }
+      for (size_t j0 = 0; j0 < tc.size(); j0 += kGradCells) {
+        int sum = 0;
+        for (size_t j = j0; j < std::min(j0 + kGradCells, tc.size()); ++j) sum += deg[tc[j]];
+        cap_list = std::max(cap_list, sum);
+      }
+      const size_t smem = 2 * (size_t)cap_list * sizeof(float4);
+      if (smem > kGradSmemMax) {
+        cap_list = 0;
+      } else if ((int)smem > ctx->grad_smem_attr) {
+        CK(cudaFuncSetAttribute(k_grad_staged<kGradNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+           "staged gradients");
+        ctx->grad_smem_attr = (int)smem;
+      }
+    }
     auto up = [&](const void* src, size_t bytes, void** dst) -> rt_status {
       void* p = nullptr;
       cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
@@ -733,6 +772,7 @@ rt_status rt_set_active(rt_ctx* ctx, const uint8_t* active) {
     a.n_touched = (int)tc.size();
     a.n_act_faces = (int)af.size();
     a.n_grad_blocks = (int)gb.size();
+    a.grad_cap_list = cap_list;
     a.hash = h;
     a.mask.swap(m);
     a.valid = true;

@@ -53,6 +53,8 @@ struct rt_ctx {
   int32_t* grad_blocks = nullptr;    // gradient blocks holding a touched cell
   uint8_t* touched = nullptr;        // per cell: has an active interface
   int n_act = 0, n_touched = 0, n_act_faces = 0, n_grad_blocks = 0;
+  int grad_cap_list = 0;             // staged gradients over the touched list: records of the largest block (0: off)
+  int grad_smem_attr = 0;            // dynamic shared memory the staged gradient kernel is allowed
   // work
   void* G = nullptr;           // [C][B][12] in sweep precision
   void* flux = nullptr;        // [F][B] 4-vectors in sweep precision
@@ -81,6 +83,7 @@ struct rt_ctx {
     int32_t *act_cells = nullptr, *touched_cells = nullptr, *act_faces = nullptr, *grad_blocks = nullptr;
     uint8_t* touched = nullptr;
     int n_act = 0, n_touched = 0, n_act_faces = 0, n_grad_blocks = 0;
+    int grad_cap_list = 0;
     std::vector<void*> allocs;
     GraphSlot graph;
   };

@@ -411,38 +411,86 @@ constexpr int kGradCells = 32;
 template <int NB>
 __global__ void __launch_bounds__(kGradCells* kMaxBins)
     k_grad_staged(Geo<float> g, const float4* __restrict__ rad, float* __restrict__ G, int limiter, float lim_eps2,
-                  int cap, int* status) {
+                  int cap, int* status, int list_mode) {
   extern __shared__ float4 sm[];  // [cap] weight records, then [cap] offset records
   __shared__ __align__(8) uint64_t bar;
+  __shared__ int so[kGradCells];  // list mode: first record of each cell in shared memory
+  static_assert(kGradCells == 32, "list mode scans one cell per lane of warp 0");
   const int B = g.B;
-  const int c0 = (g.blist ? __ldg(g.blist + blockIdx.x) : (int)blockIdx.x) * kGradCells;
-  const int c1 = min(c0 + kGradCells, g.C);
-  const int kb0 = __ldg(g.off + c0), kb1 = __ldg(g.off + c1);
   const int lt = threadIdx.x;
   const int cl = divb(lt, g.divB), b = lt - cl * B;
-  const int i = c0 + cl;
-  const bool active = i < c1 && (!g.touched || __ldg(g.touched + i));
+  int i, k0 = 0, k1 = 0, kb0 = 0;
+  bool active;
   if (lt == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  if (lt == 0) {
-    const uint32_t bytes = (uint32_t)(kb1 - kb0) * (uint32_t)sizeof(float4);
-    mbar_arrive_expect_tx(&bar, 2 * bytes);
-    bulk_g2s(sm, g.hw + kb0, bytes, &bar);
-    bulk_g2s(sm + cap, g.hx + kb0, bytes, &bar);
+  if (!list_mode) {
+    // kGradCells consecutive cells: their records are one contiguous range
+    const int c0 = (g.blist ? __ldg(g.blist + blockIdx.x) : (int)blockIdx.x) * kGradCells;
+    const int c1 = min(c0 + kGradCells, g.C);
+    kb0 = __ldg(g.off + c0);
+    const int kb1 = __ldg(g.off + c1);
+    i = c0 + cl;
+    active = i < c1 && (!g.touched || __ldg(g.touched + i));
+    __syncthreads();
+    if (lt == 0) {
+      const uint32_t bytes = (uint32_t)(kb1 - kb0) * (uint32_t)sizeof(float4);
+      mbar_arrive_expect_tx(&bar, 2 * bytes);
+      bulk_g2s(sm, g.hw + kb0, bytes, &bar);
+      bulk_g2s(sm + cap, g.hx + kb0, bytes, &bar);
+    }
+  } else {
+    // kGradCells entries of the touched-cell list: one contiguous range of
+    // records per cell, packed in shared memory at the prefix sums of the
+    // cells' face counts (warp 0, one cell per lane), one bulk copy per cell
+    // and array, all counted on the one mbarrier
+    const int l0 = blockIdx.x * kGradCells;
+    int ci = 0, o0 = 0, deg = 0, total = 0;
+    if (lt < 32) {
+      if (l0 + lt < g.nc) {
+        ci = __ldg(g.clist + l0 + lt);
+        o0 = __ldg(g.off + ci);
+        deg = __ldg(g.off + ci + 1) - o0;
+      }
+      int sc = deg;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, sc, d);
+        if (lt >= d) sc += v;
+      }
+      total = __shfl_sync(0xffffffffu, sc, 31);
+      so[lt] = sc - deg;
+    }
+    __syncthreads();
+    if (lt < 32) {
+      if (lt == 0) mbar_arrive_expect_tx(&bar, 2u * (uint32_t)total * (uint32_t)sizeof(float4));
+      if (deg > 0) {
+        const uint32_t bytes = (uint32_t)deg * (uint32_t)sizeof(float4);
+        bulk_g2s(sm + so[lt], g.hw + o0, bytes, &bar);
+        bulk_g2s(sm + cap + so[lt], g.hx + o0, bytes, &bar);
+      }
+    }
+    active = l0 + cl < g.nc;
+    i = active ? __ldg(g.clist + l0 + cl) : 0;
   }
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-  int k0 = 0, k1 = 0;
   float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
   if (active) {
     pi = __ldg(rad + (size_t)i * B + b);
-    k0 = __ldg(g.off + i) - kb0;
-    k1 = __ldg(g.off + i + 1) - kb0;
+    if (!list_mode) {
+      k0 = __ldg(g.off + i) - kb0;
+      k1 = __ldg(g.off + i + 1) - kb0;
+    } else {
+      k0 = so[cl];
+      k1 = k0 + (__ldg(g.off + i + 1) - __ldg(g.off + i));
+    }
     const float* m = g.minv + 6 * (size_t)i;
     m00 = __ldg(m); m01 = __ldg(m + 1); m02 = __ldg(m + 2); m11 = __ldg(m + 3); m12 = __ldg(m + 4);
     m22 = __ldg(m + 5);
   }
   if (!mbar_wait(&bar, 0)) {
+    // record the timeout, give the copies in flight a second bounded wait
+    // to land before the block's shared memory goes away, and give up
     if (lt == 0) atomicOr(status, kStTimeout);
+    mbar_wait(&bar, 0);
     return;
   }
   if (!active) return;
