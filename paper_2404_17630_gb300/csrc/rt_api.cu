@@ -294,7 +294,11 @@ void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
   a.heun = stage;
   const long long n = (long long)(ctx->all_active ? ctx->C : ctx->n_touched) * ctx->B;
   if (n == 0) return;
-  if (mixed(ctx) && comp_sum(ctx))
+  // with the FP32 flux array held in L2 (129 MB on GB300) the predicated form
+  const bool in_l2 = (size_t)ctx->F * ctx->B * sizeof(float4) <= ctx->l2_bytes;
+  if (mixed(ctx) && comp_sum(ctx) && in_l2)
+    k_gather<float, true, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
+  else if (mixed(ctx) && comp_sum(ctx))
     k_gather<float, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
   else if (mixed(ctx))
     k_gather<float, false><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
@@ -388,6 +392,12 @@ rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
     cudaGetLastError();
     ctx->n_sm = 1;
   }
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess || l2 < 0) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  ctx->l2_bytes = (size_t)l2;
   *out = ctx;
   return RT_OK;
 }

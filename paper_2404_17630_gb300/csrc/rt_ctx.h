@@ -18,6 +18,7 @@ struct rt_ctx {
   bool mesh_ready = false;
   int C = 0, F = 0, B = 0, max_deg = 0;
   int n_sm = 1;       // streaming multiprocessors of the device
+  size_t l2_bytes = 0;  // L2 cache size of the device
   int grad_cap = 0;  // half-edge records of the largest gradient block (0: unstaged gradient kernel)
   double min_dx_cm = 0;
   // FP64 cell and face data

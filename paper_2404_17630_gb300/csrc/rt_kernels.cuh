@@ -760,7 +760,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // FP64.  Comp (mixed precision): the FP32 terms are summed as an unevaluated
 // FP32 pair hi + lo (error-free two_sum), widened to FP64 once; otherwise
 // each term is widened and summed in FP64.  Writes the FP32 shadow if given.
-template <class R, bool Comp>
+// Pred: the face loads in batches of four with a predicated last batch (no
+// serial tail of single loads) -- faster where the flux array is held in L2,
+// slower where the loads go to HBM and the extra registers cost occupancy.
+template <class R, bool Comp, bool Pred = false>
 __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
                                                 float4* __restrict__ shadow) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -784,19 +787,34 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
         lo[q] += err;
       }
     };
-    int k = k0;
-    // batches of four faces: all index and flux loads issued before use;
-    // the terms are still added in CSR order
-    for (; k + 4 <= k1; k += 4) {
-      const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
-                e3 = __ldg(a.csr + k + 3);
-      const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
-                  v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
-      add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
-    }
-    for (; k < k1; ++k) {
-      const int e = __ldg(a.csr + k);
-      add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
+    if constexpr (Pred) {
+      for (int k = k0; k < k1; k += 4) {
+        int e[4];
+        R4<R> v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? __ldg(a.csr + k + u) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + u < k1) v[u] = ld4<R>(flux + (size_t)(e[u] >> 1) * B + b);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (k + u < k1) add(e[u], v[u]);
+      }
+    } else {
+      int k = k0;
+      // batches of four faces: all index and flux loads issued before use;
+      // the terms are still added in CSR order
+      for (; k + 4 <= k1; k += 4) {
+        const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
+                  e3 = __ldg(a.csr + k + 3);
+        const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
+                    v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
+        add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
+      }
+      for (; k < k1; ++k) {
+        const int e = __ldg(a.csr + k);
+        add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q] = f2d_int(hi[q]) + f2d_int(lo[q]);
