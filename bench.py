@@ -127,12 +127,12 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, precision, cells):
+def ncu_traffic(kernel, precision, cells, path=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     from the current kernel sources on a mesh of this many cells; else None
     (traffic does not scale in proportion between meshes that do and do not
     fit in L2)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
