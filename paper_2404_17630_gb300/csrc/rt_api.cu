@@ -156,13 +156,15 @@ rt_status check_config(const rt_config* c) {
 template <class R> Geo<R> geo(const rt_ctx* ctx);
 template <> Geo<double> geo<double>(const rt_ctx* c) {
   return Geo<double>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, c->nA64, c->rL64, c->rR64, c->w64, c->minv64,
-                     (const d4*)c->hw, (const d4*)c->hx, nullptr, nullptr, c->B, c->touched_cells, c->n_touched,
+                     (const d4*)c->hw, (const d4*)c->hx, (const double*)c->xmax, nullptr, nullptr, c->B,
+                     c->touched_cells, c->n_touched,
                      c->grad_blocks, c->n_grad_blocks, c->touched, c->act_faces, c->n_act_faces};
 }
 template <> Geo<float> geo<float>(const rt_ctx* c) {
   // the FP32 sweep reads faces through fa / fb; no per-array face copies
   return Geo<float>{c->C, c->F, c->B, make_divb(c->B), c->off, c->csr, c->nbr, c->lr, nullptr, nullptr, nullptr, nullptr,
-                    c->minv32, (const float4*)c->hw, (const float4*)c->hx, c->fa32, c->fb32, pad_bins(c->B),
+                    c->minv32, (const float4*)c->hw, (const float4*)c->hx, (const float*)c->xmax, c->fa32, c->fb32,
+                    pad_bins(c->B),
                     c->touched_cells, c->n_touched, c->grad_blocks, c->n_grad_blocks, c->touched, c->act_faces,
                     c->n_act_faces};
 }
@@ -508,6 +510,9 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
       if (e != cudaSuccess) return cuda_fail(ctx, e, "half-edges");
       ctx->allocs.push_back(p); *h = p;
     }
+    e = cudaMalloc(&p, std::max<size_t>((size_t)C * rs, 1));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "half-edges");
+    ctx->allocs.push_back(p); ctx->xmax = p;
   }
   if (mx) {
     AL(ctx->fa32, F); AL(ctx->fb32, F); AL(ctx->minv32, 6 * (size_t)C); AL(ctx->ivol, C);
@@ -563,6 +568,11 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     else
       k_build_halfedges<double><<<nblk(2LL * F), kThreads, 0, ctx->stream>>>(
           2 * F, ctx->csr, ctx->nbr, ctx->w64, ctx->rL64, ctx->rR64, (d4*)ctx->hw, (d4*)ctx->hx);
+    if (mx)
+      k_cell_xmax<float><<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->off, (const float4*)ctx->hx,
+                                                               (float*)ctx->xmax);
+    else
+      k_cell_xmax<double><<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->off, (const d4*)ctx->hx, (double*)ctx->xmax);
   }
   if ((st = launched(ctx, "geometry kernels"))) return st;
   int h_status = 0;

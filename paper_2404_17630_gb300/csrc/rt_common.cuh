@@ -198,6 +198,7 @@ template <class R> struct Geo {
   const R* minv;          // 6C: symmetric inverse of sum A n n^T (xx, xy, xz, yy, yz, zz)
   const R4<R>* hw;        // 2F half-edges in CSR order: (+-w of the face, sign + for the left cell; neighbour id bits)
   const R4<R>* hx;        // 2F half-edges in CSR order: x_f - s of this cell's side
+  const R* xmax;          // C: max over the cell's half-edges of hx.w (|x| in FP32, |x|^2 in FP64)
   const f8* fa;           // FP32 sweep, F: (n, A, x_f - s_L, left id bits)
   const float4* fb;       // FP32 sweep, F: (x_f - s_R, right id bits)
   int Bp;                 // FP32 gradient records: bins per group (pad_bins(B))

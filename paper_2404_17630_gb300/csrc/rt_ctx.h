@@ -27,6 +27,7 @@ struct rt_ctx {
   int2* lr = nullptr;
   d4 *nA64 = nullptr, *rL64 = nullptr, *rR64 = nullptr, *w64 = nullptr;
   void *hw = nullptr, *hx = nullptr;   // half-edge records in the sweep precision
+  void* xmax = nullptr;                 // per cell: the largest .w of its offset records (sweep precision)
   double* minv64 = nullptr;
   // FP32 copies (mixed precision)
   f8* fa32 = nullptr;          // FP32 face records (n, A, x_f - s_L, left)

@@ -112,6 +112,20 @@ __global__ void k_build_halfedges(int n, const int32_t* __restrict__ csr, const 
   hx[k] = b;
 }
 
+// Per cell, the largest hx.w over its half-edges (|x| in FP32, |x|^2 in FP64):
+// the limiter's one-pass test (k_grad, k_grad_staged).
+template <class R>
+__global__ void k_cell_xmax(int C, const int32_t* __restrict__ off, const R4<R>* __restrict__ hx, R* xmax) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C) return;
+  R m = R(0);
+  for (int k = off[i]; k < off[i + 1]; ++k) {
+    const R w = hx[k].w;
+    m = w > m ? w : m;
+  }
+  xmax[i] = m;
+}
+
 // Face records of the FP32 sweep: (n, A, x_f - s_L, left id) in 32 bytes
 // and (x_f - s_R, right id) in 16 bytes.
 __global__ void k_build_facerecs(int F, const int2* __restrict__ lr, const d4* __restrict__ nA,
@@ -209,6 +223,98 @@ __device__ __forceinline__ double neg_from_bits(long long m) {
   return __longlong_as_double(m ? (m | (long long)0x8000000000000000ULL) : 0LL);
 }
 
+// Limiter extremes of one (cell, bin) over its faces k0..k1-1: dpos =
+// max(0, max g.x_f) and dneg = min(0, min g.x_f) over the faces that pass
+// the regularisation test |g.x_f| > eps |g| |x_f|.  First one pass without
+// the test.  Its extremes are those of the definition whenever each nonzero
+// one clears the test bound of the cell's largest |x_f| (X): the face that
+// attains it then passes its own test, since rounding is monotone.  Only
+// otherwise (an extreme within the band; rare) the pass with the test runs.
+// FP32: eg = eps |g|, X and x.w = |x_f|.
+__device__ __forceinline__ void lim_extremes(const float4* __restrict__ xs, int k0, int k1, const float gr[4][3],
+                                             const float eg[4], float X, float dpos[4], float dneg[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.0f;
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const float4 x = xs[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+      dpos[q] = fmaxf(dpos[q], dphi);
+      dneg[q] = fminf(dneg[q], dphi);
+    }
+  }
+  bool exact = true;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float t = eg[q] * X;
+    exact = exact && (dpos[q] == 0.0f || dpos[q] > t) && (dneg[q] == 0.0f || -dneg[q] > t);
+  }
+  if (exact) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.0f;
+  for (int k = k0; k < k1; ++k) {
+    const float4 x = xs[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+      const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
+      dpos[q] = fmaxf(dpos[q], dm);
+      dneg[q] = fminf(dneg[q], dm);
+    }
+  }
+}
+
+// The same in FP64, where the test compares squares (thr = eps^2 |g|^2, X
+// and x.w = |x_f|^2) and the extremes are kept as bit patterns (integer
+// compares; the FP64 pipe is the kernel's bound).
+__device__ __forceinline__ void lim_extremes(const d4* __restrict__ xs, int k0, int k1, const double gr[4][3],
+                                             const double thr[4], double X, double dpos[4], double dneg[4]) {
+  long long bpos[4], bneg[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bpos[q] = bneg[q] = 0;
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const d4 x = ld4<double>(xs + k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+      bpos[q] = max_bits_pos(bpos[q], dphi);
+      bneg[q] = max_bits_neg(bneg[q], dphi);
+    }
+  }
+  bool exact = true;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const long long t = __double_as_longlong(thr[q] * X);
+    const double p = __longlong_as_double(bpos[q]), n = neg_from_bits(bneg[q]);
+    exact = exact && (bpos[q] == 0 || __double_as_longlong(p * p) > t) &&
+            (bneg[q] == 0 || __double_as_longlong(n * n) > t);
+  }
+  if (!exact) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bpos[q] = bneg[q] = 0;
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+      const d4 x = ld4<double>(xs + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+        if (__double_as_longlong(dphi * dphi) > __double_as_longlong(thr[q] * x.w)) {
+          bpos[q] = max_bits_pos(bpos[q], dphi);
+          bneg[q] = max_bits_neg(bneg[q], dphi);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    dpos[q] = __longlong_as_double(bpos[q]);
+    dneg[q] = neg_from_bits(bneg[q]);
+  }
+}
+
 // max / min of two finite values: one FMNMX in FP32; the FP64 sweep keeps
 // the comparison form of the limiter's definition.
 template <class R> __device__ __forceinline__ R rmax(R a, R b) {
@@ -302,52 +408,16 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
     // (most negative) g.x: two divisions per component instead of one per
     // face, with bitwise the same result.
     R dpos[4], dneg[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = R(0);
     if constexpr (sizeof(R) == 4) {
-      // |g.x| > eps |g| |x| with |x| from the record: a threshold product,
-      // an abs-compare and a select per component; excluded faces add 0
       float eg[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) eg[q] = sqrtf(lim_eps2 * gg[q]);
-#pragma unroll 4
-      for (int k = k0; k < k1; ++k) {
-        const R4<R> x = ld4<R>(g.hx + k);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-          const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
-          dpos[q] = fmaxf(dpos[q], dm);
-          dneg[q] = fminf(dneg[q], dm);
-        }
-      }
+      lim_extremes(g.hx, k0, k1, gr, eg, __ldg(g.xmax + i), dpos, dneg);
     } else {
-      // the threshold test compares two non-negative doubles and the
-      // extremes are kept as bits, as above: integer compares throughout
-      long long bpos[4], bneg[4];
       R thr[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        bpos[q] = bneg[q] = 0;
-        thr[q] = lim_eps2 * gg[q];
-      }
-#pragma unroll 1
-      for (int k = k0; k < k1; ++k) {
-        const R4<R> x = ld4<R>(g.hx + k);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const R dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-          if (__double_as_longlong(dphi * dphi) > __double_as_longlong(thr[q] * x.w)) {
-            bpos[q] = max_bits_pos(bpos[q], dphi);
-            bneg[q] = max_bits_neg(bneg[q], dphi);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        dpos[q] = __longlong_as_double(bpos[q]);
-        dneg[q] = neg_from_bits(bneg[q]);
-      }
+      for (int q = 0; q < 4; ++q) thr[q] = lim_eps2 * gg[q];
+      lim_extremes(g.hx, k0, k1, gr, thr, __ldg(g.xmax + i), dpos, dneg);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -472,7 +542,7 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
     i = active ? __ldg(g.clist + l0 + cl) : 0;
   }
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-  float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+  float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f, xm = 0.f;
   if (active) {
     pi = __ldg(rad + (size_t)i * B + b);
     if (!list_mode) {
@@ -485,6 +555,7 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
     const float* m = g.minv + 6 * (size_t)i;
     m00 = __ldg(m); m01 = __ldg(m + 1); m02 = __ldg(m + 2); m11 = __ldg(m + 3); m12 = __ldg(m + 4);
     m22 = __ldg(m + 5);
+    xm = __ldg(g.xmax + i);
   }
   if (!mbar_wait(&bar, 0)) {
     // record the timeout, give the copies in flight a second bounded wait
@@ -535,19 +606,7 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
   }
   if (limiter) {
     float dpos[4], dneg[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.f;
-#pragma unroll 4
-    for (int kk = k0; kk < k1; ++kk) {
-      const float4 x = shx[kk];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
-        const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
-        dpos[q] = fmaxf(dpos[q], dm);
-        dneg[q] = fminf(dneg[q], dm);
-      }
-    }
+    lim_extremes(shx, k0, k1, gr, eg, xm, dpos, dneg);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float vi = comp<float>(pi, q);
