@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -117,13 +118,24 @@ def algorithmic_bytes(kernel, C, F, B, w):
     raise KeyError(kernel)
 
 
-def source_hash():
+def code_text(src):
+    """C/C++/CUDA source without its comments and blank lines (string
+    literals, which hold no comment markers in these sources, are kept)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
+def source_hash(root=None):
+    """Hash of the kernel and boundary sources, comments excluded: a counter
+    summary stays valid across comment-only edits."""
+    root = root or ROOT
     h = hashlib.sha256()
     for d in ("paper_2404_17630_gb300/csrc", "include"):
-        for name in sorted(os.listdir(os.path.join(ROOT, d))):
+        for name in sorted(os.listdir(os.path.join(root, d))):
             if name.endswith((".cu", ".cuh", ".h")):
-                with open(os.path.join(ROOT, d, name), "rb") as f:
-                    h.update(f.read())
+                with open(os.path.join(root, d, name), encoding="utf-8") as f:
+                    h.update(code_text(f.read()).encode())
     return h.hexdigest()[:16]
 
 

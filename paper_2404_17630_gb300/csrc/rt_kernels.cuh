@@ -469,13 +469,16 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
 }
 
 // The same gradients and limiter for the FP32 sweep with the half-edge
-// records staged in shared memory.  A block owns kGradCells consecutive
-// cells, whose records are one contiguous range of the CSR arrays: one
-// thread issues two bulk copies (TMA engine) of that range into shared
-// memory, completed on an mbarrier, while every thread loads its own cell
-// state; afterwards the only global loads left per face are the neighbour
-// states, issued NB at a time.  `cap` is the largest record count of any
-// block (the dynamic shared memory holds 2 cap records).
+// records staged in shared memory.  A block owns kGradCells cells: in block
+// mode kGradCells consecutive cells, whose records are one contiguous range
+// of the CSR arrays, copied by two bulk copies (TMA engine) from one thread;
+// in list mode (list_mode != 0, an active set) kGradCells consecutive
+// entries of the touched-cell list, each cell's records copied by its own
+// two bulk copies to the prefix sums of the cells' face counts.  The copies
+// complete on one mbarrier while every thread loads its own cell state;
+// afterwards the only global loads left per face are the neighbour states,
+// issued NB at a time.  `cap` is the largest record count of any block (the
+// dynamic shared memory holds 2 cap records).
 constexpr int kGradCells = 32;
 
 template <int NB>

@@ -88,3 +88,20 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_source_hash_ignores_comments(tmp_path):
+    """The traffic summary is keyed by a hash of the kernel sources without
+    comments: a comment-only edit keeps it, a code edit does not."""
+    import shutil
+    root = tmp_path / "r"
+    for d in ("paper_2404_17630_gb300/csrc", "include"):
+        shutil.copytree(bench.ROOT + "/" + d, root / d)
+    h0 = bench.source_hash(str(root))
+    assert h0 == bench.source_hash()
+    f = root / "include" / "rt.h"
+    f.write_text(f.read_text() + "\n/* a note */\n// another\n")
+    assert bench.source_hash(str(root)) == h0
+    f.write_text(f.read_text() + "\nint rt_unused_symbol;\n")
+    assert bench.source_hash(str(root)) != h0
+    assert bench.code_text("a = 1; // x\n/* y\n z */ b = 2;\n\n") == "a = 1;\n  b = 2;"
