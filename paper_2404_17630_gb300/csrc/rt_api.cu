@@ -287,6 +287,18 @@ template <class R> void launch_flux(rt_ctx* ctx) {
                                                    (R4<R>*)ctx->flux);
 }
 
+template <bool Heun> void launch_gather_k(rt_ctx* ctx, const CellArgs& a, long long n, bool in_l2) {
+  const float4* f32 = (const float4*)ctx->flux;
+  if (mixed(ctx) && comp_sum(ctx) && in_l2)
+    k_gather<float, true, true, Heun><<<nblk(n), kThreads, 0, ctx->stream>>>(a, f32, ctx->shadow);
+  else if (mixed(ctx) && comp_sum(ctx))
+    k_gather<float, true, false, Heun><<<nblk(n), kThreads, 0, ctx->stream>>>(a, f32, ctx->shadow);
+  else if (mixed(ctx))
+    k_gather<float, false, false, Heun><<<nblk(n), kThreads, 0, ctx->stream>>>(a, f32, ctx->shadow);
+  else
+    k_gather<double, false, false, Heun><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const d4*)ctx->flux, nullptr);
+}
+
 // stage: 0 plain update; 1 also keeps the input state in rad0 (first Heun
 // stage); 2 forms U/2 + U2/2 with the state kept in rad0 (second stage)
 void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
@@ -298,14 +310,10 @@ void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
   if (n == 0) return;
   // with the FP32 flux array held in L2 (129 MB on GB300) the predicated form
   const bool in_l2 = (size_t)ctx->F * ctx->B * sizeof(float4) <= ctx->l2_bytes;
-  if (mixed(ctx) && comp_sum(ctx) && in_l2)
-    k_gather<float, true, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
-  else if (mixed(ctx) && comp_sum(ctx))
-    k_gather<float, true><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
-  else if (mixed(ctx))
-    k_gather<float, false><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const float4*)ctx->flux, ctx->shadow);
+  if (stage == 0)
+    launch_gather_k<false>(ctx, a, n, in_l2);
   else
-    k_gather<double, false><<<nblk(n), kThreads, 0, ctx->stream>>>(a, (const d4*)ctx->flux, nullptr);
+    launch_gather_k<true>(ctx, a, n, in_l2);
 }
 
 void launch_chem(rt_ctx* ctx, double dt) {

@@ -825,7 +825,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // Pred: the face loads in batches of four with a predicated last batch (no
 // serial tail of single loads) -- faster where the flux array is held in L2,
 // slower where the loads go to HBM and the extra registers cost occupancy.
-template <class R, bool Comp, bool Pred = false>
+// Heun: the kernel handles Heun's stages (a.heun); the plain update is its
+// own instantiation, without the stages' code (which the compiler would
+// otherwise issue as predicated FP64 instructions on every launch).
+template <class R, bool Comp, bool Pred = false, bool Heun = false>
 __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
                                                 float4* __restrict__ shadow) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -909,12 +912,12 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   // instead of a division per subcycle); the FP64 sweep divides as defined
   const double kfac = sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
   d4 u = a.rad[t];
-  if (a.heun == 1) a.rad0[t] = u;
+  if (Heun && a.heun == 1) a.rad0[t] = u;
   u.x -= kfac * acc[0];
   u.y -= kfac * acc[1];
   u.z -= kfac * acc[2];
   u.w -= kfac * acc[3];
-  if (a.heun == 2) {
+  if (Heun && a.heun == 2) {
     const d4 u0 = a.rad0[t];
     u.x = 0.5 * u0.x + 0.5 * u.x;
     u.y = 0.5 * u0.y + 0.5 * u.y;
