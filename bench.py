@@ -230,6 +230,23 @@ def l2_flush(buf):
     buf.add_(1.0)
 
 
+def max_over_ranks(ms, dist, device):
+    """The timed region's length on the slowest rank (replicas: every rank
+    times the same work on its own GPU; no data is exchanged)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, cells, n_sub, steps, ms):
+    """Whole-job cell-updates/s: the cells all ranks advanced over the
+    slowest rank's time (weak scaling: each replica holds the whole mesh)."""
+    return world * cells * n_sub * steps / (ms / 1e3)
+
+
 def run_gpu(precision, mesh, cfg, state, steps, warmup, rank, world, dev, dist, clocks=None, gather_sum=1):
     import torch
     from paper_2404_17630_gb300 import RT, make_config
@@ -263,10 +280,7 @@ def run_gpu(precision, mesh, cfg, state, steps, warmup, rank, world, dev, dist, 
     rt.sync()
     ms = ev0.elapsed_time(ev1)
     launches = rtb.rt_launch_count(rt.ctx) - n0
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     # per-kernel device times over the same number of steps (profiled pass)
     rtb.rt_profile_read(rt.ctx, reset=True)
     rtb.rt_profile_enable(rt.ctx, True)
@@ -720,7 +734,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         r64 = run_gpu("fp64", mesh, cfg, state, max(2, args.steps // 5), 1, rank, world, dev, dist)
-        fp64 = {"value": world * r64["C"] * N_SUB * max(2, args.steps // 5) / (r64["ms"] / 1e3),
+        fp64 = {"value": replica_value(world, r64["C"], N_SUB, max(2, args.steps // 5), r64["ms"]),
                 "ms_per_step": r64["ms"] / max(2, args.steps // 5), "dtype": "f64"}
         rf64, k64, rf64m = roofline(r64, "fp64", peaks, peak_kind, attempts=r64.get("attempts"))
         fp64["roofline"] = rf64
@@ -730,7 +744,7 @@ def main():
     if not args.no_fp64:
         n64s = max(2, args.steps // 2)
         r = run_gpu("mixed", mesh, cfg, state, n64s, 1, rank, world, dev, dist, gather_sum=0)
-        fp64sum = {"value": world * r["C"] * N_SUB * n64s / (r["ms"] / 1e3), "ms_per_step": r["ms"] / n64s,
+        fp64sum = {"value": replica_value(world, r["C"], N_SUB, n64s, r["ms"]), "ms_per_step": r["ms"] / n64s,
                    "note": "mixed precision with each FP32 face flux widened and summed in FP64 (gather_sum=0)"}
     e2e = None if args.no_e2e else e2e_measure("mixed", mesh, cfg, state, max(2, args.steps // 2), args.warmup, dev)
     large = None if args.no_large else measure_large(3, 1, dev)
@@ -741,7 +755,7 @@ def main():
     if rank != 0:
         return
     C, F = res["C"], res["F"]
-    value = world * C * N_SUB * args.steps / (res["ms"] / 1e3)
+    value = replica_value(world, C, N_SUB, args.steps, res["ms"])
     rf, kern, rf_mem = roofline(res, "mixed", peaks, peak_kind, attempts=res.get("attempts"))
     cpu = None if args.no_cpu else cpu_baseline(mesh, cfg, state)
     ws = (C * 3 * (32 + 16 + 48) + F * (64 + 48) + C * 200)
