@@ -28,9 +28,11 @@
  * Parity pins: uniform-field invariance, photon conservation, the travelling
  * wave, the light-front speed, ionisation equilibrium, the Stroemgren radius,
  * the Cartesian central-difference gradient and hand-expanded two-cell fluxes
- * are checked by tests/test_oracle_pins.py.  The full H+He thermal model
- * (rates, cooling) is "parity unpinned" beyond conservation, equilibrium and
- * the alpha_B(1e4 K) value: the paper prints no profiles for it.
+ * are checked by tests/test_oracle_pins.py, as is the energy budget of
+ * photoheating (thermal energy gained = heat per ionisation x ionisations).
+ * The cooling function (the KWH96 rates) is "parity unpinned" beyond
+ * conservation, equilibrium and the alpha_B(1e4 K) value: the paper prints
+ * no profiles for it.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * arithmetic is the literal sequence written here).

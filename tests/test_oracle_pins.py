@@ -236,6 +236,44 @@ def test_photon_number_and_flux_conserved_transport_only():
     assert np.abs(N1 - N0).max() > 1e-3 * N0.max()  # something did move
 
 
+def test_photoheating_energy_budget():
+    """Thermal energy (Sec. 2.3.1, reading 10 v) against the ionisation
+    count: hydrogen only, one bin, photoheating on and recombination,
+    collisional ionisation and cooling off.  Every photoionisation then
+    deposits exactly eps of heat, so per cell the thermal energy
+    3/2 k n_tot T grows by eps n_H (x_HII' - x_HII) -- the energy equation
+    and the abundance update are separate parts of the step, so a dropped
+    or misplaced heat term, a wrong n_tot or a wrong eps index fails here.
+    Over several adaptive substeps the identity telescopes."""
+    kB = 1.380649e-16
+    eps = 4.2e-12          # erg per photoionisation (grey; any positive value)
+    sigma = 3.0e-18        # cm^2
+    mesh, cfg, st = voronoi_case(n=8, n_bins=1, chem_mode=2, chem_flags=8, y_he=0.0,
+                                 sigma=[[sigma, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]],
+                                 eps=[[eps, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    st["cells"] = np.zeros(0, np.int64)
+    st["Q"] = np.zeros((0, 1))
+    st["N"] *= 1e2
+    C = mesh.n_cells
+    x5 = np.zeros((5, C))
+    x5[1] = np.random.default_rng(3).uniform(0.0, 0.5, C)
+    x5[0] = 1.0 - x5[1]
+    x5[2] = 1.0
+    st["x5"] = x5
+    o = make_oracle(mesh, cfg, st)
+    nH = st["nH"]
+    x0, T0 = o.gas()
+    dt = 4 * o.max_dt()
+    assert o.thermochemistry(dt) == 0
+    x1, T1 = o.gas()
+    assert o.substeps().max() > 1                   # several accepted substeps
+    e0 = 1.5 * kB * nH * (1.0 + x0[1]) * T0
+    e1 = 1.5 * kB * nH * (1.0 + x1[1]) * T1
+    heat = eps * nH * (x1[1] - x0[1])
+    assert heat.min() > 0 and np.all(x1[1] > x0[1])
+    np.testing.assert_allclose(e1 - e0, heat, rtol=1e-9, atol=1e-12 * np.abs(e0).max())
+
+
 def test_photon_conservation_with_absorption_no_recombination():
     """Absorption on, recombination and collisional ionisation off, no
     sources: every absorbed photon becomes one free electron, so
