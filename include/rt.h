@@ -68,8 +68,11 @@ enum {
   RT_FIELD_NSUB = 16  /* chemistry attempts of each cell in the last subcycle, C (as double) */
 };
 
-/* Method parameters (Sec. 2.2, 2.3; the chemistry rates are the readings
- * documented in the library's design notes). */
+/* Method parameters (Sec. 2.2, 2.3).  The chemistry's rate coefficients are
+ * fits the paper does not print: case-B recombination of HII and HeIII from
+ * Hui & Gnedin (1997), HeII case B plus dielectronic recombination,
+ * collisional ionisation and the cooling set from Katz, Weinberg & Hernquist
+ * (1996). */
 typedef struct {
   int n_bins;             /* 1..3 frequency bins (HI-, HeI-, HeII-ionising) */
   int precision;          /* RT_FP64, or RT_MIXED: FP32 transport sweep, FP64 update and chemistry (Sec. 6.2) */

@@ -16,7 +16,8 @@ C2E5, F2E5 = 205379, 1584871   # the 59^3 jittered-lattice Voronoi mesh
                                         (8, {"k_grad": 1115, "k_flux": 1804, "k_gather": 1007, "k_chem": 312})])
 def test_algorithmic_bytes_per_cell(w, expected):
     """Per cell at F/C = 7.717, B = 3: the compulsory traffic of each kernel
-    (mixed w = 4, FP64 w = 8), as tabulated in the design notes."""
+    (mixed w = 4, FP64 w = 8): the per-cell compulsory traffic of each
+    kernel, worked out by hand from the arrays it reads and writes."""
     for k, per_cell in expected.items():
         assert bench.algorithmic_bytes(k, C2E5, F2E5, 3, w) / C2E5 == pytest.approx(per_cell, abs=0.5), k
 
