@@ -35,3 +35,17 @@ def test_binding_has_the_c_names():
     import paper_2404_17630_gb300.rt as rt
     for s in declared_symbols():
         assert hasattr(rt, s), s
+
+
+def test_no_gpu_fails_loudly():
+    """Without a CUDA device the library refuses with a status code and a
+    message (no host fallback computes anything in its place)."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
+    with pytest.raises(rtb.RTError) as e:
+        RT(make_config(n_bins=3))
+    assert "RT_CUDA" in str(e.value)
