@@ -300,6 +300,27 @@ def test_mixed_step_fewer_bins(n_bins):
     compare_state(rt, o, 1e-4)
 
 
+@pytest.mark.parametrize("n_bins", [1, 2])
+def test_sparse_active_set_fewer_bins(n_bins):
+    """A clustered sparse mask (the cells within a quarter box length of
+    the centre, 6 % active: the touched cells fill about a third of the
+    32-cell blocks they reach, so the staged gradients run over the
+    touched-cell list) with one and two bins in the mixed path, against the
+    oracle."""
+    mesh, cfg, st = voronoi_case(n=12, n_bins=n_bins, n_src=3)
+    c = np.stack([mesh.cx, mesh.cy, mesh.cz], axis=1)
+    m = np.linalg.norm(c - cfg["box"] / 2, axis=1) < 0.25 * cfg["box"]
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1)
+    o.set_active(m)
+    rt.set_active(m)
+    dt = o.max_dt()
+    assert o.step(2 * dt, 2) == 0
+    rt.step(2 * dt, 2)
+    assert rt.sync() == 0
+    compare_state(rt, o, 1e-4)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_no_cell_active(precision):
     """A mask with no active cell: no sources, no chemistry, no interface
