@@ -126,16 +126,23 @@ def code_text(src):
     return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
 
 
+# Translation units that define no subcycle kernel (the allocation-free
+# gradient entry point and the failure-path check): they are left out of the
+# hash that dates the counter summaries.
+NOT_SUBCYCLE = ("rt_noalloc.cu", "rt_selftest.cu")
+
+
 def source_hash(root=None):
-    """Hash of the kernel and boundary sources, comments excluded: a counter
-    summary stays valid across comment-only edits."""
+    """Hash of the sources of the subcycle kernels and their launches
+    (`csrc/` but the units in NOT_SUBCYCLE), comments excluded: a counter
+    summary stays valid across comment-only edits and changes elsewhere."""
     root = root or ROOT
     h = hashlib.sha256()
-    for d in ("paper_2404_17630_gb300/csrc", "include"):
-        for name in sorted(os.listdir(os.path.join(root, d))):
-            if name.endswith((".cu", ".cuh", ".h")):
-                with open(os.path.join(root, d, name), encoding="utf-8") as f:
-                    h.update(code_text(f.read()).encode())
+    d = os.path.join(root, "paper_2404_17630_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")) and name not in NOT_SUBCYCLE:
+            with open(os.path.join(d, name), encoding="utf-8") as f:
+                h.update(code_text(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -224,6 +224,14 @@ rt_status rt_profile_read(rt_ctx *ctx, int n, double *ms, int64_t *launches, int
  * was created; mesh setup and state transfer kernels are not counted. */
 rt_status rt_launch_count(rt_ctx *ctx, int64_t *out);
 
+/* Failure-path check (not a step of the method): enqueues one block that
+ * waits on an mbarrier phase nothing completes, giving up after `polls`
+ * polls (1..65536) the way every bounded device wait of the library does;
+ * the block records the timeout in the status word.  rt_sync then returns
+ * RT_TIMEOUT, and the context stays usable.  RT_INVALID_ARG for polls out of
+ * range. */
+rt_status rt_selftest_wait_timeout(rt_ctx *ctx, uint32_t polls);
+
 /* Allocation-free gradients, for callers that cannot allocate device memory
  * (a host framework that owns all device memory through its own pool, a
  * real-time loop that must not allocate, a plug-in that only receives device

@@ -128,6 +128,7 @@ def load():
                 "rt_profile_enable": [vp, i32],
                 "rt_profile_read": [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
                 "rt_launch_count": [vp, ctypes.POINTER(i64)],
+                "rt_selftest_wait_timeout": [vp, ctypes.c_uint32],
                 "rt_adjoint": [vp, dbl, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
             }
             for name, args in sig.items():
@@ -357,6 +358,11 @@ def rt_launch_count(ctx):
     out = ctypes.c_int64()
     _check(lib, ctx, lib.rt_launch_count(ctx, ctypes.byref(out)))
     return out.value
+
+
+def rt_selftest_wait_timeout(ctx, polls):
+    lib = load()
+    _check(lib, ctx, lib.rt_selftest_wait_timeout(ctx, int(polls)))
 
 
 def rt_destroy(ctx):

@@ -92,16 +92,19 @@ def test_reference_arm_json_line():
 
 
 def test_source_hash_ignores_comments(tmp_path):
-    """The traffic summary is keyed by a hash of the kernel sources without
-    comments: a comment-only edit keeps it, a code edit does not."""
+    """The traffic summary is keyed by a hash of the subcycle kernels'
+    sources without comments: a comment-only edit keeps it, a code edit
+    changes it, and the units that define no subcycle kernel do not enter."""
     import shutil
     root = tmp_path / "r"
-    for d in ("paper_2404_17630_gb300/csrc", "include"):
-        shutil.copytree(bench.ROOT + "/" + d, root / d)
+    shutil.copytree(bench.ROOT + "/paper_2404_17630_gb300/csrc", root / "paper_2404_17630_gb300" / "csrc")
     h0 = bench.source_hash(str(root))
     assert h0 == bench.source_hash()
-    f = root / "include" / "rt.h"
+    f = root / "paper_2404_17630_gb300" / "csrc" / "rt_kernels.cuh"
     f.write_text(f.read_text() + "\n/* a note */\n// another\n")
+    assert bench.source_hash(str(root)) == h0
+    g = root / "paper_2404_17630_gb300" / "csrc" / bench.NOT_SUBCYCLE[1]
+    g.write_text(g.read_text() + "\nint rt_unused_symbol;\n")
     assert bench.source_hash(str(root)) == h0
     f.write_text(f.read_text() + "\nint rt_unused_symbol;\n")
     assert bench.source_hash(str(root)) != h0

@@ -423,3 +423,27 @@ def test_errors_are_status_codes():
     assert e.value.status == RT_CHEM_SUBSTEPS
     # the context stays usable after a reported error
     rt2.sync()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device wait that nothing completes gives up after its poll bound and
+    is reported as RT_TIMEOUT by rt_sync (the failure path of every bounded
+    wait); afterwards the same context still steps correctly."""
+    from paper_2404_17630_gb300 import rt as rtb
+    mesh, cfg, st = voronoi_case(n=8, n_src=2)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1)
+    with pytest.raises(rtb.RTError) as e:
+        rtb.rt_selftest_wait_timeout(rt.ctx, 0)
+    assert e.value.status == rtb.RT_INVALID_ARG
+    rtb.rt_selftest_wait_timeout(rt.ctx, 64)
+    with pytest.raises(rtb.RTError) as e:
+        rt.sync()
+    assert e.value.status == rtb.RT_TIMEOUT
+    assert rt.sync() == 0           # the status word was cleared
+    dt = o.max_dt()
+    assert o.step(2 * dt, 2) == 0
+    rt.step(2 * dt, 2)
+    assert rt.sync() == 0
+    compare_state(rt, o, 1e-4)
+
