@@ -91,12 +91,47 @@ def workload(n=LATTICE, seed=1, n_src=16):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch (compulsory traffic: each array the kernel
-# needs is read or written once; neighbour re-reads are not counted)
+# algorithmic bytes per launch
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(kernel, C, F, B, w):
-    """w = bytes per word of the transport sweep (8 FP64, 4 mixed)."""
+def survey_bytes(kernel, C, F, w):
+    """Compulsory bytes of one launch under the hot-path contract's traffic
+    model (each array streamed once per kernel that needs it, neighbour
+    re-reads hitting L2; per cell with fbar = F/C faces per cell; w = 8 FP64,
+    4 mixed; CSR ids and face L/R int32):
+      gradients  prim 12w + M^-1 6w + s 3w + G out 36w + CSR (4 + 8 fbar)
+                 + faces (L/R 8 + w_f 3w + x_f 3w) fbar
+      face flux  prim + G of the cells 48w + s 3w + faces (8 + (A, n, x_f) 7w)
+                 fbar + flux out 12w fbar
+      gather + chemistry  CSR (4 + 8 fbar) + flux in 12w fbar + 1/V 8
+                 + radiation master r/w (FP64 192; mixed: N FP64 + F/c FP32
+                 r/w 120 + FP32 shadow out 48) + chemistry state r/w 104
+    Totals: FP64 1176 + 328 fbar, mixed 720 + 180 fbar per cell-update.  The
+    gather and the chemistry are two kernels here: the chemistry gets its
+    104 bytes of state, the flux application the rest of that row."""
+    rad = 192 if w == 8 else 168
+    if kernel == "k_grad":
+        return (57 * w + 4) * C + (16 + 6 * w) * F
+    if kernel == "k_flux":
+        return 51 * w * C + (8 + 19 * w) * F
+    if kernel == "k_gather":
+        return (4 + 8 + rad) * C + (8 + 12 * w) * F
+    if kernel == "k_chem":
+        return 104 * C
+    raise KeyError(kernel)
+
+
+def survey_bytes_per_cell_update(C, F, w):
+    """720 + 180 fbar (mixed) or 1176 + 328 fbar (FP64) bytes."""
+    return sum(survey_bytes(k, C, F, w) for k in ("k_grad", "k_flux", "k_gather", "k_chem")) / C
+
+
+def layout_bytes(kernel, C, F, B, w):
+    """Bytes one launch moves in this implementation's data layout (each
+    array it touches read or written once; w = bytes per word of the
+    transport sweep, 8 FP64, 4 mixed).  Reported beside the contract's
+    model: it counts the offsets x_f - s of both sides and the gradient
+    records as laid out, so it is larger."""
     if kernel == "k_grad":
         # prim 4wBC, M^-1 6wC, offsets 4C, CSR 8F, face ids 8F, w_f 3wF,
         # x_f - s_L and x_f - s_R 6wF, gradients out 12wBC
@@ -127,9 +162,10 @@ def code_text(src):
 
 
 # Translation units that define no subcycle kernel (the allocation-free
-# gradient entry point and the failure-path check): they are left out of the
-# hash that dates the counter summaries.
-NOT_SUBCYCLE = ("rt_noalloc.cu", "rt_selftest.cu")
+# gradient entry point, the failure-path check and the FP64 peak
+# measurement): they are left out of the hash that dates the counter
+# summaries.
+NOT_SUBCYCLE = ("rt_noalloc.cu", "rt_selftest.cu", "rt_peak.cu")
 
 
 def source_hash(root=None):
@@ -358,96 +394,198 @@ FP64_FLOP = {
     "fp64": {"k_chem": (1238.0, "attempt"), "k_grad": (2762.4, "cell"), "k_flux": (5578.0, "cell"),
              "k_gather": (439.4, "cell")},
 }
-# GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
+# Fallback FP64 peak from unit counts and clock, used only when the
+# measurement (rt_fp64_peak) is not available: 152 SMs x 2 FP64 FMA lanes per
 # clock per SM (ncu: 16 cycles per warp instruction on the FP64 pipe) x 2 FLOP
-# x 2.07 GHz = 1.259 TFLOP/s, the nominal 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_PEAK_SOURCE = "FP64 units x clock (152 SMs x 2 FMA lanes/clk x 2 x 2.07 GHz)"
+# x 2.07 GHz = 1.259 TFLOP/s.
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def roofline(res, precision, peaks, peak_kind, attempts=None):
-    """Roofline of the kernel with the largest time share.  A kernel whose
-    FP64 work is known (FP64_FLOP) against the FP64 peak (`alu`): the
-    chemistry, and every kernel of the FP64 path; the others against the
-    measured HBM copy bandwidth.  Beside it, the memory-bound kernel with the
-    largest share against HBM."""
+def fp64_peak(stream=None):
+    """(TFLOP/s, source): the measured FMA-stream peak of this device
+    (rt_fp64_peak, best of 5 launches of ~16 ms), else the derived figure."""
+    try:
+        from paper_2404_17630_gb300 import rt as rtb
+        tf, ms = rtb.rt_fp64_peak(stream, 4096, 5)
+        return tf, f"measured: rt_fp64_peak DFMA stream, best of 5 launches ({ms:.2f} ms each)"
+    except Exception as e:  # noqa: BLE001 -- reported, then the derived figure
+        return FP64_PEAK_DERIVED, f"derived (152 SMs x 2 FMA lanes/clk x 2 x 2.07 GHz); measurement failed: {e}"
+
+
+def roofline(res, precision, peaks, peak_kind, fp64pk, attempts=None, n_sub=None, steps=None):
+    """Per-kernel rooflines.  Bytes are the contract's traffic model
+    (survey_bytes); this layout's own bytes are reported beside them
+    (`layout_*`).  A kernel whose FP64 work is known (FP64_FLOP) is also
+    reported against the measured FP64 peak (`alu`): the chemistry, and every
+    kernel of the FP64 path.  Returns the line of the kernel with the largest
+    time share (`alu` if it is FP64-bound, else `hbm`), the per-kernel table,
+    the largest memory-bound kernel's `hbm` line and the whole subcycle's."""
     C, F, B = res["C"], res["F"], 3
     w = 4 if precision == "mixed" else 8
     prof = {k: v for k, v in res["prof"].items() if v[1] > 0}
     total = sum(v[0] for v in prof.values())
     shares = {k: (v[0] / total if total else 0.0) for k, v in prof.items()}
-    kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": round(shares[k], 4),
-                "alg_bytes_per_launch": algorithmic_bytes(k, C, F, B, w),
-                "GBs": algorithmic_bytes(k, C, F, B, w) / (v[0] / 1e3 / max(v[1], 1)) / 1e9 if v[0] else None}
-            for k, v in prof.items()}
     peak = float(peaks["hbm_gbs"])
+    fpk, fsrc = fp64pk
+    kern = {}
+    for k, v in prof.items():
+        ms = v[0] / max(v[1], 1)
+        sb, lb = survey_bytes(k, C, F, w), layout_bytes(k, C, F, B, w)
+        kern[k] = {"ms_per_launch": ms, "launches": v[1], "share": round(shares[k], 4),
+                   "alg_bytes_per_launch": sb, "GBs": sb / (ms / 1e3) / 1e9 if ms else None,
+                   "layout_bytes_per_launch": lb, "layout_GBs": lb / (ms / 1e3) / 1e9 if ms else None}
+        kern[k]["hbm_frac"] = round(kern[k]["GBs"] / peak, 4) if kern[k]["GBs"] else None
     units = {"cell": C, "attempt": attempts if attempts else C}
     flops = FP64_FLOP.get(precision, {})
     for k in kern:
-        kern[k]["hbm_frac"] = round(kern[k]["GBs"] / peak, 4) if kern[k]["GBs"] else None
         if k in flops and kern[k]["ms_per_launch"] > 0:
             f, u = flops[k]
             tf = f * units[u] / (kern[k]["ms_per_launch"] / 1e3) / 1e12
             kern[k]["fp64_tflops"] = round(tf, 4)
-            kern[k]["fp64_frac"] = round(tf / FP64_PEAK_TFLOPS, 4)
+            kern[k]["fp64_frac"] = round(tf / fpk, 4)
+    if "k_gather" in kern and "k_chem" in kern:
+        # the contract's gather + chemistry row, over the two kernels' time
+        ms = kern["k_gather"]["ms_per_launch"] + kern["k_chem"]["ms_per_launch"] * prof["k_chem"][1] / max(
+            prof["k_gather"][1], 1)
+        sb = survey_bytes("k_gather", C, F, w) + survey_bytes("k_chem", C, F, w)
+        kern["k_gather+k_chem"] = {"ms_per_subcycle": ms, "alg_bytes_per_launch": sb,
+                                   "GBs": sb / (ms / 1e3) / 1e9, "hbm_frac": round(sb / (ms / 1e3) / 1e9 / peak, 4)}
 
     def hbm_line(k):
         return {"kernel": k, "bound": "hbm", "achieved": round(kern[k]["GBs"], 1), "peak": peak, "unit": "GB/s",
                 "frac": kern[k]["hbm_frac"], "peak_source": f"hbm_gbs of {peak_kind}",
-                "traffic": ncu_traffic(k, precision, C), "alg_bytes_per_launch": kern[k]["alg_bytes_per_launch"]}
+                "traffic": ncu_traffic(k, precision, C), "alg_bytes_per_launch": kern[k]["alg_bytes_per_launch"],
+                "bytes_model": "contract (survey) traffic model",
+                "layout_bytes_per_launch": kern[k]["layout_bytes_per_launch"],
+                "layout_frac": round(kern[k]["layout_GBs"] / peak, 4)}
 
     top = max(prof, key=lambda k: prof[k][0])
     mem = [k for k in prof if k != "k_chem"]
     top_mem = max(mem, key=lambda k: prof[k][0])
     if top in flops:
         f, u = flops[top]
-        line = {"kernel": top, "bound": "alu", "achieved": kern[top]["fp64_tflops"],
-                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": kern[top]["fp64_frac"],
-                "peak_source": FP64_PEAK_SOURCE, "traffic": ncu_traffic(top, precision, C),
-                "alg_flop_per_launch": f * units[u], "flop_per_" + u: f, u + "s_per_launch": units[u]}
+        line = {"kernel": top, "bound": "alu", "achieved": kern[top]["fp64_tflops"], "peak": round(fpk, 4),
+                "unit": "TFLOP/s", "frac": kern[top]["fp64_frac"], "peak_source": fsrc,
+                "traffic": ncu_traffic(top, precision, C), "alg_flop_per_launch": f * units[u], "flop_per_" + u: f,
+                u + "s_per_launch": units[u], "alg_bytes_per_launch": kern[top]["alg_bytes_per_launch"],
+                "hbm_frac_of_alg_bytes": kern[top]["hbm_frac"]}
     else:
         line = hbm_line(top)
-    return line, kern, hbm_line(top_mem)
+    sub = None
+    if n_sub and steps and res.get("ms"):
+        bpc = survey_bytes_per_cell_update(C, F, w)
+        gbs = bpc * C * n_sub * steps / (res["ms"] / 1e3) / 1e9
+        sub = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+               "bytes_per_cell_update": round(bpc, 1), "faces_per_cell": round(F / C, 4),
+               "bytes_model": "contract (survey): 720 + 180 fbar mixed, 1176 + 328 fbar FP64",
+               "peak_source": f"hbm_gbs of {peak_kind}"}
+    return line, kern, hbm_line(top_mem), sub
 
 
-def cpu_baseline(mesh, cfg, state, budget_s=12.0):
-    """The FP64 oracle as it stands, single thread, on the same workload:
-    subcycles of the full mesh until ~budget_s of CPU time."""
-    from tests._cases import make_oracle
-    o = make_oracle(mesh, cfg, state)
+def _oracle_rate(mesh, cfg, state, threads, budget_s, max_sub=50):
+    """Cell-updates/s of the FP64 oracle as it stands on the full mesh from
+    the workload's initial state: subcycles until ~budget_s."""
+    from oracle import Oracle, default_config
+    o = Oracle(default_config(**cfg), mesh, threads=threads)
+    o.set_radiation(state["N"], state["fr"])
+    o.set_gas(state["nH"], state["x5"], state["T"])
+    o.set_sources(state["cells"], state["Q"])
     dt = o.max_dt()
     t0 = time.perf_counter()
     n = 0
     while True:
         o.step(dt, 1)
         n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 50:
+        if time.perf_counter() - t0 > budget_s or n >= max_sub:
             break
     sec = time.perf_counter() - t0
-    return {"value": mesh.n_cells * n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} subcycles of the full {mesh.n_cells}-cell workload from its initial state "
-                      f"({sec:.1f} s, FP64, single thread)"}
+    return mesh.n_cells * n / sec, n, sec, o.threads
 
 
-def measure_large(steps, warmup, dev):
-    """Mixed precision on the 2.1M-cell THESAN-like box, 100 subcycles/step."""
+def cpu_baseline(mesh, cfg, state, budget_s=10.0):
+    """The FP64 oracle as it stands on the host cores, on the same workload:
+    all host cores (the OpenMP build of the same source, bitwise the same
+    results) and one thread, each on subcycles of the full mesh until
+    ~budget_s."""
+    from oracle import oracle_threads_available
+    host = os.cpu_count() or 1
+    v1, n1, s1, _ = _oracle_rate(mesh, cfg, state, 1, budget_s)
+    single = {"value": v1, "unit": UNIT, "cores": 1,
+              "sample": f"{n1} subcycles of the full {mesh.n_cells}-cell workload from its initial state "
+                        f"({s1:.1f} s, FP64, one thread)"}
+    if host > 1 and oracle_threads_available():
+        v, n, sec, th = _oracle_rate(mesh, cfg, state, 0, budget_s)
+        return {"value": v, "unit": UNIT, "cores": th, "host_cores": host, "kind": "oracle",
+                "sample": f"{n} subcycles of the full {mesh.n_cells}-cell workload from its initial state "
+                          f"({sec:.1f} s, FP64, {th} threads: the OpenMP build of the oracle source)",
+                "single_thread": single, "speedup_all_cores_over_one": round(v / v1, 2)}
+    return dict(single, kind="oracle", host_cores=host)
+
+
+def field_errors(a, b):
+    """Per field (N, F, x5, T) of a against b: the largest |a - b| over the
+    field's largest |b|, and the largest per-cell relative error
+    |a - b| / |b| over the cells where |b| > 1e-30 max|b|."""
+    out = {}
+    for k in ("N", "F", "x5", "T"):
+        x, y = np.asarray(a[k], dtype=np.float64), np.asarray(b[k], dtype=np.float64)
+        m = float(np.abs(y).max())
+        d = np.abs(x - y)
+        sel = np.abs(y) > 1e-30 * m
+        out[k] = {"max_rel": float(d.max() / m) if m > 0 else float(d.max()),
+                  "cell_rel": float((d[sel] / np.abs(y[sel])).max()) if sel.any() else 0.0}
+    return out
+
+
+def measure_large(steps, warmup, dev, fp64pk, n_sub=100):
+    """Mixed precision on the 2.1M-cell THESAN-like box, 100 subcycles/step;
+    the FP64 path timed on one step of the same subcycles from the same
+    initial state, and the per-field error of the mixed path against it."""
     t0 = time.perf_counter()
     mesh, cfg, state = thesan_like()
     build_s = time.perf_counter() - t0
-    n_sub = 100
     import torch
     from paper_2404_17630_gb300 import RT, make_config
     from paper_2404_17630_gb300 import rt as rtb
     stream = torch.cuda.current_stream(dev)
-    rt = RT(make_config(precision="mixed", gather_sum=1, **cfg), mesh, stream=stream)
-    rt.set_gas(state["nH"], state["x5"], state["T"])
-    rt.set_radiation(state["N"], state["fr"] * cfg["c_red"])
-    rt.set_sources(state["cells"], state["Q"])
+
+    def fresh(prec):
+        r = RT(make_config(precision=prec, gather_sum=1, **cfg), mesh, stream=stream)
+        r.set_gas(state["nH"], state["x5"], state["T"])
+        r.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+        r.set_sources(state["cells"], state["Q"])
+        return r
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_step(r, dt):
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        r.step(dt, n_sub)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1)
+
+    # first step of each precision from the initial state: the error of the
+    # mixed path against the FP64 path, and the FP64 path's time
+    fields, first_ms = {}, {}
+    for prec in ("fp64", "mixed"):
+        r2 = fresh(prec)
+        dt = r2.max_dt() * n_sub
+        r2.step(dt, n_sub)   # builds the step graph outside the timed step
+        r2.sync()
+        r2.set_gas(state["nH"], state["x5"], state["T"])     # back to the initial state
+        r2.set_radiation(state["N"], state["fr"] * cfg["c_red"])
+        first_ms[prec] = timed_step(r2, dt)
+        r2.sync()
+        fields[prec] = r2.fields()
+        del r2
+    # mixed: steady-state steps
+    rt = fresh("mixed")
     dt = rt.max_dt() * n_sub
     for _ in range(warmup):
         rt.step(dt, n_sub)
     rt.sync()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     for _ in range(steps):
@@ -459,32 +597,28 @@ def measure_large(steps, warmup, dev):
     rtb.rt_profile_enable(rt.ctx, True)
     rt.step(dt, n_sub)
     prof = rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, False)
     rt.sync()
     C, F, _ = rt.mesh_info()
     res = dict(ms=ms, C=C, F=F, prof=prof)
     peaks, kind = measured_peaks()
     f = rt.fields()
-    rf, kern, rf_mem = roofline(res, "mixed", peaks, kind, attempts=float(f["nsub"].sum()))
-    # per-field error of the mixed path against the FP64 path: one step of
-    # n_sub subcycles of each from the initial state
-    fields = {}
-    for prec in ("mixed", "fp64"):
-        r2 = RT(make_config(precision=prec, gather_sum=1, **cfg), mesh, stream=stream)
-        r2.set_gas(state["nH"], state["x5"], state["T"])
-        r2.set_radiation(state["N"], state["fr"] * cfg["c_red"])
-        r2.set_sources(state["cells"], state["Q"])
-        r2.step(dt, n_sub)
-        r2.sync()
-        fields[prec] = r2.fields()
-        del r2
-    a, b = fields["mixed"], fields["fp64"]
-    err = {k: float(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300)) for k in ("N", "F", "x5", "T")}
+    rf, kern, rf_mem, rf_sub = roofline(res, "mixed", peaks, kind, fp64pk, attempts=float(f["nsub"].sum()),
+                                        n_sub=n_sub, steps=steps)
+    v_mixed = C * n_sub * steps / (ms / 1e3)
+    v64_first = C * n_sub / (first_ms["fp64"] / 1e3)
+    v_mixed_first = C * n_sub / (first_ms["mixed"] / 1e3)
     return {"workload": f"THESAN-like voronoi 128^3 ({C} cells, {F} faces), GRF n_H, 4096 peak sources, "
                         f"c_red 0.2c, {n_sub} subcycles/step, mixed",
-            "mixed_vs_fp64_after_one_step": {"metric": "max|mixed - fp64| / max|fp64| per field", **err},
-            "value": C * n_sub * steps / (ms / 1e3),
-            "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "roofline": rf,
-            "roofline_memory_kernel": rf_mem,
+            "mixed_vs_fp64_after_one_step": {"metric": "per field: max|mixed - fp64| / max|fp64| (max_rel) and "
+                                                       "max over cells of |mixed - fp64| / |fp64| where "
+                                                       "|fp64| > 1e-30 max|fp64| (cell_rel)",
+                                             **field_errors(fields["mixed"], fields["fp64"])},
+            "value": v_mixed, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+            "fp64_first_step": {"value": v64_first, "ms": first_ms["fp64"]},
+            "mixed_first_step": {"value": v_mixed_first, "ms": first_ms["mixed"]},
+            "speedup_mixed_over_fp64_first_step": round(v_mixed_first / v64_first, 2),
+            "roofline": rf, "roofline_memory_kernel": rf_mem, "roofline_subcycle": rf_sub,
             "kernels": kern, "mesh_build_s": round(build_s, 1), "x_HII_mean": float(f["x5"][1].mean())}
 
 
@@ -600,7 +734,7 @@ def measure_timebins(dev, n_steps=8):
             "ms_masked": ms_masked, "ms_all_active": ms_all, "time_ratio": ms_masked / ms_all}
 
 
-def measure_config5(dev, n=256, n_sub=200, adj_sub=20, k=20):
+def measure_config5(dev, fp64pk, n=256, n_sub=200, adj_sub=20, k=20, adjoint=True):
     """The large box: Voronoi mesh of a 256^3 jittered lattice (16.8M cells,
     7.16 Mpc, exp(GRF) density as the THESAN-like box, 32768 peak sources,
     c_red = 0.2 c).  Mixed forward of one step of n_sub subcycles (after one
@@ -611,6 +745,7 @@ def measure_config5(dev, n=256, n_sub=200, adj_sub=20, k=20):
     import torch
     import synth
     from paper_2404_17630_gb300 import RT, make_config
+    from paper_2404_17630_gb300 import rt as rtb
     t0 = time.perf_counter()
     mesh, cfg, state = synth.thesan_like(n, 10, 32768, 7160.0, 256)
     build_s = time.perf_counter() - t0
@@ -634,9 +769,22 @@ def measure_config5(dev, n=256, n_sub=200, adj_sub=20, k=20):
     ms = ev0.elapsed_time(ev1)
     rt.sync()
     free1, _ = torch.cuda.mem_get_info(dev)
+    rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, True)
+    rt.step(dt, n_sub)
+    prof = rtb.rt_profile_read(rt.ctx, reset=True)
+    rtb.rt_profile_enable(rt.ctx, False)
+    rt.sync()
+    Cm, Fm, _ = rt.mesh_info()
+    peaks, kind = measured_peaks()
+    rf, kern, rf_mem, rf_sub = roofline(dict(ms=ms, C=Cm, F=Fm, prof=prof), "mixed", peaks, kind, fp64pk,
+                                        attempts=float(rt.fields()["nsub"].sum()), n_sub=n_sub, steps=1)
     out["forward_mixed"] = {"value": C * n_sub / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "n_sub": n_sub,
-                            "device_GB_in_use": round((free0 - free1) / 1e9, 1)}
+                            "device_GB_in_use": round((free0 - free1) / 1e9, 1), "roofline": rf,
+                            "roofline_memory_kernel": rf_mem, "roofline_subcycle": rf_sub, "kernels": kern}
     del rt
+    if not adjoint:
+        return out
     torch.cuda.synchronize(dev)
     rt = RT(make_config(precision="fp64", **dict(cfg, chem_mode=2)), mesh, stream=stream)
     rt.set_gas(state["nH"], state["x5"], state["T"])
@@ -713,8 +861,10 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 2.1M-cell THESAN-like run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode run")
     ap.add_argument("--no-hii", action="store_true", help="skip the HII-region and time-step-hierarchy runs")
-    ap.add_argument("--config5", action="store_true",
-                    help="also run the 16.8M-cell box (forward and reverse mode; minutes, ~170 GB of device memory)")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the 16.8M-cell box (mixed forward and a 20-subcycle FP64 reverse mode; ~190 GB of "
+                         "device memory)")
+    ap.add_argument("--config5-no-adjoint", action="store_true", help="the 16.8M-cell box without the reverse mode")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -735,6 +885,7 @@ def main():
 
     mesh, cfg, state = workload()
     peaks, peak_kind = measured_peaks()
+    fp64pk = fp64_peak(torch.cuda.current_stream(dev))
     clocks = ClockSampler(local)
     res = run_gpu("mixed", mesh, cfg, state, args.steps, args.warmup, rank, world, dev, dist, clocks)
     cl = clocks.summary()
@@ -743,9 +894,11 @@ def main():
         r64 = run_gpu("fp64", mesh, cfg, state, max(2, args.steps // 5), 1, rank, world, dev, dist)
         fp64 = {"value": replica_value(world, r64["C"], N_SUB, max(2, args.steps // 5), r64["ms"]),
                 "ms_per_step": r64["ms"] / max(2, args.steps // 5), "dtype": "f64"}
-        rf64, k64, rf64m = roofline(r64, "fp64", peaks, peak_kind, attempts=r64.get("attempts"))
+        rf64, k64, rf64m, rf64s = roofline(r64, "fp64", peaks, peak_kind, fp64pk, attempts=r64.get("attempts"),
+                                           n_sub=N_SUB, steps=max(2, args.steps // 5))
         fp64["roofline"] = rf64
         fp64["roofline_memory_kernel"] = rf64m
+        fp64["roofline_subcycle"] = rf64s
         fp64["kernels"] = k64
     fp64sum = None
     if not args.no_fp64:
@@ -754,16 +907,17 @@ def main():
         fp64sum = {"value": replica_value(world, r["C"], N_SUB, n64s, r["ms"]), "ms_per_step": r["ms"] / n64s,
                    "note": "mixed precision with each FP32 face flux widened and summed in FP64 (gather_sum=0)"}
     e2e = None if args.no_e2e else e2e_measure("mixed", mesh, cfg, state, max(2, args.steps // 2), args.warmup, dev)
-    large = None if args.no_large else measure_large(3, 1, dev)
+    large = None if args.no_large else measure_large(3, 1, dev, fp64pk)
     adjoint = None if args.no_adjoint else measure_adjoint(dev)
     hii = None if args.no_hii else measure_hii(3, 1, dev)
-    config5 = measure_config5(dev) if args.config5 else None
     timebins = None if args.no_hii else measure_timebins(dev)
+    config5 = None if args.no_config5 else measure_config5(dev, fp64pk, adjoint=not args.config5_no_adjoint)
     if rank != 0:
         return
     C, F = res["C"], res["F"]
     value = replica_value(world, C, N_SUB, args.steps, res["ms"])
-    rf, kern, rf_mem = roofline(res, "mixed", peaks, peak_kind, attempts=res.get("attempts"))
+    rf, kern, rf_mem, rf_sub = roofline(res, "mixed", peaks, peak_kind, fp64pk, attempts=res.get("attempts"),
+                                        n_sub=N_SUB, steps=args.steps)
     cpu = None if args.no_cpu else cpu_baseline(mesh, cfg, state)
     ws = (C * 3 * (32 + 16 + 48) + F * (64 + 48) + C * 200)
     out = {
@@ -774,9 +928,10 @@ def main():
                                f"{F / C:.3f} faces/cell), lognormal n_H, 16 sources, 3 bins, {N_SUB} subcycles/step",
                    "cells": C, "faces": F, "n_sub": N_SUB,
                    "precision": "mixed (FP32 sweep; FP64 state, update and chemistry; face-flux sums as compensated FP32 pairs)",
-                   "l2": f"working set ~{ws / 1e6:.0f} MB > L2 129 MB (no flush needed)",
+                   "l2": f"working set ~{ws / 1e6:.0f} MB > L2 129 MB; L2 also flushed once before the timed region",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": rf, "roofline_memory_kernel": rf_mem, "kernels": kern,
+        "roofline": rf, "roofline_memory_kernel": rf_mem, "roofline_subcycle": rf_sub, "kernels": kern,
+        "fp64_peak": {"tflops": round(fp64pk[0], 4), "source": fp64pk[1]},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "mixed_fp64_sums": fp64sum,
@@ -789,13 +944,19 @@ def main():
 
 
 def reference_arm(args, rank):
-    """The FP64 oracle timed on the host cores, on the same workload: each
-    step is a bounded sample (one subcycle of the full mesh)."""
+    """The FP64 oracle as it stands, timed on the host cores (the OpenMP
+    build of its source on all of them, bitwise the single-threaded results),
+    on the same workload: each step is a bounded sample (one subcycle of the
+    full mesh)."""
     if rank != 0:
         return
     mesh, cfg, state = workload()
-    from tests._cases import make_oracle
-    o = make_oracle(mesh, cfg, state)
+    from oracle import Oracle, default_config, oracle_threads_available
+    threads = 0 if oracle_threads_available() else 1
+    o = Oracle(default_config(**cfg), mesh, threads=threads)
+    o.set_radiation(state["N"], state["fr"])
+    o.set_gas(state["nH"], state["x5"], state["T"])
+    o.set_sources(state["cells"], state["Q"])
     dt = o.max_dt()
     for _ in range(args.warmup):
         o.step(dt, 1)
@@ -809,8 +970,10 @@ def reference_arm(args, rank):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"voronoi {LATTICE}^3 jittered lattice ({mesh.n_cells} cells), one subcycle per step",
                       "cells": mesh.n_cells, "n_sub": 1},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} timed subcycles after {args.warmup} warm-up subcycles"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.threads, "host_cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"{args.steps} timed subcycles of the full mesh after {args.warmup} warm-up "
+                                      f"subcycles, {o.threads} threads"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -232,6 +232,20 @@ rt_status rt_launch_count(rt_ctx *ctx, int64_t *out);
  * range. */
 rt_status rt_selftest_wait_timeout(rt_ctx *ctx, uint32_t polls);
 
+/* Measured FP64 peak of the current device, the denominator of the FP64
+ * rooflines (the FP64 sweep and the chemistry are bound by the FP64 unit).
+ * Not a step of the method: the measurement that the roofline needs.  One
+ * kernel of 8 independent fused multiply-add chains per thread, 8 blocks of
+ * 256 threads per SM, `iters` iterations (1..2^20), timed with CUDA events on
+ * `stream` (NULL: the default stream) after one warm-up launch; the best of
+ * `reps` (1..100) launches.  *tflops = 2 x FMAs / time / 1e12; *ms_best (may
+ * be NULL) the best launch in milliseconds.  Allocates (and frees) one small
+ * output buffer; synchronises on its events.  RT_INVALID_ARG for arguments
+ * out of range, RT_CUDA for a failed CUDA call; message from
+ * rt_fp64_peak_last_error(). */
+rt_status rt_fp64_peak(void *stream, int iters, int reps, double *tflops, double *ms_best);
+const char *rt_fp64_peak_last_error(void);
+
 /* Allocation-free gradients, for callers that cannot allocate device memory
  * (a host framework that owns all device memory through its own pool, a
  * real-time loop that must not allocate, a plug-in that only receives device
@@ -246,16 +260,23 @@ rt_status rt_selftest_wait_timeout(rt_ctx *ctx, uint32_t polls);
  *   N[B*C], F_red[3*B*C]: photon densities and reduced fluxes F / c_red;
  *   G[C*B*12] out, layout as rt_stage_gradients; *bad_cell (device int) is
  *   set to 1 if a cell's least-squares matrix is singular, else 0.
- * The arrays must describe a valid mesh (ids in range); they are not checked.
+ * Every array must be device memory of the current device (or managed
+ * memory); anything else, device memory of another GPU included, gets
+ * RT_INVALID_ARG before anything is enqueued.  The arrays must describe a
+ * valid mesh (ids in range); they are not checked.
  * Its only scratch is a static device array of 6 doubles per cell for at
  * most 262144 cells (12.6 MB held on every GPU that loads the library until
  * the process exits); larger meshes get RT_INVALID_ARG.  Nothing is
  * allocated.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls on a device share the array: work enqueued by calls
- * that may overlap on the GPU (other streams, unordered host threads) races.
- * Asynchronous on stream; host-side errors are returned as status codes,
- * with a message from rt_noalloc_last_error(). */
+ * address (cudaGetSymbolAddress) and caches it with the device's current
+ * context; a call made after that context was replaced (cudaDeviceReset)
+ * looks it up again.  Make the first call on a device, and the first after
+ * a reset, before any stream capture.  All calls on a device share the
+ * array: work enqueued by calls that may overlap on the GPU (other streams,
+ * unordered host threads) races.  Asynchronous on stream; host-side errors
+ * and failed launches of its own kernels are returned as status codes, with
+ * a message from rt_noalloc_last_error(); an error the caller left pending
+ * in the CUDA runtime is neither reported nor cleared. */
 rt_status rt_gradients_noalloc(const rt_cells *cells, const rt_faces *faces, const int32_t *cell_off,
                                const int32_t *cell_faces, int n_bins, int order, int limiter, double lim_eps,
                                double box, const double *N, const double *F_red, double *G, int *bad_cell,

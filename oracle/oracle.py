@@ -9,7 +9,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB = None
+_LIBS = {}
 _LOCK = threading.Lock()
 
 ST_OK, ST_CFL, ST_CHEM, ST_NONFINITE = 0, 3, 4, 5
@@ -71,22 +71,46 @@ def default_config(**kw) -> OracleConfig:
     return c
 
 
-def build_oracle_lib(force: bool = False) -> str:
+_FLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def _build_one(out, extra, force):
     src = os.path.join(_HERE, "rt_oracle.c")
-    out = os.path.join(_HERE, "_rt_oracle.so")
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", src, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *_FLAGS, *extra, src, "-o", tmp, "-lm"])
         os.replace(tmp, out)
     return out
 
 
-def _lib():
-    global _LIB
+def build_oracle_lib(force: bool = False, omp: bool = False) -> str:
+    """The single-threaded oracle library; with omp=True the same source
+    built with -fopenmp (its per-cell and per-face loops on all host cores,
+    bitwise the same results).  Building the single-threaded one also tries
+    the OpenMP one, which is optional: without OpenMP support only
+    oracle_threads_available() is False."""
+    if omp:
+        return _build_one(os.path.join(_HERE, "_rt_oracle_omp.so"), ["-fopenmp"], force)
+    out = _build_one(os.path.join(_HERE, "_rt_oracle.so"), [], force)
+    try:
+        build_oracle_lib(force, omp=True)
+    except (OSError, subprocess.CalledProcessError):
+        pass
+    return out
+
+
+def oracle_threads_available() -> bool:
+    try:
+        _lib(True)
+        return True
+    except (OSError, subprocess.CalledProcessError):
+        return False
+
+
+def _lib(omp: bool = False):
     with _LOCK:
-        if _LIB is None:
-            lib = ctypes.CDLL(build_oracle_lib())
+        if omp not in _LIBS:
+            lib = ctypes.CDLL(build_oracle_lib(omp=omp))
             vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
             ip32 = ctypes.POINTER(ctypes.c_int32)
             ip64 = ctypes.POINTER(ctypes.c_int64)
@@ -120,8 +144,14 @@ def _lib():
             lib.orc_adjoint.restype = ctypes.c_int
             lib.orc_cooling.argtypes = [ctypes.c_double] * 7
             lib.orc_cooling.restype = ctypes.c_double
-            _LIB = lib
-    return _LIB
+            lib.orc_rates.argtypes = [ctypes.c_double, dp]
+            lib.orc_rates.restype = None
+            lib.orc_cooling_coeffs.argtypes = [ctypes.c_double, dp]
+            lib.orc_cooling_coeffs.restype = None
+            lib.orc_threads.argtypes = [ctypes.c_int]
+            lib.orc_threads.restype = ctypes.c_int
+            _LIBS[omp] = lib
+    return _LIBS[omp]
 
 
 def _d(a):
@@ -136,19 +166,43 @@ def rate_probe(name: str, *args) -> float:
     return getattr(_lib(), "orc_" + name)(*[float(a) for a in args])
 
 
+def rates(T: float) -> dict:
+    """The oracle's rate coefficients at T (cm^3/s)."""
+    out = np.empty(6)
+    _lib().orc_rates(float(T), _d(out))
+    return dict(zip(("alpha_HII", "alpha_HeII", "alpha_HeIII", "beta_HI", "beta_HeI", "beta_HeII"), out))
+
+
+COOLING_TERMS = ("ce_HI", "ce_HeII", "ci_HI", "ci_HeI", "ci_HeII", "rc_HII", "rc_HeII", "rc_HeIII", "diel_HeII",
+                 "ff")
+
+
+def cooling_coeffs(T: float) -> dict:
+    """The oracle's cooling coefficients K_t(T) (erg cm^3/s), Lambda =
+    n_e sum_t K_t n_(t): collisional excitation of HI and HeII, collisional
+    ionisation of HI, HeI, HeII, recombination to HI, HeI, HeII, dielectronic
+    recombination of HeII, and free-free (on n_HII + n_HeII + 4 n_HeIII)."""
+    out = np.empty(10)
+    _lib().orc_cooling_coeffs(float(T), _d(out))
+    return dict(zip(COOLING_TERMS, out))
+
+
 class Oracle:
     """One oracle instance over a fixed mesh.  Arrays: N [B, C], fr [B, 3, C]
     (reduced flux F/c_red), x5 [5, C] = (x_HI, x_HII, y_HeI, y_HeII, y_HeIII),
     T [C], sources (cell [n], Q [n, B] photons/s)."""
 
-    def __init__(self, cfg: OracleConfig, mesh):
+    def __init__(self, cfg: OracleConfig, mesh, threads: int = 1):
+        """threads > 1 (or 0: all host cores) runs the per-cell and per-face
+        loops of the OpenMP build, bitwise the results of threads = 1."""
         self.cfg = cfg
         self.B = cfg.n_bins
         self.C, self.F = mesh.n_cells, mesh.n_faces
         self._keep = [_f64(getattr(mesh, k)) for k in ("volume", "cx", "cy", "cz")]
         lr = [np.ascontiguousarray(mesh.left, dtype=np.int32), np.ascontiguousarray(mesh.right, dtype=np.int32)]
         fk = [_f64(getattr(mesh, k)) for k in ("area", "nx", "ny", "nz", "fx", "fy", "fz")]
-        lib = _lib()
+        lib = _lib(threads != 1)
+        self.threads = lib.orc_threads(int(threads) if threads > 1 else os.cpu_count() or 1) if threads != 1 else 1
         ip32 = ctypes.POINTER(ctypes.c_int32)
         self._h = lib.orc_create(ctypes.byref(cfg), self.C, self.F, *[_d(a) for a in self._keep],
                                  lr[0].ctypes.data_as(ip32), lr[1].ctypes.data_as(ip32), *[_d(a) for a in fk])

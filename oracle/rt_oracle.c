@@ -30,13 +30,25 @@
  * the Cartesian central-difference gradient and hand-expanded two-cell fluxes
  * are checked by tests/test_oracle_pins.py, as is the energy budget of
  * photoheating (thermal energy gained = heat per ionisation x ionisations).
- * The cooling function (the KWH96 rates) is "parity unpinned" beyond
- * conservation, equilibrium and the alpha_B(1e4 K) value: the paper prints
- * no profiles for it.
+ * The rate fits are pinned by tests/test_oracle_rate_pins.py to independent
+ * atomic data: activation temperatures (NIST energies), cooling per
+ * collisional ionisation and per dielectronic recombination, case-B tables,
+ * an independent collisional-ionisation fit and the bremsstrahlung Gaunt
+ * range.  "Parity unpinned": the prefactors of collisional-excitation and
+ * radiative-recombination cooling, and the shape of KWH96's high-temperature
+ * factor 1 / (1 + (T / 1e5)^(1/2)).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
- * arithmetic is the literal sequence written here).
+ * arithmetic is the literal sequence written here).  The same source is also
+ * built with -fopenmp: the pragmas below then run the loops whose iterations
+ * each write only their own cell or face (geometry, gradients, face fluxes,
+ * flux application, sources, chemistry) on all host cores.  No floating-point
+ * value is reduced across iterations, so the results are bitwise those of
+ * the single-threaded build; without -fopenmp the pragmas are ignored.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -133,6 +145,8 @@ static void sep(const orc_t *o, int64_t i, int64_t j, double d[3]) {
 static int64_t other_cell(const orc_t *o, int64_t f, int64_t i) { return o->left[f] == i ? o->right[f] : o->left[f]; }
 
 static int geometry(orc_t *o) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t i = 0; i < o->C; ++i) {
     double m[9] = {0};
     for (int64_t k = o->off[i]; k < o->off[i + 1]; ++k) {
@@ -144,9 +158,9 @@ static int geometry(orc_t *o) {
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) m[3 * a + b] += o->area[f] * n[a] * n[b];
     }
-    if (invert3(m, o->minv + 9 * i)) return 2;
+    if (invert3(m, o->minv + 9 * i)) bad = 1;
   }
-  return 0;
+  return bad ? 2 : 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -173,6 +187,7 @@ static double *Gp(const orc_t *o, int64_t i, int b, int q) { return o->G + (((i 
 /* ------------------------------------------------------------------------ */
 static void gradients(orc_t *o) {
   const int B = o->cfg.n_bins;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < o->C; ++i) {
     for (int b = 0; b < B; ++b) {
       for (int q = 0; q < 4; ++q) {
@@ -284,6 +299,7 @@ static int face_active(const orc_t *o, int64_t f) { return cell_active(o, o->lef
 
 static void face_fluxes(orc_t *o) {
   const int B = o->cfg.n_bins;
+#pragma omp parallel for schedule(static)
   for (int64_t f = 0; f < o->F; ++f) {
     double n[3] = {o->nx[f], o->ny[f], o->nz[f]};
     if (!face_active(o, f)) {
@@ -312,6 +328,7 @@ static void face_fluxes(orc_t *o) {
 static void apply_fluxes(orc_t *o, double dt) {
   const int B = o->cfg.n_bins;
   const double lam = o->cfg.c_red * dt / o->cfg.unit_length_cm;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < o->C; ++i) {
     for (int b = 0; b < B; ++b) {
       double acc[4] = {0, 0, 0, 0};
@@ -586,6 +603,7 @@ static int chemistry_cell(orc_t *o, int64_t i, double dt_sub) {
 /* Source term S of Eq. (E): photons emitted into the host cell over dt. */
 static void inject_sources(orc_t *o, double dt) {
   const double lu = o->cfg.unit_length_cm;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < o->C; ++i)
     for (int b = 0; b < o->cfg.n_bins && cell_active(o, i); ++b) {
       double S = o->src[b * o->C + i];
@@ -600,13 +618,16 @@ static int thermochemistry(orc_t *o, double dt) {
     for (int64_t i = 0; i < o->C; ++i) o->nsub[i] = 0;
     return st;
   }
+  /* the only status a cell reports is ST_CHEM: the largest over cells is the
+   * last nonzero one of the serial loop */
+#pragma omp parallel for schedule(dynamic, 256) reduction(max : st)
   for (int64_t i = 0; i < o->C; ++i) {
     if (!cell_active(o, i)) {   /* passive cells are not integrated this step */
       o->nsub[i] = 0;
       continue;
     }
     int s = chemistry_cell(o, i, dt);
-    if (s) st = s;
+    if (s > st) st = s;
   }
   return st;
 }
@@ -753,6 +774,7 @@ int orc_thermochemistry(orc_t *o, double dt) { return thermochemistry(o, dt); }
  * eta * min_i V_i^(1/3) / c_red, in seconds. */
 double orc_max_dt(const orc_t *o) {
   double m = INFINITY;
+#pragma omp parallel for schedule(static) reduction(min : m)
   for (int64_t i = 0; i < o->C; ++i) {
     double dx = cbrt(o->vol[i]) * o->cfg.unit_length_cm;
     if (dx < m) m = dx;
@@ -814,11 +836,35 @@ int orc_step(orc_t *o, double dt, int n_sub) {
   return st;
 }
 
+/* Host threads of the loops above: n > 0 sets them (OpenMP build only);
+ * returns the number in use (1 in the single-threaded build). */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* Rate-coefficient probes for the pins (cm^3/s). */
 double orc_alphaB_HII(double T) { return alphaB_HII(T); }
 double orc_alphaB_HeII(double T) { return alphaB_HeII(T); }
 double orc_alphaB_HeIII(double T) { return alphaB_HeIII(T); }
 double orc_beta_HI(double T) { return beta_HI(T); }
+/* out[6] = alpha_B(HII), alpha(HeII) (case B + dielectronic), alpha_B(HeIII),
+ * beta(HI), beta(HeI), beta(HeII) in cm^3/s */
+void orc_rates(double T, double *out) {
+  out[0] = alphaB_HII(T); out[1] = alphaB_HeII(T); out[2] = alphaB_HeIII(T);
+  out[3] = beta_HI(T); out[4] = beta_HeI(T); out[5] = beta_HeII(T);
+}
+/* K[10]: the cooling rate's coefficients, Lambda = n_e sum_t K_t n_(t)
+ * (see cooling_coeffs), erg cm^3 s^-1 */
+void orc_cooling_coeffs(double T, double *K) {
+  double dK[10];
+  cooling_coeffs(T, K, dK);
+}
 double orc_cooling(double T, double ne, double nHI, double nHII, double nHeI, double nHeII, double nHeIII) {
   return cooling(T, ne, nHI, nHII, nHeI, nHeII, nHeIII);
 }

@@ -9,10 +9,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libm1rt.so")
-SOURCES = ["rt_api.cu", "rt_noalloc.cu", "rt_selftest.cu"]
+SOURCES = ["rt_api.cu", "rt_noalloc.cu", "rt_selftest.cu", "rt_peak.cu"]
 HEADERS = ["rt_common.cuh", "rt_chem.cuh", "rt_kernels.cuh", "rt_ctx.h", "rt_adjoint.cuh"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
-              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
+              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr", "-Xptxas", "-v", "--threads", "4"]
 
 
 def nvcc() -> str:

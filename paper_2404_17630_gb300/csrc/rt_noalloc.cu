@@ -15,10 +15,16 @@
 // overwrites the entries of its cells before reading them, so nothing needs
 // clearing, but calls that overlap on the GPU (different streams, or host
 // threads without ordering) race on it.
+//
+// The array's device address is looked up once per device context and
+// cached; when the device's current context changes (a cudaDeviceReset tears
+// the primary context down and the next runtime call creates a new one), the
+// next call looks it up again.
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rt.h"
@@ -34,6 +40,32 @@ __device__ __align__(256) double g_noalloc_minv[6 * kNoallocMaxCells];
 
 std::mutex g_mu;
 double* g_minv_ptr[kMaxDevices] = {};
+void* g_minv_ctx[kMaxDevices] = {};   // the context each cached address belongs to
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library does
+// not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return (CtxGetCurrentFn)p;
+  }();
+  return fn;
+}
+
+// Kernel launch that returns this launch's own status (a triple-chevron
+// launch only leaves it in the thread's last-error slot, where an error the
+// caller left pending is indistinguishable from it).
+template <class T> struct ident { using type = T; };
+template <class... KA>
+cudaError_t launch(void (*k)(KA...), dim3 grid, dim3 block, cudaStream_t s, typename ident<KA>::type... args) {
+  void* p[] = {(void*)&args...};
+  return cudaLaunchKernel((const void*)k, grid, block, p, 0, s);
+}
 
 thread_local char g_err[256];
 
@@ -153,13 +185,17 @@ __global__ void k_noalloc_grad(int C, int B, double box, int limiter, double lim
   }
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device `dev`, or managed memory.  Device memory
+// of another GPU is refused: the kernels run on `dev` and would otherwise read
+// another GPU's memory (a fault, or peer traffic where peer access is on).
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -179,19 +215,25 @@ rt_status rt_gradients_noalloc(const rt_cells* cells, const rt_faces* faces, con
   if (C > kNoallocMaxCells)
     return set_err(RT_INVALID_ARG, "rt_gradients_noalloc: more than 262144 cells (size of its static scratch)");
   if (F > (1LL << 29)) return set_err(RT_INVALID_ARG, "rt_gradients_noalloc: too many faces");
-  const void* dev_ptrs[] = {cells->cx, cells->cy, cells->cz, faces->left, faces->right, faces->area, faces->fx,
-                            faces->fy, faces->fz, cell_off, cell_faces, N, F_red, G, bad_cell};
-  for (const void* p : dev_ptrs)
-    if (!p || !on_device(p)) return set_err(RT_INVALID_ARG, "rt_gradients_noalloc: every array must be device memory");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return set_err(RT_CUDA, "rt_gradients_noalloc: no current device");
   }
+  const void* dev_ptrs[] = {cells->cx, cells->cy, cells->cz, faces->left, faces->right, faces->area, faces->fx,
+                            faces->fy, faces->fz, cell_off, cell_faces, N, F_red, G, bad_cell};
+  for (const void* p : dev_ptrs)
+    if (!p || !on_device(p, dev))
+      return set_err(RT_INVALID_ARG, "rt_gradients_noalloc: every array must be device memory of the current device");
   double* minv = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_minv_ptr[dev]) {   // once per device, with that device current
+    CUcontext cur = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
+    if (!g_minv_ptr[dev] || (cur && cur != (CUcontext)g_minv_ctx[dev])) {
+      // first call on this device, or its context was replaced: look the
+      // address up with this device current
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_minv);
       if (e != cudaSuccess || !p) {
@@ -199,6 +241,7 @@ rt_status rt_gradients_noalloc(const rt_cells* cells, const rt_faces* faces, con
         return set_err(RT_CUDA, "rt_gradients_noalloc: cudaGetSymbolAddress failed");
       }
       g_minv_ptr[dev] = (double*)p;
+      g_minv_ctx[dev] = (void*)cur;
     }
     minv = g_minv_ptr[dev];
   }
@@ -217,15 +260,18 @@ rt_status rt_gradients_noalloc(const rt_cells* cells, const rt_faces* faces, con
     return set_err(RT_CUDA, "rt_gradients_noalloc: memset failed");
   }
   const int t = 256;
-  k_noalloc_minv<<<(Ci + t - 1) / t, t, 0, s>>>(Ci, box, cell_off, cell_faces, faces->left, faces->right, cells->cx,
-                                                cells->cy, cells->cz, faces->area, minv, bad_cell);
-  const long long n = (long long)C * n_bins;
-  k_noalloc_grad<<<(int)((n + t - 1) / t), t, 0, s>>>(Ci, n_bins, box, limiter, lim_eps * lim_eps, cell_off,
-                                                     cell_faces, faces->left, faces->right, cells->cx, cells->cy,
-                                                     cells->cz, faces->area, faces->fx, faces->fy, faces->fz, minv,
-                                                     N, F_red, G);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return set_err(RT_CUDA, cudaGetErrorString(e));
+  cudaError_t e = launch(k_noalloc_minv, dim3((Ci + t - 1) / t), dim3(t), s, Ci, box, cell_off, cell_faces,
+                         faces->left, faces->right, cells->cx, cells->cy, cells->cz, faces->area, minv, bad_cell);
+  if (e == cudaSuccess) {
+    const long long n = (long long)C * n_bins;
+    e = launch(k_noalloc_grad, dim3((unsigned)((n + t - 1) / t)), dim3(t), s, Ci, n_bins, box, limiter,
+               lim_eps * lim_eps, cell_off, cell_faces, faces->left, faces->right, cells->cx, cells->cy, cells->cz,
+               faces->area, faces->fx, faces->fy, faces->fz, (const double*)minv, N, F_red, G);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // the failed launch's own error
+    return set_err(RT_CUDA, cudaGetErrorString(e));
+  }
   return RT_OK;
 }
 

@@ -138,6 +138,10 @@ def load():
             lib.rt_gradients_noalloc.argtypes = [ctypes.POINTER(rt_cells), ctypes.POINTER(rt_faces), vp, vp, i32, i32,
                                                  i32, dbl, dbl, vp, vp, vp, vp, vp]
             lib.rt_gradients_noalloc.restype = ctypes.c_int
+            lib.rt_fp64_peak.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+            lib.rt_fp64_peak.restype = ctypes.c_int
+            lib.rt_fp64_peak_last_error.argtypes = []
+            lib.rt_fp64_peak_last_error.restype = ctypes.c_char_p
             lib.rt_noalloc_last_error.argtypes = []
             lib.rt_noalloc_last_error.restype = ctypes.c_char_p
             lib.rt_last_error.argtypes = [vp]
@@ -318,6 +322,21 @@ def rt_gradients_noalloc(cells: rt_cells, faces: rt_faces, cell_off, cell_faces,
     if st != RT_OK:
         raise RTError(st, (lib.rt_noalloc_last_error() or b"").decode())
     return st
+
+
+def rt_fp64_peak(stream=None, iters=4096, reps=5):
+    """Measured FP64 peak of the current device (see include/rt.h):
+    returns (TFLOP/s, best launch in ms)."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib.rt_fp64_peak(_stream_handle(stream), int(iters), int(reps), ctypes.byref(tf), ctypes.byref(ms))
+    if st != RT_OK:
+        raise RTError(st, (lib.rt_fp64_peak_last_error() or b"").decode())
+    return tf.value, ms.value
+
+
+def rt_fp64_peak_last_error() -> str:
+    return (load().rt_fp64_peak_last_error() or b"").decode()
 
 
 def rt_noalloc_last_error() -> str:
