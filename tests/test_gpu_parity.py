@@ -491,3 +491,15 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert rt.sync() == 0
     compare_state(rt, o, 1e-4)
 
+
+
+def test_fp64_peak_measurement():
+    """rt_fp64_peak: a DFMA stream over every SM; GB300's FP64 unit gives
+    about 1.2 TFLOP/s, and the measurement is repeatable to a few percent."""
+    from paper_2404_17630_gb300 import rt as rtb
+    tf1, ms1 = rtb.rt_fp64_peak(None, 2048, 3)
+    tf2, _ = rtb.rt_fp64_peak(None, 2048, 3)
+    assert 0.2 < tf1 < 5.0 and ms1 > 0
+    assert abs(tf1 / tf2 - 1) < 0.1
+    with pytest.raises(rtb.RTError):
+        rtb.rt_fp64_peak(None, 0, 3)
