@@ -150,6 +150,7 @@ rt_status check_config(const rt_config* c) {
   if (c->gather_sum < 0 || c->gather_sum > 1) return fail(nullptr, RT_INVALID_ARG, "gather_sum must be 0 or 1");
   if (c->splitting < 0 || c->splitting > 1) return fail(nullptr, RT_INVALID_ARG, "splitting must be 0 or 1");
   if (c->time_order < 1 || c->time_order > 2) return fail(nullptr, RT_INVALID_ARG, "time_order must be 1 or 2");
+  if (c->split_kernels < 0 || c->split_kernels > 1) return fail(nullptr, RT_INVALID_ARG, "split_kernels must be 0 or 1");
   return RT_OK;
 }
 
@@ -324,7 +325,12 @@ void launch_chem(rt_ctx* ctx, double dt) {
   const int nc = ctx->all_active ? ctx->C : ctx->n_act;
   if (nc == 0) return;
   if (!mixed(ctx)) {
-    k_chem<<<nblk(nc, t), t, 0, ctx->stream>>>(a, P, nullptr);
+    // first attempt of every cell, then the rejected cells (as the mixed path)
+    k_chem64_first<<<nblk(nc, t), t, 0, ctx->stream>>>(a, P, ctx->work_cell, ctx->work_f1d, ctx->work_ctl);
+    if (!a.do_chem) return;
+    ctx->launches++;
+    const int nb = (int)std::min<long long>(nblk(nc, t), ctx->n_sm);
+    k_chem64_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->work_cell, ctx->work_f1d, ctx->work_ctl);
     return;
   }
   // first attempt of every cell, then the rejected cells (a persistent grid
@@ -336,6 +342,30 @@ void launch_chem(rt_ctx* ctx, double dt) {
   ctx->launches++;
   const int nb = (int)std::min<long long>(nblk(nc, t), ctx->n_sm);
   k_chem_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
+}
+
+// Whether rt_step runs the flux application of a subcycle and the sources +
+// first chemistry attempt of the next as one kernel (k_gather_chem).
+bool fused_gather_chem(const rt_ctx* ctx) {
+  return ctx->gc_ok && !ctx->cfg.split_kernels && mixed(ctx) && comp_sum(ctx) && ctx->all_active &&
+         ctx->cfg.splitting == 0 && ctx->cfg.time_order == 1 && ctx->cfg.chem_mode > 0;
+}
+
+// Flux application over dt, then sources and chemistry of the next
+// subcycle (of the same length): the fused kernel, then the worklist pass.
+void launch_gather_chem(rt_ctx* ctx, double dt) {
+  ProfScope ps(ctx, RT_KERNEL_GATHER_CHEM);
+  const CellArgs ga = cell_args(ctx, dt, 1, 0, 0);
+  const CellArgs ca = cell_args(ctx, dt, 0, 1, 1);
+  const ChemParams P = chem_params(ctx);
+  const ChemWork w{ctx->work_cell, ctx->work_f1, ctx->work_ctl};
+  const int n_tiles = (ctx->C + kGcTile - 1) / kGcTile;
+  const int nb = std::min(2 * ctx->n_sm, (n_tiles + kGcTeams - 1) / kGcTeams);
+  k_gather_chem<<<nb, kGcThreads, 0, ctx->stream>>>(ga, ca, P, (const float4*)ctx->flux, ctx->shadow, w, n_tiles);
+  ctx->launches++;
+  const int t = 128;
+  const int nb2 = (int)std::min<long long>(nblk(ctx->C, t), ctx->n_sm);
+  k_chem_rest<<<nb2, t, 0, ctx->stream>>>(ca, P, ctx->shadow, w);
 }
 
 void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
@@ -408,6 +438,13 @@ rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
     l2 = 0;
   }
   ctx->l2_bytes = (size_t)l2;
+  // The fused flux application + chemistry kernel splits its registers
+  // between warpgroups (setmaxnreg) out of the allocation it is launched
+  // with: use it only if it was compiled with exactly that allocation.
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_gather_chem) == cudaSuccess)
+    ctx->gc_ok = fa.numRegs == kGcRegsLaunch && fa.maxThreadsPerBlock >= kGcThreads;
+  cudaGetLastError();
   *out = ctx;
   return RT_OK;
 }
@@ -522,10 +559,13 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     if (e != cudaSuccess) return cuda_fail(ctx, e, "half-edges");
     ctx->allocs.push_back(p); ctx->xmax = p;
   }
+  AL(ctx->work_cell, C); AL(ctx->work_ctl, 4);
   if (mx) {
     AL(ctx->fa32, F); AL(ctx->fb32, F); AL(ctx->minv32, 6 * (size_t)C); AL(ctx->ivol, C);
-    AL(ctx->work_cell, C); AL(ctx->work_f1, C); AL(ctx->work_ctl, 4);
+    AL(ctx->work_f1, C);
     AL(ctx->shadow, (size_t)C * B);
+  } else {
+    AL(ctx->work_f1d, C);
   }
 #undef AL
   if ((st = copy_in(ctx, ctx->vol, cells->volume, (size_t)C * 8))) return st;
@@ -558,7 +598,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
                                                             sfx, sfy, sfz, sA, ctx->rL64, ctx->rR64, ctx->w64);
   }
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
-  if (mx) CK(cudaMemsetAsync(ctx->work_ctl, 0, 4 * sizeof(int), ctx->stream), "worklist");
+  CK(cudaMemsetAsync(ctx->work_ctl, 0, 4 * sizeof(int), ctx->stream), "worklist");
   k_geometry_cells<<<nblk(C), kThreads, 0, ctx->stream>>>(C, ctx->cfg.box, ctx->off, ctx->csr, ctx->lr, ctx->cx,
                                                           ctx->cy, ctx->cz, sA, ctx->minv64, ctx->status);
   if (mx && F > 0) {
@@ -859,10 +899,24 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   // Subcycle: sources + chemistry, gradients, fluxes, application (Lie);
   // Strang puts half the chemistry on each side of the transport.
   const bool strang = ctx->cfg.splitting == 1;
-  for (int s = 0; s < n_sub; ++s) {
-    launch_chem(ctx, strang ? 0.5 * dts : dts);
-    transport(ctx, dts);
-    if (strang) launch_chem(ctx, 0.5 * dts);
+  if (fused_gather_chem(ctx)) {
+    // the same launches with each flux application but the last fused with
+    // the next subcycle's sources and chemistry
+    launch_chem(ctx, dts);
+    for (int s = 0; s < n_sub; ++s) {
+      launch_grad_any(ctx);
+      launch_flux_any(ctx);
+      if (s + 1 < n_sub)
+        launch_gather_chem(ctx, dts);
+      else
+        launch_gather(ctx, dts, 0);
+    }
+  } else {
+    for (int s = 0; s < n_sub; ++s) {
+      launch_chem(ctx, strang ? 0.5 * dts : dts);
+      transport(ctx, dts);
+      if (strang) launch_chem(ctx, 0.5 * dts);
+    }
   }
   if (!capture) return launched(ctx, "rt_step");
   cudaGraph_t graph = nullptr;

@@ -469,9 +469,13 @@ __device__ bool chemistry_mixed_first(const ChemParams& P, double nH, double dt_
   return true;
 }
 
-__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {
-  double rem = dt_sub, dt = dt_sub;
-  int n = 0;
+// Adaptive substeps of the FP64 path (the oracle's arithmetic).  The loop
+// can resume after a rejected first attempt (two-pass chemistry): dt0 = the
+// next attempt's length, n0 = attempts already made.
+__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped, double dt0,
+                         int n0) {
+  double rem = dt_sub, dt = dt0;
+  int n = n0;
   CellState t;
   *capped = false;
   while (rem > 0) {
@@ -490,6 +494,22 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
     if (dt > rem) dt = rem;
   }
   return n;
+}
+__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {
+  return chemistry(P, nH, dt_sub, s, capped, dt_sub, 0);
+}
+
+// First attempt of the FP64 chemistry over the whole subcycle.  Accepted
+// (returns true): s is the end state.  Rejected: s is unchanged and *f1
+// holds the attempt's measure; the loop resumes with dt_sub * f_s / f1
+// (chemistry with n0 = 1), exactly where the single loop would go on.
+__device__ bool chemistry_first(const ChemParams& P, double nH, double dt_sub, CellState& s, double* f1) {
+  CellState t;
+  const double f = photochem_attempt(P, nH, dt_sub, s, t);
+  *f1 = f;
+  if (f > P.f_max) return false;
+  s = t;
+  return true;
 }
 
 }  // namespace m1rt

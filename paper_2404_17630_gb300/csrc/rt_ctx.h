@@ -18,6 +18,7 @@ struct rt_ctx {
   bool mesh_ready = false;
   int C = 0, F = 0, B = 0, max_deg = 0;
   int n_sm = 1;       // streaming multiprocessors of the device
+  bool gc_ok = false; // k_gather_chem compiled with the register count its warpgroup split assumes
   size_t l2_bytes = 0;  // L2 cache size of the device
   int grad_cap = 0;  // half-edge records of the largest gradient block (0: unstaged gradient kernel)
   double min_dx_cm = 0;
@@ -45,6 +46,7 @@ struct rt_ctx {
   double* ivol = nullptr;
   int32_t* work_cell = nullptr;  // mixed chemistry worklist (cells whose first attempt was rejected)
   float* work_f1 = nullptr;
+  double* work_f1d = nullptr;    // FP64 chemistry worklist: the rejected first attempt's measure
   int* work_ctl = nullptr;       // entries, next entry, finished blocks (zero between subcycles)
   // individual time steps: the lists of the current active set (all null /
   // zero when every cell is active), a view of one entry of `sets`

@@ -828,17 +828,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // Heun: the kernel handles Heun's stages (a.heun); the plain update is its
 // own instantiation, without the stages' code (which the compiler would
 // otherwise issue as predicated FP64 instructions on every launch).
-template <class R, bool Comp, bool Pred = false, bool Heun = false>
-__global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
-                                                float4* __restrict__ shadow) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+// The flux application's sum for (cell i, bin b): the cell's stored face
+// fluxes in CSR order, + where the cell is the left cell, - where it is the
+// right cell.  Comp (mixed precision): the FP32 terms summed as an
+// unevaluated FP32 pair hi + lo (error-free two_sum), widened to FP64 once;
+// otherwise each term widened and summed in FP64.  Pred: the face loads in
+// batches of four with a predicated last batch (no serial tail of single
+// loads) -- faster where the flux array is held in L2, slower where the
+// loads go to HBM and the extra registers cost occupancy.  k_gather and
+// k_gather_chem share it (and sub_flux), so the two round alike.
+template <class R, bool Comp, bool Pred>
+__device__ __forceinline__ void flux_sum(const CellArgs& a, const R4<R>* __restrict__ flux, int i, int b,
+                                         double acc[4]) {
   const int B = a.B;
-  if (t >= (a.list ? a.n : a.C) * B) return;
-  const int ii = divb(t, a.divB), b = t - ii * B;
-  const int i = a.list ? __ldg(a.list + ii) : ii;
-  t = i * B + b;
   const int k0 = a.off[i], k1 = a.off[i + 1];
-  double acc[4];
   if (Comp) {
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     auto add = [&](int e, const R4<R>& v) {
@@ -908,15 +911,42 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
       add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
     }
   }
-  // FP32 sweep: lam (1/V) with 1/V formed once per mesh (one FP64 multiply
-  // instead of a division per subcycle); the FP64 sweep divides as defined
-  const double kfac = sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
-  d4 u = a.rad[t];
-  if (Heun && a.heun == 1) a.rad0[t] = u;
+}
+
+// U <- U - c dt / V * sum (FP32 sweep: lam (1/V) with 1/V formed once per
+// mesh, one FP64 multiply instead of a division per subcycle; the FP64 sweep
+// divides as defined).
+template <class R> __device__ __forceinline__ double gather_kfac(const CellArgs& a, int i) {
+  return sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
+}
+__device__ __forceinline__ void sub_flux(d4& u, double kfac, const double acc[4]) {
   u.x -= kfac * acc[0];
   u.y -= kfac * acc[1];
   u.z -= kfac * acc[2];
   u.w -= kfac * acc[3];
+}
+
+// Flux application, one thread per (cell, bin): U <- U - c dt / V * sum of
+// the cell's stored face fluxes (flux_sum) in FP64.  Writes the FP32 shadow
+// if given.  Heun: the kernel handles Heun's stages (a.heun); the plain
+// update is its own instantiation, without the stages' code (which the
+// compiler would otherwise issue as predicated FP64 instructions on every
+// launch).
+template <class R, bool Comp, bool Pred = false, bool Heun = false>
+__global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
+                                                float4* __restrict__ shadow) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int B = a.B;
+  if (t >= (a.list ? a.n : a.C) * B) return;
+  const int ii = divb(t, a.divB), b = t - ii * B;
+  const int i = a.list ? __ldg(a.list + ii) : ii;
+  t = i * B + b;
+  double acc[4];
+  flux_sum<R, Comp, Pred>(a, flux, i, b, acc);
+  const double kfac = gather_kfac<R>(a, i);
+  d4 u = a.rad[t];
+  if (Heun && a.heun == 1) a.rad0[t] = u;
+  sub_flux(u, kfac, acc);
   if (Heun && a.heun == 2) {
     const d4 u0 = a.rad0[t];
     u.x = 0.5 * u0.x + 0.5 * u.x;
@@ -952,6 +982,15 @@ struct ChemWork {
   int* ctl;        // [0] entries, [1] next entry to hand out, [2] finished blocks
 };
 
+// Source term of Eq. (E) over the subcycle: the photons of the cell's
+// sources (rates summed in source order) added to N.
+__device__ __forceinline__ void inject_cell(const CellArgs& a, int i, int si, double N[kMaxBins]) {
+  const double vcm3 = a.vol[i] * a.lu3;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b)
+    if (b < a.B) N[b] += (a.src_rate[(size_t)si * a.B + b] * a.dt) / vcm3;
+}
+
 __device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasState& s, bool inject) {
   const int B = a.B;
 #pragma unroll
@@ -959,12 +998,7 @@ __device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasSta
     if (b < B) s.N[b] = a.rad[(size_t)i * B + b].x;
   if (inject) {
     const int si = a.src_idx[i];
-    if (si >= 0) {
-      const double vcm3 = a.vol[i] * a.lu3;
-#pragma unroll
-      for (int b = 0; b < kMaxBins; ++b)
-        if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
-    }
+    if (si >= 0) inject_cell(a, i, si, s.N);
   }
   const size_t C = a.C;
   s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
@@ -972,16 +1006,17 @@ __device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasSta
 }
 
 // Final state of a cell: radiation (flux scaled by S), shadow, gas, count.
+// The flux is read from u_in (the cell's master records, or a copy of them).
 __device__ __forceinline__ void chem_store_mixed(const CellArgs& a, int i, const GasState& s,
                                                  const double S[kMaxBins], int n, bool gas,
-                                                 float4* __restrict__ shadow) {
+                                                 float4* __restrict__ shadow, const d4* u_in = nullptr) {
   const int B = a.B;
   bool bad = false;
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
       d4* r = a.rad + (size_t)i * B + b;
-      const d4 u = *r;
+      const d4 u = u_in ? u_in[b] : *r;
       const d4 o = make_d4(s.N[b], u.y * S[b], u.z * S[b], u.w * S[b]);
       *r = o;
       if (!isfinite(o.x)) bad = true;
@@ -1025,17 +1060,23 @@ __global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, fl
   w.f1[k] = f1;
 }
 
+// The worklist's cells, one per thread, handed out 32 at a time to warps.
+// The cells left after the first pass are few and stiff (each runs its own
+// serial chain of attempts, and a warp runs as long as its slowest cell), so
+// the first chunks go to warp 0 of every block -- one warp per SM, each with
+// the SM's FP64 unit to itself -- then to warp 1 of every block, and so on;
+// later chunks go to whichever warp is free.
 __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, float4* __restrict__ shadow,
                                                    ChemWork w) {
-  __shared__ int base;
   const int total = *(volatile int*)w.ctl;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  // static first chunk: warp-in-block major, so that consecutive chunks lie
+  // on different SMs; then dynamic chunks after all the static ones
+  int chunk = wib * gridDim.x + blockIdx.x;
   for (;;) {
-    if (threadIdx.x == 0) base = atomicAdd(w.ctl + 1, (int)blockDim.x);
-    __syncthreads();
-    const int k = base + (int)threadIdx.x;
-    const bool more = base < total;
-    __syncthreads();
-    if (!more) break;
+    const int k = chunk * 32 + lane;
+    if (chunk * 32 >= total) break;
     if (k < total) {
       const int i = w.cell[k];
       GasState s;
@@ -1047,11 +1088,14 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
       if (capped) atomicOr(a.status, kStChemSubsteps);
       chem_store_mixed(a, i, s, S, n, true, shadow);
     }
+    int next = 0;
+    if (lane == 0) next = n_warps + atomicAdd(w.ctl + 1, 1);
+    chunk = __shfl_sync(0xffffffffu, next, 0);
   }
-  // the last block to finish resets the worklist for the next subcycle
-  if (threadIdx.x == 0) {
+  // the last warp to finish resets the worklist for the next subcycle
+  if (lane == 0) {
     __threadfence();
-    if (atomicAdd(w.ctl + 2, 1) == (int)gridDim.x - 1) {
+    if (atomicAdd(w.ctl + 2, 1) == n_warps - 1) {
       w.ctl[0] = 0;
       w.ctl[1] = 0;
       w.ctl[2] = 0;
@@ -1060,51 +1104,244 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
   }
 }
 
-__global__ void __launch_bounds__(128) k_chem(CellArgs a, ChemParams P, float4* __restrict__ shadow) {
+// Flux application of subcycle s fused with the sources and the first
+// chemistry attempt of subcycle s + 1 (mixed precision, every cell active,
+// Lie splitting, forward-Euler transport).  The flux application is bound by
+// memory and the chemistry by GB300's FP64 unit; as two kernels they run one
+// after the other, here they run at the same time in every SM:
+//
+//   * a block is four warpgroups: warpgroup 0 runs the chemistry (one thread
+//     per cell), warpgroups 1-3 the flux application (one thread per
+//     (cell, bin), as k_gather);
+//   * four teams per block, team t = warp t of each warpgroup: 32 cells at
+//     a time; the three flux-application warps sum the fluxes of tile k + 1
+//     (and fetch its gas state) into a shared-memory slot while the
+//     chemistry warp works through tile k; a ring of kGcSlots slots per team,
+//     each with a "full" and an "empty" mbarrier;
+//   * the flux-application warpgroups give registers to the chemistry
+//     warpgroup (setmaxnreg: 48 and 104 of the 64 per thread the block is
+//     launched with; 3 x 128 x 48 + 128 x 104 = 31744 <= 512 x 64).
+//
+// The arithmetic of every cell is that of k_gather followed by k_chem_first
+// (the same device functions), so the results are bit for bit those of the
+// two kernels.  Rejected first attempts go to the worklist for k_chem_rest.
+// Every wait is bounded: a wait that gives up records kStTimeout and its
+// warp leaves (nothing is in flight).
+constexpr int kGcThreads = 512;
+constexpr int kGcTeams = 4;
+constexpr int kGcSlots = 2;
+constexpr int kGcTile = 32;
+constexpr int kGcRegsChem = 104, kGcRegsGather = 48, kGcRegsLaunch = 64;
+static_assert(128 * kGcRegsChem + 384 * kGcRegsGather <= kGcThreads * kGcRegsLaunch,
+              "register split above the block's launch allocation");
+
+struct GcSlot {
+  d4 U[kGcTile][kMaxBins];      // the cell's state after the flux application
+  double gas[7][kGcTile];       // n_H, x_HI, x_HII, y_HeI, y_HeII, y_HeIII, T
+  int src[kGcTile];             // source index of the cell, -1 for none
+};
+
+__global__ void __launch_bounds__(kGcThreads, 2)
+    k_gather_chem(CellArgs ga, CellArgs ca, ChemParams P, const float4* __restrict__ flux,
+                  float4* __restrict__ shadow, ChemWork w, int n_tiles) {
+  __shared__ GcSlot slot[kGcTeams][kGcSlots];
+  __shared__ __align__(8) uint64_t full[kGcTeams][kGcSlots], empty[kGcTeams][kGcSlots];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = warp >> 2, team = warp & 3;
+  const int B = ga.B;
+  if (threadIdx.x < kGcTeams * kGcSlots) {
+    const int tm = threadIdx.x / kGcSlots, sl = threadIdx.x % kGcSlots;
+    mbar_init(&full[tm][sl], 96);    // every thread of the team's three flux-application warps
+    mbar_init(&empty[tm][sl], 32);   // every thread of the team's chemistry warp
+  }
+  __syncthreads();
+  const int n_teams = gridDim.x * kGcTeams;
+  const int first = blockIdx.x * kGcTeams + team;
+  if (wg == 0) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kGcRegsChem));
+    // chemistry: lane = cell of the tile
+    for (int k = 0, tile = first; tile < n_tiles; ++k, tile += n_teams) {
+      const int sl = k % kGcSlots;
+      GcSlot& S = slot[team][sl];
+      if (!mbar_wait(&full[team][sl], (uint32_t)((k / kGcSlots) & 1))) {
+        atomicOr(ca.status, kStTimeout);
+        return;
+      }
+      const int i = tile * kGcTile + lane;
+      if (i < ca.C) {
+        GasState s;
+        double Sc[kMaxBins];
+#pragma unroll
+        for (int b = 0; b < kMaxBins; ++b) {
+          Sc[b] = 1.0;
+          if (b < B) s.N[b] = S.U[lane][b].x;
+        }
+        if (ca.do_inject) {
+          const int si = S.src[lane];
+          if (si >= 0) inject_cell(ca, i, si, s.N);
+        }
+        s.xHI = S.gas[1][lane]; s.xHII = S.gas[2][lane]; s.yI = S.gas[3][lane]; s.yII = S.gas[4][lane];
+        s.yIII = S.gas[5][lane]; s.T = S.gas[6][lane];
+        float f1;
+        if (chemistry_mixed_first(P, S.gas[0][lane], ca.dt, s, Sc, &f1)) {
+          chem_store_mixed(ca, i, s, Sc, 1, true, shadow, S.U[lane]);
+        } else {
+          // rejected: the state after the flux application with the injected
+          // photons, for the second pass
+#pragma unroll
+          for (int b = 0; b < kMaxBins; ++b) {
+            if (b < B) {
+              const d4 u = S.U[lane][b];
+              ca.rad[(size_t)i * B + b] = make_d4(s.N[b], u.y, u.z, u.w);
+            }
+          }
+          const int q = atomicAdd(w.ctl, 1);
+          w.cell[q] = i;
+          w.f1[q] = f1;
+        }
+      }
+      mbar_arrive(&empty[team][sl]);
+    }
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kGcRegsGather));
+    // flux application: thread q of the team = (cell q / B, bin q % B)
+    const int q = (wg - 1) * 32 + lane;
+    const int c = divb(q, ga.divB), b = q - c * B;
+    const bool gathers = q < kGcTile * B;
+    for (int k = 0, tile = first; tile < n_tiles; ++k, tile += n_teams) {
+      const int sl = k % kGcSlots;
+      GcSlot& S = slot[team][sl];
+      if (!mbar_wait(&empty[team][sl], (uint32_t)(((k / kGcSlots) & 1) ^ 1))) {
+        atomicOr(ga.status, kStTimeout);
+        return;
+      }
+      const int i0 = tile * kGcTile;
+      const int i = i0 + c;
+      if (gathers && i < ga.C) {
+        double acc[4];
+        flux_sum<float, true, false>(ga, flux, i, b, acc);
+        const double kfac = gather_kfac<float>(ga, i);
+        d4 u = ga.rad[(size_t)i * B + b];
+        sub_flux(u, kfac, acc);
+        if (!isfinite(u.x)) atomicOr(ga.status, kStNonFinite);
+        S.U[c][b] = u;
+      }
+      // the tile's gas state and source indices for the chemistry warp
+      const size_t C = ga.C;
+      for (int e = q; e < 8 * kGcTile; e += 96) {
+        const int cc = e & (kGcTile - 1), v = e >> 5;
+        const int ic = i0 + cc;
+        if (ic < ga.C) {
+          if (v == 0) S.gas[0][cc] = ca.nH[ic];
+          else if (v < 6) S.gas[v][cc] = ca.x5[(size_t)(v - 1) * C + ic];
+          else if (v == 6) S.gas[6][cc] = ca.T[ic];
+          else S.src[cc] = ca.do_inject ? ca.src_idx[ic] : -1;
+        }
+      }
+      mbar_arrive(&full[team][sl]);
+    }
+  }
+}
+
+// FP64 path: a cell's state (radiation of every bin and gas) in and out.
+__device__ __forceinline__ void chem_load64(const CellArgs& a, int i, CellState& s, bool inject) {
+  const int B = a.B;
+  const size_t C = a.C;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      d4 v = a.rad[(size_t)i * B + b];
+      s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
+    }
+  }
+  if (inject) {
+    const int si = a.src_idx[i];
+    if (si >= 0) inject_cell(a, i, si, s.N);
+  }
+  s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
+  s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+}
+__device__ __forceinline__ void chem_store64(const CellArgs& a, int i, const CellState& s, bool gas) {
+  const int B = a.B;
+  const size_t C = a.C;
+  if (gas) {
+    a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
+    a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+  }
+  bool bad = false;
+#pragma unroll
+  for (int b = 0; b < kMaxBins; ++b) {
+    if (b < B) {
+      a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
+      if (!isfinite(s.N[b])) bad = true;
+    }
+  }
+  if (bad) atomicOr(a.status, kStNonFinite);
+}
+
+// Sources and thermochemistry of the FP64 path in two passes, as the mixed
+// path (Sec. 6.2's remedy for the divergence of the substep loop): the first
+// attempt of every cell, then the rejected cells from a worklist.  The
+// attempts of every cell are those of the single loop.
+__global__ void __launch_bounds__(128) k_chem64_first(CellArgs a, ChemParams P, int32_t* __restrict__ work_cell,
+                                                      double* __restrict__ work_f1, int* __restrict__ work_ctl) {
   const int ii = blockIdx.x * blockDim.x + threadIdx.x;
   if (ii >= (a.list ? a.n : a.C)) return;
   const int i = a.list ? __ldg(a.list + ii) : ii;
-  const int B = a.B;
-  const size_t C = a.C;
-  {
-    CellState s;
+  CellState s;
+  chem_load64(a, i, s, a.do_inject);
+  if (!a.do_chem) {
+    chem_store64(a, i, s, false);
+    return;
+  }
+  double f1;
+  if (chemistry_first(P, a.nH[i], a.dt, s, &f1)) {
+    a.nsub[i] = 1;
+    chem_store64(a, i, s, true);
+    return;
+  }
+  // rejected: keep the injected photons, hand the cell to the second pass
 #pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) {
-      if (b < B) {
-        d4 v = a.rad[(size_t)i * B + b];
-        s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
-      }
-    }
-    if (a.do_inject) {
-      const int si = a.src_idx[i];
-      if (si >= 0) {
-        const double vcm3 = a.vol[i] * a.lu3;
-#pragma unroll
-        for (int b = 0; b < kMaxBins; ++b)
-          if (b < B) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
-      }
-    }
-    if (a.do_chem) {
-      s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
-      s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
+  for (int b = 0; b < kMaxBins; ++b)
+    if (b < a.B) a.rad[(size_t)i * a.B + b].x = s.N[b];
+  const int k = atomicAdd(work_ctl, 1);
+  work_cell[k] = i;
+  work_f1[k] = f1;
+}
+
+// The FP64 worklist, handed out as k_chem_rest hands out the mixed one.
+__global__ void __launch_bounds__(128) k_chem64_rest(CellArgs a, ChemParams P, const int32_t* __restrict__ work_cell,
+                                                     const double* __restrict__ work_f1, int* work_ctl) {
+  const int total = *(volatile int*)work_ctl;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  int chunk = wib * gridDim.x + blockIdx.x;
+  for (;;) {
+    const int k = chunk * 32 + lane;
+    if (chunk * 32 >= total) break;
+    if (k < total) {
+      const int i = work_cell[k];
+      CellState s;
+      chem_load64(a, i, s, false);
       bool capped;
-      const int n = chemistry(P, a.nH[i], a.dt, s, &capped);
+      const double dt0 = a.dt * div_nr(P.f_s, work_f1[k]);
+      const int n = chemistry(P, a.nH[i], a.dt, s, &capped, dt0, 1);
       a.nsub[i] = n;
       if (capped) atomicOr(a.status, kStChemSubsteps);
-      a.x5[i] = s.xHI; a.x5[C + i] = s.xHII; a.x5[2 * C + i] = s.yI; a.x5[3 * C + i] = s.yII;
-      a.x5[4 * C + i] = s.yIII; a.T[i] = s.T;
+      chem_store64(a, i, s, true);
     }
-    bool bad = false;
-#pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) {
-      if (b < B) {
-        a.rad[(size_t)i * B + b] = make_d4(s.N[b], s.f[b][0], s.f[b][1], s.f[b][2]);
-        if (!isfinite(s.N[b])) bad = true;
-        if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(s.N[b]), d2f_int(s.f[b][0]), d2f_int(s.f[b][1]),
-                                                            d2f_int(s.f[b][2]));
-      }
+    int next = 0;
+    if (lane == 0) next = n_warps + atomicAdd(work_ctl + 1, 1);
+    chunk = __shfl_sync(0xffffffffu, next, 0);
+  }
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(work_ctl + 2, 1) == n_warps - 1) {
+      work_ctl[0] = 0;
+      work_ctl[1] = 0;
+      work_ctl[2] = 0;
+      __threadfence();
     }
-    if (bad) atomicOr(a.status, kStNonFinite);
   }
 }
 
