@@ -118,8 +118,6 @@ def survey_bytes(kernel, C, F, w):
         return (4 + 8 + rad) * C + (8 + 12 * w) * F
     if kernel == "k_chem":
         return 104 * C
-    if kernel == "k_gather_chem":
-        return survey_bytes("k_gather", C, F, w) + survey_bytes("k_chem", C, F, w)
     raise KeyError(kernel)
 
 
@@ -152,13 +150,6 @@ def layout_bytes(kernel, C, F, B, w):
         # source ids 4C, n_H 8C, abundances r/w 80C, T r/w 16C, substep counts 4C
         shadow = 16 * B * C if w == 4 else 0
         return 64 * B * C + shadow + 8 * C + 4 * C + 8 * C + 80 * C + 16 * C + 4 * C
-    if kernel == "k_gather_chem":
-        # the flux application's reads (offsets, CSR, fluxes, 1/V, master
-        # radiation) and the chemistry's writes (master radiation, FP32
-        # shadow, abundances, T, substep counts) and gas reads (n_H,
-        # abundances, T, source ids): the radiation makes one round trip
-        return (4 * C + 8 * F + 4 * w * B * F + 8 * C + 32 * B * C + 32 * B * C + 16 * B * C
-                + 8 * C + 40 * C + 8 * C + 4 * C + 40 * C + 8 * C + 4 * C)
     raise KeyError(kernel)
 
 
@@ -399,7 +390,7 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
 # steady state), per cell for the FP64 sweep kernels.  The unit counts behind
 # the `alu` rooflines; re-measured after each change of these kernels.
 FP64_FLOP = {
-    "mixed": {"k_chem": (176.0, "attempt"), "k_gather_chem": (215.0, "attempt")},
+    "mixed": {"k_chem": (176.0, "attempt")},
     "fp64": {"k_chem": (1238.0, "attempt"), "k_grad": (2762.4, "cell"), "k_flux": (5578.0, "cell"),
              "k_gather": (439.4, "cell")},
 }
@@ -452,11 +443,10 @@ def roofline(res, precision, peaks, peak_kind, fp64pk, attempts=None, n_sub=None
             tf = f * units[u] / (kern[k]["ms_per_launch"] / 1e3) / 1e12
             kern[k]["fp64_tflops"] = round(tf, 4)
             kern[k]["fp64_frac"] = round(tf / fpk, 4)
-    parts = [k for k in ("k_gather", "k_chem", "k_gather_chem") if k in prof]
+    parts = [k for k in ("k_gather", "k_chem") if k in prof]
     if "k_grad" in prof and parts:
-        # the contract's gather + chemistry row over the time of the kernels
-        # that do it (separate, or fused with the next subcycle's chemistry),
-        # per subcycle
+        # the contract's gather + chemistry row over the time of the two
+        # kernels that do it, per subcycle
         ms = sum(prof[k][0] for k in parts) / prof["k_grad"][1]
         sb = survey_bytes("k_gather", C, F, w) + survey_bytes("k_chem", C, F, w)
         kern["k_gather+k_chem"] = {"ms_per_subcycle": ms, "alg_bytes_per_launch": sb, "kernels": parts,
@@ -471,7 +461,7 @@ def roofline(res, precision, peaks, peak_kind, fp64pk, attempts=None, n_sub=None
                 "layout_frac": round(kern[k]["layout_GBs"] / peak, 4)}
 
     top = max(prof, key=lambda k: prof[k][0])
-    mem = [k for k in prof if k not in ("k_chem", "k_gather_chem")]
+    mem = [k for k in prof if k != "k_chem"]
     top_mem = max(mem, key=lambda k: prof[k][0])
     if top in flops:
         f, u = flops[top]

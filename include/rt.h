@@ -100,10 +100,6 @@ typedef struct {
   int time_order;         /* 1 = forward-Euler transport (no time extrapolation, Sec. 2.3.3);
                              2 = Heun's method in SSP form: U1 = U + dt L(U), U2 = U1 + dt L(U1),
                              U' = U/2 + U2/2 (second order in time, positive under the same CFL) */
-  int split_kernels;      /* RT_MIXED, Lie, forward Euler, every cell active: 0 = the flux application of a
-                             subcycle and the sources + first chemistry attempt of the next run as one kernel
-                             (memory-bound and FP64-bound warps side by side in every SM; bit for bit the
-                             results of separate kernels); 1 = separate kernels */
 } rt_config;
 
 /* Cells of the static mesh (structure of arrays, n entries each). */
@@ -220,9 +216,7 @@ rt_status rt_adjoint(rt_ctx *ctx, double dt, int n_sub, int checkpoint_every, co
  * class k (RT_KERNEL_*), the summed device time ms[k] (milliseconds) and the
  * number of launches[k] since the last reset; reset != 0 clears them.
  * n = length of the caller's arrays (at most RT_KERNEL_COUNT are filled). */
-enum { RT_KERNEL_CHEM = 0, RT_KERNEL_GRAD = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_GATHER = 3,
-       RT_KERNEL_GATHER_CHEM = 4, /* the fused flux application + next subcycle's chemistry (split_kernels 0) */
-       RT_KERNEL_COUNT = 5 };
+enum { RT_KERNEL_CHEM = 0, RT_KERNEL_GRAD = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_GATHER = 3, RT_KERNEL_COUNT = 4 };
 rt_status rt_profile_enable(rt_ctx *ctx, int on);
 rt_status rt_profile_read(rt_ctx *ctx, int n, double *ms, int64_t *launches, int reset);
 

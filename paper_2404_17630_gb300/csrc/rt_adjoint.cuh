@@ -26,19 +26,22 @@ namespace m1rt {
 // transport
 // ---------------------------------------------------------------------------
 
-// Reverse of m1_normal (N D n): lamP -> lamN, lamf (accumulated).
+// Reverse of m1_normal (N D n): lamP -> lamN, lamf (accumulated).  Its
+// quotients by one refined reciprocal per denominator (div_nr).
 __device__ __forceinline__ void m1_normal_vjp(const double v[4], double n0, double n1, double n2, const double lP[3],
                                               double& lN, double lf[3]) {
   const double fl = sqrt(v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
   const double lPn = lP[0] * n0 + lP[1] * n1 + lP[2] * n2;
   if (v[0] > 0.0 && fl > 0.0) {
-    double f = fl / v[0];
+    const double iv0 = div_nr(1.0, v[0]), ifl = div_nr(1.0, fl);
+    double f = fl * iv0;
     const bool clamped = f > 1.0;
     if (clamped) f = 1.0;
     const double s = sqrt(4.0 - 3.0 * f * f);
     const double den = 5.0 + 2.0 * s;
-    const double chi = (3.0 + 4.0 * f * f) / den;
-    const double u0 = v[1] / fl, u1 = v[2] / fl, u2 = v[3] / fl;
+    const double iden = div_nr(1.0, den);
+    const double chi = (3.0 + 4.0 * f * f) * iden;
+    const double u0 = v[1] * ifl, u1 = v[2] * ifl, u2 = v[3] * ifl;
     const double un = u0 * n0 + u1 * n1 + u2 * n2;
     const double a = 0.5 * (1.0 - chi), bb = 0.5 * (3.0 * chi - 1.0);
     const double lPu = lP[0] * u0 + lP[1] * u1 + lP[2] * u2;
@@ -48,16 +51,16 @@ __device__ __forceinline__ void m1_normal_vjp(const double v[4], double n0, doub
     const double lu1 = v[0] * bb * (n1 * lPu + un * lP[1]);
     const double lu2 = v[0] * bb * (n2 * lPu + un * lP[2]);
     const double lchi = -0.5 * la + 1.5 * lbb;
-    const double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f / s) / (den * den);
+    const double dchi = (8.0 * f * den + (3.0 + 4.0 * f * f) * 6.0 * f * div_nr(1.0, s)) * (iden * iden);
     const double lff = clamped ? 0.0 : lchi * dchi;
-    const double lfl = lff / v[0];
-    lN -= lff * (fl / v[0]) / v[0];
+    const double lfl = lff * iv0;
+    lN -= lff * (fl * iv0) * iv0;
     const double luu = lu0 * u0 + lu1 * u1 + lu2 * u2;
-    lf[0] += (lu0 - luu * u0) / fl + lfl * u0;
-    lf[1] += (lu1 - luu * u1) / fl + lfl * u1;
-    lf[2] += (lu2 - luu * u2) / fl + lfl * u2;
+    lf[0] += (lu0 - luu * u0) * ifl + lfl * u0;
+    lf[1] += (lu1 - luu * u1) * ifl + lfl * u1;
+    lf[2] += (lu2 - luu * u2) * ifl + lfl * u2;
   } else {
-    lN += lPn / 3.0;
+    lN += lPn * (1.0 / 3.0);
   }
 }
 
@@ -89,10 +92,11 @@ __device__ __forceinline__ void face_post_vjp(const double pre[4], const double 
   const double fl = sqrt(pre[1] * pre[1] + pre[2] * pre[2] + pre[3] * pre[3]);
   lpre[0] = lv[0]; lpre[1] = lv[1]; lpre[2] = lv[2]; lpre[3] = lv[3];
   if (fl > v0) {
+    const double ifl = div_nr(1.0, fl);
     const double lvf = lv[1] * pre[1] + lv[2] * pre[2] + lv[3] * pre[3];
-    lpre[0] = lv[0] + lvf / fl;
+    lpre[0] = lv[0] + lvf * ifl;
 #pragma unroll
-    for (int k = 1; k < 4; ++k) lpre[k] = (v0 / fl) * (lv[k] - (lvf / fl) * (pre[k] / fl));
+    for (int k = 1; k < 4; ++k) lpre[k] = (v0 * ifl) * (lv[k] - (lvf * ifl) * (pre[k] * ifl));
   }
   if (clampN) lpre[0] = 0.0;
 }
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256) k_adj_face(AdjArgs a) {
   const d4 nA = a.nA[f];
   const size_t sL = (size_t)c.x * B + b, sR = (size_t)c.y * B + b;
   const d4 lo_L = a.lam_out[sL], lo_R = a.lam_out[sR];
-  const double iVL = 1.0 / a.vol[c.x], iVR = 1.0 / a.vol[c.y];
+  const double iVL = div_nr(1.0, a.vol[c.x]), iVR = div_nr(1.0, a.vol[c.y]);
   double lout[4] = {a.lam * (lo_R.x * iVR - lo_L.x * iVL), a.lam * (lo_R.y * iVR - lo_L.y * iVL),
                     a.lam * (lo_R.z * iVR - lo_L.z * iVL), a.lam * (lo_R.w * iVR - lo_L.w * iVL)};
   double preL[4], preR[4], vL[4], vR[4];
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256) k_adj_cellgrad(AdjArgs a) {
           const double dphi = g[0] * x.x + g[1] * x.y + g[2] * x.z;
           const double xx = x.x * x.x + x.y * x.y + x.z * x.z;
           if (dphi * dphi > a.lim_eps2 * gg * xx) {
-            const double lim = dphi > 0.0 ? (mx[q] - vi) / dphi : (mn[q] - vi) / dphi;
+            const double lim = div_nr(dphi > 0.0 ? mx[q] - vi : mn[q] - vi, dphi);
             if (lim < psi) {
               psi = lim; dstar = dphi; xs[0] = x.x; xs[1] = x.y; xs[2] = x.z;
               js = dphi > 0.0 ? jmx[q] : jmn[q];
@@ -236,11 +240,12 @@ __global__ void __launch_bounds__(256) k_adj_cellgrad(AdjArgs a) {
         }
         if (js >= 0) {
           const double sdot = lG[q][0] * g[0] + lG[q][1] * g[1] + lG[q][2] * g[2];
+          const double sd = div_nr(sdot, dstar);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) lg[d] = psi * lG[q][d] - sdot * psi / dstar * xs[d];
+          for (int d = 0; d < 3; ++d) lg[d] = psi * lG[q][d] - sd * psi * xs[d];
           if (js != i) {
-            lU[q] -= sdot / dstar;
-            coef[q] = sdot / dstar;
+            lU[q] -= sd;
+            coef[q] = sd;
             jst[q] = js;
           }
         }
@@ -328,71 +333,66 @@ __device__ __forceinline__ void unpack_state(const double* s, int B, CellState& 
 }
 
 // Temperature derivatives of the rate fits (RateEval<false>) for the
-// reverse mode of the thermal network.  The Hui & Gnedin form
-// a lam^1.5 / (1 + (lam/2.74)^0.407)^2.242 with lam = 2 T_tr / T has
-// d ln alpha / d ln T = -(1.5 - 2.242 * 0.407 u / (1 + u)), u = (lam/2.74)^0.407.
+// reverse mode of the thermal network, from the same functions of T the
+// fits use (TFns: one logarithm, the shared Boltzmann factors).  The Hui &
+// Gnedin form a lam^1.5 / (1 + (lam/2.74)^0.407)^2.242 with lam = 2 T_tr / T
+// has d ln alpha / d ln T = -(1.5 - 2.242 * 0.407 u / (1 + u)),
+// u = (lam/2.74)^0.407; d ln(1 / (1 + (T/1e5)^(1/2))) / dT = -(1 - tf) / (2T)
+// with tf that factor.
 struct RateSlopes {
   double aHII, aHeII, aHeIII, bHI, bHeI, bHeII;   // d/dT
 };
 
-__device__ __forceinline__ double hg_slope(double T, double t_tr, double coef) {
-  const double lam = 2.0 * t_tr / T;
-  const double u = pow(lam / 2.740, 0.407);
-  const double a = coef * pow(lam, 1.5) / pow(1.0 + u, 2.242);
-  return -a * (1.5 - 2.242 * 0.407 * u / (1.0 + u)) / T;
-}
-// d/dT of c T^-1.5 exp(-470000/T) (1 + 0.3 exp(-94000/T))
-__device__ __forceinline__ double diel_slope(double T, double c) {
-  const double e1 = exp(-470000.0 / T), e2 = exp(-94000.0 / T);
-  const double g = c * pow(T, -1.5) * e1;
-  return g * ((470000.0 / (T * T) - 1.5 / T) * (1.0 + 0.3 * e2) + 0.3 * e2 * 94000.0 / (T * T));
-}
-// d ln(1 / (1 + sqrt(T / 1e5))) / dT
-__device__ __forceinline__ double tf_slope(double T) {
-  const double r = sqrt(T / 1e5);
-  return -0.5 * r / (T * (1.0 + r));
-}
-
-__device__ RateSlopes rate_slopes(double T, const Rates& r) {
+__device__ RateSlopes rate_slopes(const TFns& t, const Rates& r) {
   RateSlopes d;
-  d.aHII = hg_slope(T, 157807.0, 2.753e-14);
-  d.aHeII = -0.75 * 1.26e-14 * pow(2.0 * 285335.0 / T, 0.750) / T + diel_slope(T, 1.9e-3);
-  d.aHeIII = hg_slope(T, 631515.0, 5.506e-14);
-  const double ts = tf_slope(T);
-  d.bHI = r.bHI * (0.5 / T + 157809.1 / (T * T) + ts);
-  d.bHeI = r.bHeI * (0.5 / T + 285335.4 / (T * T) + ts);
-  d.bHeII = r.bHeII * (0.5 / T + 631515.0 / (T * T) + ts);
+  const double uH = exp(0.407 * (kLnAH - t.lnT)), uHe2 = exp(0.407 * (kLnAHe2 - t.lnT));
+  d.aHII = -r.aHII * (1.5 - 2.242 * 0.407 * div_nr(uH, 1.0 + uH)) * t.iT;
+  d.aHeIII = -r.aHeIII * (1.5 - 2.242 * 0.407 * div_nr(uHe2, 1.0 + uHe2)) * t.iT;
+  // HeII: radiative 1.26e-14 lam^0.75 and dielectronic
+  // 1.9e-3 T^-1.5 exp(-470000/T) (1 + 0.3 exp(-94000/T))
+  const double iT2 = t.iT * t.iT;
+  const double rad = 1.26e-14 * exp(0.750 * (kLnLHe - t.lnT));
+  const double g = 1.9e-3 * div_nr(t.iT, t.sT) * t.e470;
+  d.aHeII = -0.75 * rad * t.iT +
+            g * ((470000.0 * iT2 - 1.5 * t.iT) * (1.0 + 0.3 * t.e94) + 0.3 * t.e94 * 94000.0 * iT2);
+  const double ts = -0.5 * (1.0 - t.tf) * t.iT;
+  d.bHI = r.bHI * (0.5 * t.iT + 157809.1 * iT2 + ts);
+  d.bHeI = r.bHeI * (0.5 * t.iT + 285335.4 * iT2 + ts);
+  d.bHeII = r.bHeII * (0.5 * t.iT + 631515.0 * iT2 + ts);
   return d;
 }
 
 // The cooling function as n_e (k_HI n_HI + k_HII n_HII + k_HeI n_HeI +
 // k_HeII n_HeII + k_HeIII n_HeIII), per-species coefficients and their T
-// derivatives (the terms of RateEval<false>::cooling grouped by species).
+// derivatives (the terms of RateEval<false>::cooling grouped by species),
+// from the same functions of T.
 struct CoolCoef {
   double k[5], dk[5];   // HI, HII, HeI, HeII, HeIII
 };
 
-__device__ CoolCoef cooling_coef(double T) {
-  const double sT = sqrt(T), tf = 1.0 / (1.0 + sqrt(T / 1e5)), ts = tf_slope(T), iT2 = 1.0 / (T * T);
+__device__ CoolCoef cooling_coef(const TFns& t) {
+  const double sT = t.sT, tf = t.tf, iT = t.iT, iT2 = iT * iT, ts = -0.5 * (1.0 - tf) * iT;
   // collisional excitation and ionisation
-  const double ceH = 7.50e-19 * exp(-118348.0 / T) * tf, dceH = ceH * (118348.0 * iT2 + ts);
-  const double ceHe = 5.54e-17 * pow(T, -0.397) * exp(-473638.0 / T) * tf,
-               dceHe = ceHe * (473638.0 * iT2 - 0.397 / T + ts);
-  const double ciH = 1.27e-21 * sT * exp(-157809.1 / T) * tf, dciH = ciH * (0.5 / T + 157809.1 * iT2 + ts);
-  const double ciHe = 9.38e-22 * sT * exp(-285335.4 / T) * tf, dciHe = ciHe * (0.5 / T + 285335.4 * iT2 + ts);
-  const double ciHe2 = 4.95e-22 * sT * exp(-631515.0 / T) * tf, dciHe2 = ciHe2 * (0.5 / T + 631515.0 * iT2 + ts);
+  const double ceH = 7.50e-19 * exp(-118348.0 * iT) * tf, dceH = ceH * (118348.0 * iT2 + ts);
+  const double ceHe = 5.54e-17 * exp(-0.397 * t.lnT - 473638.0 * iT) * tf,
+               dceHe = ceHe * (473638.0 * iT2 - 0.397 * iT + ts);
+  const double ciH = 1.27e-21 * sT * t.e157 * tf, dciH = ciH * (0.5 * iT + 157809.1 * iT2 + ts);
+  const double ciHe = 9.38e-22 * sT * t.e285 * tf, dciHe = ciHe * (0.5 * iT + 285335.4 * iT2 + ts);
+  const double ciHe2 = 4.95e-22 * sT * t.e631 * tf, dciHe2 = ciHe2 * (0.5 * iT + 631515.0 * iT2 + ts);
   // recombination
-  const double q = pow(T / 1e6, 0.7);
-  const double t3 = pow(T / 1e3, -0.2) / (1.0 + q), lt3 = -0.2 / T - 0.7 * q / (T * (1.0 + q));
-  const double rH = 8.70e-27 * sT * t3, drH = rH * (0.5 / T + lt3);
-  const double rHe = 1.55e-26 * pow(T, 0.3647), drHe = rHe * 0.3647 / T;
-  const double rHe2 = 3.48e-26 * sT * t3, drHe2 = rHe2 * (0.5 / T + lt3);
-  const double di = 1.24e-13 * pow(T, -1.5) * exp(-470000.0 / T) * (1.0 + 0.3 * exp(-94000.0 / T));
-  const double ddi = diel_slope(T, 1.24e-13);
+  const double q = exp(0.7 * (t.lnT - kLn1e6));
+  const double iq = div_nr(1.0, 1.0 + q);
+  const double t3 = exp(-0.2 * (t.lnT - kLn1e3)) * iq, lt3 = -0.2 * iT - 0.7 * q * iT * iq;
+  const double rH = 8.70e-27 * sT * t3, drH = rH * (0.5 * iT + lt3);
+  const double rHe = 1.55e-26 * exp(0.3647 * t.lnT), drHe = rHe * 0.3647 * iT;
+  const double rHe2 = 3.48e-26 * sT * t3, drHe2 = rHe2 * (0.5 * iT + lt3);
+  const double g = 1.24e-13 * div_nr(iT, sT) * t.e470;
+  const double di = g * (1.0 + 0.3 * t.e94);
+  const double ddi = g * ((470000.0 * iT2 - 1.5 * iT) * (1.0 + 0.3 * t.e94) + 0.3 * t.e94 * 94000.0 * iT2);
   // bremsstrahlung with the Gaunt factor 1.1 + 0.34 exp(-(5.5 - log10 T)^2 / 3)
-  const double lg = log10(T), w = exp(-(5.5 - lg) * (5.5 - lg) / 3.0);
-  const double gff = 1.1 + 0.34 * w, dgff = 0.34 * w * (2.0 * (5.5 - lg) / 3.0) / (T * 2.302585092994046);
-  const double br = 1.42e-27 * gff * sT, dbr = 1.42e-27 * (dgff * sT + 0.5 * gff / sT);
+  const double lg = t.lnT * kInvLn10, w = exp(-(5.5 - lg) * (5.5 - lg) * (1.0 / 3.0));
+  const double gff = 1.1 + 0.34 * w, dgff = 0.34 * w * (2.0 * (5.5 - lg) * (1.0 / 3.0)) * (iT * kInvLn10);
+  const double br = 1.42e-27 * gff * sT, dbr = 1.42e-27 * (dgff * sT + 0.5 * gff * div_nr(1.0, sT));
   CoolCoef c;
   c.k[0] = ceH + ciH;                    c.dk[0] = dceH + dciH;
   c.k[1] = rH + br;                      c.dk[1] = drH + dbr;
@@ -412,35 +412,38 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   const double c = P.c_red, yhe = P.y_he, nHe = yhe * nH;
   const bool recomb = P.flags & 1, coll = P.flags & 2;
   const double T = s[4 * B + 5];
-  const Rates rt = RateEval<false>::eval(T);
+  const TFns tfn = tfns(T);
+  const Rates rt = RateEval<false>::eval(tfn);
   const double aHII = recomb ? rt.aHII : 0.0, aHeII = recomb ? rt.aHeII : 0.0, aHeIII = recomb ? rt.aHeIII : 0.0;
   const double bHI = coll ? rt.bHI : 0.0, bHeI = coll ? rt.bHeI : 0.0, bHeII = coll ? rt.bHeII : 0.0;
   const double xHI = s[4 * B], xHII = s[4 * B + 1], yI = s[4 * B + 2], yII = s[4 * B + 3], yIII = s[4 * B + 4];
   const double ns0 = nH * xHI, ns1 = nHe * yI, ns2 = nHe * yII;
-  double kap[kMaxBins], den[kMaxBins], Nbar[kMaxBins];
+  // every quotient below by one refined reciprocal of its denominator
+  // (div_nr, within 0.51 ulp), as the forward FP64 path
+  double kap[kMaxBins], iden[kMaxBins], Nbar[kMaxBins];
   double Gm0 = 0, Gm1 = 0, Gm2 = 0;
   for (int b = 0; b < B; ++b) {
     kap[b] = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
-    den[b] = 1.0 + c * dt * kap[b];
-    Nbar[b] = s[b] / den[b];
+    iden[b] = div_nr(1.0, 1.0 + c * dt * kap[b]);
+    Nbar[b] = s[b] * iden[b];
     Gm0 += c * P.sigma[b][0] * Nbar[b];
     Gm1 += c * P.sigma[b][1] * Nbar[b];
     Gm2 += c * P.sigma[b][2] * Nbar[b];
   }
   const double ne0 = nH * xHII + nHe * (yII + 2.0 * yIII);
   const double aH = dt * (Gm0 + bHI * ne0), bH = dt * aHII * ne0;
-  const double D1 = 1.0 + aH + bH;
-  const double xHI1 = (xHI * (1.0 + bH) + bH * xHII) / D1;
-  const double xHII1 = (xHII * (1.0 + aH) + aH * xHI) / D1;
+  const double iD1 = div_nr(1.0, 1.0 + aH + bH);
+  const double xHI1 = (xHI * (1.0 + bH) + bH * xHII) * iD1;
+  const double xHII1 = (xHII * (1.0 + aH) + aH * xHI) * iD1;
   const double ne1 = nH * xHII1 + nHe * (yII + 2.0 * yIII);
   const double A = dt * (Gm1 + bHeI * ne1), Bb = dt * aHeII * ne1, Cc = dt * (Gm2 + bHeII * ne1),
                Dd = dt * aHeIII * ne1;
-  const double opA = 1.0 + A, opD = 1.0 + Dd;
-  const double num = yII + A * yI / opA + Dd * yIII / opD;
-  const double dn = 1.0 + Bb / opA + Cc / opD;
-  const double yII1 = num / dn;
-  const double yI1 = (yI + Bb * yII1) / opA;
-  const double yIII1 = (yIII + Cc * yII1) / opD;
+  const double iA = div_nr(1.0, 1.0 + A), iD = div_nr(1.0, 1.0 + Dd);
+  const double num = yII + A * yI * iA + Dd * yIII * iD;
+  const double idn = div_nr(1.0, 1.0 + Bb * iA + Cc * iD);
+  const double yII1 = num * idn;
+  const double yI1 = (yI + Bb * yII1) * iA;
+  const double yIII1 = (yIII + Cc * yII1) * iD;
   const double m0 = nH * xHI1, m1 = nHe * yI1, m2 = nHe * yII1;
   const double in_x[5] = {xHI, xHII, yI, yII, yIII};
   const double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
@@ -454,7 +457,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
     ntot0 = nH * (1.0 + yhe) + ne0;
     e0 = 1.5 * kBoltzmann * ntot0 * T;
     if (cool) {
-      cc = cooling_coef(T);
+      cc = cooling_coef(tfn);
       lamc = ne0 * (cc.k[0] * nsp[0] + cc.k[1] * nsp[1] + cc.k[2] * nsp[2] + cc.k[3] * nsp[3] + cc.k[4] * nsp[4]);
     }
     double heat_e = 0.0;
@@ -464,7 +467,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
                                       P.eps[b][2] * P.sigma[b][2] * m2);
     e1 = e0 + heat_e - dt * lamc;
     ntot1 = nH * (1.0 + yhe) + nH * xHII1 + nHe * (yII1 + 2.0 * yIII1);
-    T1 = e1 / (1.5 * kBoltzmann * ntot1);
+    T1 = div_nr(e1, 1.5 * kBoltzmann * ntot1);
   }
 
   double lx1[5], lxin[5] = {0, 0, 0, 0, 0};
@@ -472,8 +475,9 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   double lT0 = 0.0, le0 = 0.0, le1 = 0.0, lne0e = 0.0;
   if (thermal) {
     const double lT1 = lt[4 * B + 5];
-    le1 = lT1 / (1.5 * kBoltzmann * ntot1);
-    const double lnt1 = -lT1 * T1 / ntot1;
+    const double intot1 = div_nr(1.0, ntot1);
+    le1 = lT1 * (1.0 / (1.5 * kBoltzmann)) * intot1;
+    const double lnt1 = -lT1 * T1 * intot1;
     lx1[1] += lnt1 * nH;
     lx1[3] += lnt1 * nHe;
     lx1[4] += lnt1 * 2.0 * nHe;
@@ -494,15 +498,16 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
       if (r > best) { best = r; kb = k; }
     }
     if (best > 0 && kb == 5) {
-      const double mm = fabs(e0), sg = e1 > e0 ? 1.0 : -1.0;
-      le1 += lf * sg / mm;
-      le0 += -lf * sg / mm - lf * (fabs(e1 - e0) / mm / mm) * (e0 > 0 ? 1.0 : -1.0);
+      const double imm = div_nr(1.0, fabs(e0)), sg = e1 > e0 ? 1.0 : -1.0;
+      le1 += lf * sg * imm;
+      le0 += -lf * sg * imm - lf * (fabs(e1 - e0) * imm * imm) * (e0 > 0 ? 1.0 : -1.0);
     } else if (best > 0) {
       const double av = in_x[kb], bo = out_x[kb];
-      const double mm = fabs(av) > P.x_floor ? fabs(av) : P.x_floor;
+      const double imm = div_nr(1.0, fabs(av) > P.x_floor ? fabs(av) : P.x_floor);
       const double sg = bo > av ? 1.0 : -1.0;
-      lx1[kb] += lf * sg / mm;
-      lxin[kb] += -lf * sg / mm - lf * (fabs(bo - av) / mm / mm) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
+      lx1[kb] += lf * sg * imm;
+      lxin[kb] += -lf * sg * imm -
+                  lf * (fabs(bo - av) * imm * imm) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
     }
   }
   double lNbar[kMaxBins] = {0, 0, 0}, lm0 = 0, lm1 = 0, lm2 = 0;
@@ -549,7 +554,8 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
     double N1 = s[b] - rem;
     const bool clamped = N1 < 0;
     if (clamped) N1 = 0;
-    const double scale = s[b] > 0 ? N1 / s[b] : 0.0;
+    const double is = s[b] > 0 ? div_nr(1.0, s[b]) : 0.0;
+    const double scale = N1 * is;
     double lscale = 0.0;
     for (int k = 0; k < 3; ++k) {
       ls[B + 3 * b + k] += lt[B + 3 * b + k] * scale;
@@ -557,8 +563,8 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
     }
     double lN1 = lt[b];
     if (s[b] > 0) {
-      lN1 += lscale / s[b];
-      ls[b] -= lscale * (N1 / s[b]) / s[b];
+      lN1 += lscale * is;
+      ls[b] -= lscale * scale * is;
     }
     if (!clamped) {
       ls[b] += lN1;
@@ -577,26 +583,26 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   double lyII1 = lx1[3];
   const double lyI1 = lx1[2], lyIII1 = lx1[4];
   double lCc = 0, lBb = 0, lA = 0, lDd = 0, lopA = 0, lopD = 0;
-  lxin[4] += lyIII1 / opD;
-  lCc += lyIII1 * yII1 / opD;
-  lyII1 += lyIII1 * Cc / opD;
-  lopD -= lyIII1 * yIII1 / opD;
-  lxin[2] += lyI1 / opA;
-  lBb += lyI1 * yII1 / opA;
-  lyII1 += lyI1 * Bb / opA;
-  lopA -= lyI1 * yI1 / opA;
-  const double lnum = lyII1 / dn, ldn = -lyII1 * yII1 / dn;
-  lBb += ldn / opA;
-  lopA -= ldn * Bb / (opA * opA);
-  lCc += ldn / opD;
-  lopD -= ldn * Cc / (opD * opD);
+  lxin[4] += lyIII1 * iD;
+  lCc += lyIII1 * yII1 * iD;
+  lyII1 += lyIII1 * Cc * iD;
+  lopD -= lyIII1 * yIII1 * iD;
+  lxin[2] += lyI1 * iA;
+  lBb += lyI1 * yII1 * iA;
+  lyII1 += lyI1 * Bb * iA;
+  lopA -= lyI1 * yI1 * iA;
+  const double lnum = lyII1 * idn, ldn = -lyII1 * yII1 * idn;
+  lBb += ldn * iA;
+  lopA -= ldn * Bb * (iA * iA);
+  lCc += ldn * iD;
+  lopD -= ldn * Cc * (iD * iD);
   lxin[3] += lnum;
-  lA += lnum * yI / opA;
-  lxin[2] += lnum * A / opA;
-  lopA -= lnum * A * yI / (opA * opA);
-  lDd += lnum * yIII / opD;
-  lxin[4] += lnum * Dd / opD;
-  lopD -= lnum * Dd * yIII / (opD * opD);
+  lA += lnum * yI * iA;
+  lxin[2] += lnum * A * iA;
+  lopA -= lnum * A * yI * (iA * iA);
+  lDd += lnum * yIII * iD;
+  lxin[4] += lnum * Dd * iD;
+  lopD -= lnum * Dd * yIII * (iD * iD);
   lA += lopA;
   lDd += lopD;
   ldt += lA * (Gm1 + bHeI * ne1) + lBb * aHeII * ne1 + lCc * (Gm2 + bHeII * ne1) + lDd * aHeIII * ne1;
@@ -608,11 +614,11 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lnH += lne1 * (xHII1 + yhe * (yII + 2.0 * yIII));
   lxin[3] += lne1 * nHe;
   lxin[4] += lne1 * 2.0 * nHe;
-  const double lD1 = -(lxHI1 * xHI1 + lxHII1 * xHII1) / D1;
-  lxin[1] += lxHII1 * (1.0 + aH) / D1 + lxHI1 * bH / D1;
-  lxin[0] += lxHII1 * aH / D1 + lxHI1 * (1.0 + bH) / D1;
-  const double laH = lxHII1 * (xHII + xHI) / D1 + lD1;
-  const double lbH = lxHI1 * (xHI + xHII) / D1 + lD1;
+  const double lD1 = -(lxHI1 * xHI1 + lxHII1 * xHII1) * iD1;
+  lxin[1] += lxHII1 * (1.0 + aH) * iD1 + lxHI1 * bH * iD1;
+  lxin[0] += lxHII1 * aH * iD1 + lxHI1 * (1.0 + bH) * iD1;
+  const double laH = lxHII1 * (xHII + xHI) * iD1 + lD1;
+  const double lbH = lxHI1 * (xHI + xHII) * iD1 + lD1;
   ldt += laH * (Gm0 + bHI * ne0) + lbH * aHII * ne0;
   lG0 += laH * dt;
   const double lne0 = laH * dt * bHI + lbH * dt * aHII;
@@ -621,7 +627,7 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lxin[3] += lne0 * nHe;
   lxin[4] += lne0 * 2.0 * nHe;
   {
-    const RateSlopes d = rate_slopes(T, rt);
+    const RateSlopes d = rate_slopes(tfn, rt);
     if (coll) lT0 += laH * dt * d.bHI * ne0 + lA * dt * d.bHeI * ne1 + lCc * dt * d.bHeII * ne1;
     if (recomb) lT0 += lbH * dt * d.aHII * ne0 + lBb * dt * d.aHeII * ne1 + lDd * dt * d.aHeIII * ne1;
     lxin[1] += lne0e * nH;
@@ -632,8 +638,8 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   double lns0 = 0, lns1 = 0, lns2 = 0;
   for (int b = 0; b < B; ++b) {
     lNbar[b] += c * (P.sigma[b][0] * lG0 + P.sigma[b][1] * lG1 + P.sigma[b][2] * lG2);
-    ls[b] += lNbar[b] / den[b];
-    const double lden = -lNbar[b] * Nbar[b] / den[b];
+    ls[b] += lNbar[b] * iden[b];
+    const double lden = -lNbar[b] * Nbar[b] * iden[b];
     ldt += lden * c * kap[b];
     const double lkap = lden * c * dt;
     lns0 += lkap * P.sigma[b][0];

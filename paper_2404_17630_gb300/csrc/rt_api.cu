@@ -150,7 +150,6 @@ rt_status check_config(const rt_config* c) {
   if (c->gather_sum < 0 || c->gather_sum > 1) return fail(nullptr, RT_INVALID_ARG, "gather_sum must be 0 or 1");
   if (c->splitting < 0 || c->splitting > 1) return fail(nullptr, RT_INVALID_ARG, "splitting must be 0 or 1");
   if (c->time_order < 1 || c->time_order > 2) return fail(nullptr, RT_INVALID_ARG, "time_order must be 1 or 2");
-  if (c->split_kernels < 0 || c->split_kernels > 1) return fail(nullptr, RT_INVALID_ARG, "split_kernels must be 0 or 1");
   return RT_OK;
 }
 
@@ -344,30 +343,6 @@ void launch_chem(rt_ctx* ctx, double dt) {
   k_chem_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->shadow, w);
 }
 
-// Whether rt_step runs the flux application of a subcycle and the sources +
-// first chemistry attempt of the next as one kernel (k_gather_chem).
-bool fused_gather_chem(const rt_ctx* ctx) {
-  return ctx->gc_ok && !ctx->cfg.split_kernels && mixed(ctx) && comp_sum(ctx) && ctx->all_active &&
-         ctx->cfg.splitting == 0 && ctx->cfg.time_order == 1 && ctx->cfg.chem_mode > 0;
-}
-
-// Flux application over dt, then sources and chemistry of the next
-// subcycle (of the same length): the fused kernel, then the worklist pass.
-void launch_gather_chem(rt_ctx* ctx, double dt) {
-  ProfScope ps(ctx, RT_KERNEL_GATHER_CHEM);
-  const CellArgs ga = cell_args(ctx, dt, 1, 0, 0);
-  const CellArgs ca = cell_args(ctx, dt, 0, 1, 1);
-  const ChemParams P = chem_params(ctx);
-  const ChemWork w{ctx->work_cell, ctx->work_f1, ctx->work_ctl};
-  const int n_tiles = (ctx->C + kGcTile - 1) / kGcTile;
-  const int nb = std::min(2 * ctx->n_sm, (n_tiles + kGcTeams - 1) / kGcTeams);
-  k_gather_chem<<<nb, kGcThreads, 0, ctx->stream>>>(ga, ca, P, (const float4*)ctx->flux, ctx->shadow, w, n_tiles);
-  ctx->launches++;
-  const int t = 128;
-  const int nb2 = (int)std::min<long long>(nblk(ctx->C, t), ctx->n_sm);
-  k_chem_rest<<<nb2, t, 0, ctx->stream>>>(ca, P, ctx->shadow, w);
-}
-
 void launch_grad_any(rt_ctx* ctx) { mixed(ctx) ? launch_grad<float>(ctx) : launch_grad<double>(ctx); }
 void launch_flux_any(rt_ctx* ctx) { mixed(ctx) ? launch_flux<float>(ctx) : launch_flux<double>(ctx); }
 
@@ -438,13 +413,6 @@ rt_status rt_create(const rt_config* cfg, void* stream, rt_ctx** out) {
     l2 = 0;
   }
   ctx->l2_bytes = (size_t)l2;
-  // The fused flux application + chemistry kernel splits its registers
-  // between warpgroups (setmaxnreg) out of the allocation it is launched
-  // with: use it only if it was compiled with exactly that allocation.
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, k_gather_chem) == cudaSuccess)
-    ctx->gc_ok = fa.numRegs == kGcRegsLaunch && fa.maxThreadsPerBlock >= kGcThreads;
-  cudaGetLastError();
   *out = ctx;
   return RT_OK;
 }
@@ -899,24 +867,10 @@ rt_status rt_step(rt_ctx* ctx, double dt, int n_sub) {
   // Subcycle: sources + chemistry, gradients, fluxes, application (Lie);
   // Strang puts half the chemistry on each side of the transport.
   const bool strang = ctx->cfg.splitting == 1;
-  if (fused_gather_chem(ctx)) {
-    // the same launches with each flux application but the last fused with
-    // the next subcycle's sources and chemistry
-    launch_chem(ctx, dts);
-    for (int s = 0; s < n_sub; ++s) {
-      launch_grad_any(ctx);
-      launch_flux_any(ctx);
-      if (s + 1 < n_sub)
-        launch_gather_chem(ctx, dts);
-      else
-        launch_gather(ctx, dts, 0);
-    }
-  } else {
-    for (int s = 0; s < n_sub; ++s) {
-      launch_chem(ctx, strang ? 0.5 * dts : dts);
-      transport(ctx, dts);
-      if (strang) launch_chem(ctx, 0.5 * dts);
-    }
+  for (int s = 0; s < n_sub; ++s) {
+    launch_chem(ctx, strang ? 0.5 * dts : dts);
+    transport(ctx, dts);
+    if (strang) launch_chem(ctx, 0.5 * dts);
   }
   if (!capture) return launched(ctx, "rt_step");
   cudaGraph_t graph = nullptr;

@@ -18,7 +18,6 @@ struct rt_ctx {
   bool mesh_ready = false;
   int C = 0, F = 0, B = 0, max_deg = 0;
   int n_sm = 1;       // streaming multiprocessors of the device
-  bool gc_ok = false; // k_gather_chem compiled with the register count its warpgroup split assumes
   size_t l2_bytes = 0;  // L2 cache size of the device
   int grad_cap = 0;  // half-edge records of the largest gradient block (0: unstaged gradient kernel)
   double min_dx_cm = 0;

@@ -835,8 +835,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // otherwise each term widened and summed in FP64.  Pred: the face loads in
 // batches of four with a predicated last batch (no serial tail of single
 // loads) -- faster where the flux array is held in L2, slower where the
-// loads go to HBM and the extra registers cost occupancy.  k_gather and
-// k_gather_chem share it (and sub_flux), so the two round alike.
+// loads go to HBM and the extra registers cost occupancy. 
 template <class R, bool Comp, bool Pred>
 __device__ __forceinline__ void flux_sum(const CellArgs& a, const R4<R>* __restrict__ flux, int i, int b,
                                          double acc[4]) {
@@ -1100,145 +1099,6 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
       w.ctl[1] = 0;
       w.ctl[2] = 0;
       __threadfence();
-    }
-  }
-}
-
-// Flux application of subcycle s fused with the sources and the first
-// chemistry attempt of subcycle s + 1 (mixed precision, every cell active,
-// Lie splitting, forward-Euler transport).  The flux application is bound by
-// memory and the chemistry by GB300's FP64 unit; as two kernels they run one
-// after the other, here they run at the same time in every SM:
-//
-//   * a block is four warpgroups: warpgroup 0 runs the chemistry (one thread
-//     per cell), warpgroups 1-3 the flux application (one thread per
-//     (cell, bin), as k_gather);
-//   * four teams per block, team t = warp t of each warpgroup: 32 cells at
-//     a time; the three flux-application warps sum the fluxes of tile k + 1
-//     (and fetch its gas state) into a shared-memory slot while the
-//     chemistry warp works through tile k; a ring of kGcSlots slots per team,
-//     each with a "full" and an "empty" mbarrier;
-//   * the flux-application warpgroups give registers to the chemistry
-//     warpgroup (setmaxnreg: 48 and 104 of the 64 per thread the block is
-//     launched with; 3 x 128 x 48 + 128 x 104 = 31744 <= 512 x 64).
-//
-// The arithmetic of every cell is that of k_gather followed by k_chem_first
-// (the same device functions), so the results are bit for bit those of the
-// two kernels.  Rejected first attempts go to the worklist for k_chem_rest.
-// Every wait is bounded: a wait that gives up records kStTimeout and its
-// warp leaves (nothing is in flight).
-constexpr int kGcThreads = 512;
-constexpr int kGcTeams = 4;
-constexpr int kGcSlots = 2;
-constexpr int kGcTile = 32;
-constexpr int kGcRegsChem = 104, kGcRegsGather = 48, kGcRegsLaunch = 64;
-static_assert(128 * kGcRegsChem + 384 * kGcRegsGather <= kGcThreads * kGcRegsLaunch,
-              "register split above the block's launch allocation");
-
-struct GcSlot {
-  d4 U[kGcTile][kMaxBins];      // the cell's state after the flux application
-  double gas[7][kGcTile];       // n_H, x_HI, x_HII, y_HeI, y_HeII, y_HeIII, T
-  int src[kGcTile];             // source index of the cell, -1 for none
-};
-
-__global__ void __launch_bounds__(kGcThreads, 2)
-    k_gather_chem(CellArgs ga, CellArgs ca, ChemParams P, const float4* __restrict__ flux,
-                  float4* __restrict__ shadow, ChemWork w, int n_tiles) {
-  __shared__ GcSlot slot[kGcTeams][kGcSlots];
-  __shared__ __align__(8) uint64_t full[kGcTeams][kGcSlots], empty[kGcTeams][kGcSlots];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wg = warp >> 2, team = warp & 3;
-  const int B = ga.B;
-  if (threadIdx.x < kGcTeams * kGcSlots) {
-    const int tm = threadIdx.x / kGcSlots, sl = threadIdx.x % kGcSlots;
-    mbar_init(&full[tm][sl], 96);    // every thread of the team's three flux-application warps
-    mbar_init(&empty[tm][sl], 32);   // every thread of the team's chemistry warp
-  }
-  __syncthreads();
-  const int n_teams = gridDim.x * kGcTeams;
-  const int first = blockIdx.x * kGcTeams + team;
-  if (wg == 0) {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kGcRegsChem));
-    // chemistry: lane = cell of the tile
-    for (int k = 0, tile = first; tile < n_tiles; ++k, tile += n_teams) {
-      const int sl = k % kGcSlots;
-      GcSlot& S = slot[team][sl];
-      if (!mbar_wait(&full[team][sl], (uint32_t)((k / kGcSlots) & 1))) {
-        atomicOr(ca.status, kStTimeout);
-        return;
-      }
-      const int i = tile * kGcTile + lane;
-      if (i < ca.C) {
-        GasState s;
-        double Sc[kMaxBins];
-#pragma unroll
-        for (int b = 0; b < kMaxBins; ++b) {
-          Sc[b] = 1.0;
-          if (b < B) s.N[b] = S.U[lane][b].x;
-        }
-        if (ca.do_inject) {
-          const int si = S.src[lane];
-          if (si >= 0) inject_cell(ca, i, si, s.N);
-        }
-        s.xHI = S.gas[1][lane]; s.xHII = S.gas[2][lane]; s.yI = S.gas[3][lane]; s.yII = S.gas[4][lane];
-        s.yIII = S.gas[5][lane]; s.T = S.gas[6][lane];
-        float f1;
-        if (chemistry_mixed_first(P, S.gas[0][lane], ca.dt, s, Sc, &f1)) {
-          chem_store_mixed(ca, i, s, Sc, 1, true, shadow, S.U[lane]);
-        } else {
-          // rejected: the state after the flux application with the injected
-          // photons, for the second pass
-#pragma unroll
-          for (int b = 0; b < kMaxBins; ++b) {
-            if (b < B) {
-              const d4 u = S.U[lane][b];
-              ca.rad[(size_t)i * B + b] = make_d4(s.N[b], u.y, u.z, u.w);
-            }
-          }
-          const int q = atomicAdd(w.ctl, 1);
-          w.cell[q] = i;
-          w.f1[q] = f1;
-        }
-      }
-      mbar_arrive(&empty[team][sl]);
-    }
-  } else {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kGcRegsGather));
-    // flux application: thread q of the team = (cell q / B, bin q % B)
-    const int q = (wg - 1) * 32 + lane;
-    const int c = divb(q, ga.divB), b = q - c * B;
-    const bool gathers = q < kGcTile * B;
-    for (int k = 0, tile = first; tile < n_tiles; ++k, tile += n_teams) {
-      const int sl = k % kGcSlots;
-      GcSlot& S = slot[team][sl];
-      if (!mbar_wait(&empty[team][sl], (uint32_t)(((k / kGcSlots) & 1) ^ 1))) {
-        atomicOr(ga.status, kStTimeout);
-        return;
-      }
-      const int i0 = tile * kGcTile;
-      const int i = i0 + c;
-      if (gathers && i < ga.C) {
-        double acc[4];
-        flux_sum<float, true, false>(ga, flux, i, b, acc);
-        const double kfac = gather_kfac<float>(ga, i);
-        d4 u = ga.rad[(size_t)i * B + b];
-        sub_flux(u, kfac, acc);
-        if (!isfinite(u.x)) atomicOr(ga.status, kStNonFinite);
-        S.U[c][b] = u;
-      }
-      // the tile's gas state and source indices for the chemistry warp
-      const size_t C = ga.C;
-      for (int e = q; e < 8 * kGcTile; e += 96) {
-        const int cc = e & (kGcTile - 1), v = e >> 5;
-        const int ic = i0 + cc;
-        if (ic < ga.C) {
-          if (v == 0) S.gas[0][cc] = ca.nH[ic];
-          else if (v < 6) S.gas[v][cc] = ca.x5[(size_t)(v - 1) * C + ic];
-          else if (v == 6) S.gas[6][cc] = ca.T[ic];
-          else S.src[cc] = ca.do_inject ? ca.src_idx[ic] : -1;
-        }
-      }
-      mbar_arrive(&full[team][sl]);
     }
   }
 }

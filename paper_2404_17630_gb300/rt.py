@@ -56,7 +56,6 @@ class rt_config(ctypes.Structure):
         ("gather_sum", ctypes.c_int),
         ("splitting", ctypes.c_int),
         ("time_order", ctypes.c_int),
-        ("split_kernels", ctypes.c_int),
     ]
 
 
@@ -76,7 +75,7 @@ def make_config(**kw) -> rt_config:
     defaults = dict(n_bins=3, precision=RT_FP64, c_red=0.01 * 2.99792458e10, unit_length_cm=3.0856775814913673e21,
                     box=0.0, cfl=0.3, chem_mode=2, chem_flags=15, limiter=1, lim_eps=1e-5, order=2, f_s=0.05,
                     f_max=0.1, x_floor=1e-4, max_substeps=10000, y_he=0.0, gather_sum=0,
-                    splitting=0, time_order=1, split_kernels=0)
+                    splitting=0, time_order=1)
     defaults.update(kw)
     for k, v in defaults.items():
         if k in ("sigma", "eps"):
@@ -356,7 +355,7 @@ def rt_adjoint(ctx, dt, n_sub, checkpoint_every, lam_N=None, lam_F=None, lam_x5=
                                            o(dL_dQ), o(dL_dnH), o(lam0_N), o(lam0_F), o(lam0_x5), o(lam0_T)))
 
 
-RT_KERNEL_NAMES = ("k_chem", "k_grad", "k_flux", "k_gather", "k_gather_chem")
+RT_KERNEL_NAMES = ("k_chem", "k_grad", "k_flux", "k_gather")
 
 
 def rt_profile_enable(ctx, on=True):

@@ -504,34 +504,3 @@ def test_fp64_peak_measurement():
     assert abs(tf1 / tf2 - 1) < 0.1
     with pytest.raises(rtb.RTError):
         rtb.rt_fp64_peak(None, 0, 3)
-
-
-@pytest.mark.parametrize("n_bins", [3, 2, 1])
-def test_fused_gather_chem_bit_identical(n_bins):
-    """rt_step with the flux application fused with the next subcycle's
-    sources and first chemistry attempt (k_gather_chem; the default where it
-    applies) against separate kernels (split_kernels = 1): bit for bit, on a
-    mesh whose last 32-cell tile is ragged, with rejected first attempts
-    (second pass) and sources; the fused kernel did run."""
-    from paper_2404_17630_gb300 import rt as rtb
-    mesh, cfg, st = voronoi_case(n=13, n_bins=n_bins, n_src=6)
-    assert mesh.n_cells % 32 != 0
-    outs, prof = [], None
-    for split in (0, 1):
-        rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1, split_kernels=split)
-        dt = rt.max_dt() * 6
-        rt.step(dt, 6)
-        assert rt.sync() == 0
-        if split == 0:
-            rtb.rt_profile_enable(rt.ctx, True)
-            rt.step(dt, 6)
-            prof = rtb.rt_profile_read(rt.ctx, reset=True)
-            rtb.rt_profile_enable(rt.ctx, False)
-        else:
-            rt.step(dt, 6)
-        assert rt.sync() == 0
-        outs.append(rt.fields())
-    assert prof["k_gather_chem"][1] == 5 and prof["k_gather"][1] == 1 and prof["k_chem"][1] == 1
-    assert outs[0]["nsub"].max() > 1          # some first attempts were rejected
-    for k in outs[0]:
-        np.testing.assert_array_equal(outs[0][k], outs[1][k], err_msg=k)
