@@ -159,3 +159,13 @@ def test_source_hash_ignores_comments(tmp_path):
     f.write_text(f.read_text() + "\nint rt_unused_symbol;\n")
     assert bench.source_hash(str(root)) != h0
     assert bench.code_text("a = 1; // x\n/* y\n z */ b = 2;\n\n") == "a = 1;\n  b = 2;"
+
+
+def test_fp64_pipe_fraction():
+    """The FP64-instruction rate of an `alu` kernel over the DFMA stream's
+    instruction rate (peak FLOP / 2)."""
+    prof = {"k_chem": (13.4, 200), "k_grad": (11.0, 200), "k_flux": (11.6, 200), "k_gather": (9.0, 200)}
+    line, kern, _, _ = bench.roofline(_res(prof), "mixed", {"hbm_gbs": 6777.3}, "measured", PK, attempts=float(C2E5))
+    rate = 127.1 * C2E5 / (13.4e-3 / 200)
+    assert line["fp64_pipe_frac"] == pytest.approx(rate / (1.2e12 / 2), rel=1e-3)
+    assert line["fp64_pipe_frac"] > line["frac"]
