@@ -1268,6 +1268,7 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
       launch_chem(ctx, dts);
       CK(cudaMemcpyAsync(A.tp_rad_trans + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
                          ctx->stream), "tape");
+      if (s + 1 == s1) break;   // the segment's end state is not needed: the reverse starts from the tapes
       launch_grad_any(ctx);
       launch_flux_any(ctx);
       launch_gather(ctx, dts);
