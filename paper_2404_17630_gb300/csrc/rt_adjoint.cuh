@@ -675,7 +675,8 @@ struct ChemAdjArgs {
   double dt;              // subcycle length
   double lu3;
   int do_inject, do_chem;
-  int record;             // 0: count only, 1: write records
+  int record;             // 0: count only, 1: write records (at most count[i] per cell)
+  int* bad;               // record: set to 1 if a cell's attempts differ from count[i]
 };
 
 __device__ __forceinline__ void load_cell(const ChemAdjArgs& a, int i, CellState& s) {
@@ -696,8 +697,11 @@ __device__ __forceinline__ void load_cell(const ChemAdjArgs& a, int i, CellState
   }
 }
 
-// Re-run the attempts of the forward chemistry_cell<false>; count them, or
-// write their records.
+// Re-run the attempts of the forward chemistry (the same attempt and the
+// same controller arithmetic as chemistry() of the forward FP64 path); count
+// them, or write their records.  Recording writes at most count[i] records
+// (the count the forward recompute made) and flags a cell whose attempts
+// differ from it.
 __global__ void __launch_bounds__(128) k_chem_tape(ChemAdjArgs a, ChemParams P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.C) return;
@@ -707,32 +711,35 @@ __global__ void __launch_bounds__(128) k_chem_tape(ChemAdjArgs a, ChemParams P) 
   double rem = a.dt, dt = a.dt;
   int n = 0;
   ChemRec* out = a.record ? a.rec + a.off[i] : nullptr;
+  const int cap = a.record ? a.count[i] : 0;
   while (rem > 0) {
     if (n >= P.max_sub) { atomicOr(a.status, kStChemSubsteps); break; }
-    if (out) {
-      pack_state(s, a.B, out[n].s);
-      out[n].dt = dt;
-      out[n].rem = rem;
+    ChemRec* o = out && n < cap ? out + n : nullptr;
+    if (o) {
+      pack_state(s, a.B, o->s);
+      o->dt = dt;
+      o->rem = rem;
     }
     const double f = photochem_attempt(P, nH, dt, s, t);
-    if (out) out[n].f = f;
+    if (o) o->f = f;
     ++n;
     if (f > P.f_max) {
-      if (out) { out[n - 1].accepted = 0; out[n - 1].grow_is_ratio = 0; out[n - 1].clipped = 0; }
-      dt = dt * (P.f_s / f);
+      if (o) { o->accepted = 0; o->grow_is_ratio = 0; o->clipped = 0; }
+      dt = dt * div_nr(P.f_s, f);
       continue;
     }
     s = t;
     rem = (dt == rem) ? 0.0 : rem - dt;
-    double grow = (f > 0) ? P.f_s / f : 2.0;
+    double grow = (f > 0) ? div_nr(P.f_s, f) : 2.0;
     const int ratio = f > 0 && grow <= 2.0;
     if (grow > 2.0) grow = 2.0;
     const double dtn = dt * grow;
     const int clipped = dtn > rem;
     dt = clipped ? rem : dtn;
-    if (out) { out[n - 1].accepted = 1; out[n - 1].grow_is_ratio = ratio; out[n - 1].clipped = clipped; }
+    if (o) { o->accepted = 1; o->grow_is_ratio = ratio; o->clipped = clipped; }
   }
   if (!a.record) a.count[i] = n;
+  else if (n != cap) atomicOr(a.bad, 1);
 }
 
 // Reverse over the recorded attempts of one cell, then the source term.

@@ -1104,6 +1104,7 @@ rt_status adj_prepare(rt_ctx* ctx, int nseg, int k) {
   AA(A.lam_rad, C * B); AA(A.lam_part, C * B); AA(A.lam_in, C * B); AA(A.lampre, F * B * 2); AA(A.lamr, C * B * 3);
   AA(A.lam_x5, 5 * C); AA(A.lam_T, C); AA(A.lam_nH, C); AA(A.lam_S, B * C); AA(A.lim_coef, C * B * 4);
   AA(A.lim_cell, C * B * 4); AA(A.count, C); AA(A.chem_off, C + 1);
+  AA(A.cnt_slot, (size_t)k * C); AA(A.tape_bad, 1);
 #undef AA
   A.nseg = nseg;
   A.k = k;
@@ -1149,6 +1150,7 @@ ChemAdjArgs chem_adj_args(rt_ctx* ctx, const d4* rad, const double* x5, const do
   a.do_inject = ctx->n_src_cells > 0;
   a.do_chem = ctx->cfg.chem_mode > 0;
   a.record = 0;
+  a.bad = ctx->adj.tape_bad;
   return a;
 }
 
@@ -1178,28 +1180,47 @@ rt_status adj_subcycle(rt_ctx* ctx, int slot, double dts) {
   ChemAdjArgs ca = chem_adj_args(ctx, pc_rad, pc_x5, pc_T, dts);
   const int t = 128;
   if (ca.do_chem) {
-    k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
-    CK(cudaMemsetAsync(ctx->stage, 0, sizeof(int), ctx->stream), "scan");
-    k_scan_counts<<<1, 1024, 0, ctx->stream>>>((int)C, A.count, A.chem_off, (int*)ctx->stage);
-    int32_t total = 0, ovf = 0;
-    CK(cudaMemcpyAsync(&total, A.chem_off + C, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
-    CK(cudaMemcpyAsync(&ovf, ctx->stage, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
-    CK(cudaStreamSynchronize(ctx->stream), "scan");
-    if (ovf) return fail(ctx, RT_OOM, "adjoint: chemistry tape exceeds 2^31 attempts");
-    if ((size_t)total > A.rec_cap) {
-      if (A.rec) {
-        cudaFree(A.rec);
-        A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.rec));
+    // offsets from the attempt counts of the recompute's chemistry of this
+    // subcycle, records written by the tape (the same attempts); should a
+    // cell's attempts differ from that count, the tape is laid out again
+    // from a counting pass of its own
+    for (int pass = 0; pass < 2; ++pass) {
+      const int32_t* cnt = A.cnt_slot + (size_t)slot * C;
+      if (pass == 1) {
+        ca.record = 0;
+        ca.count = A.count;
+        k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
+        cnt = A.count;
       }
-      size_t cap = std::max<size_t>((size_t)total + total / 4, 1024);
-      ChemRec* r = nullptr;
-      if ((st = aalloc(ctx, &r, cap, "chemistry tape"))) return st;
-      A.rec = r;
-      A.rec_cap = cap;
+      CK(cudaMemsetAsync(ctx->stage, 0, sizeof(int), ctx->stream), "scan");
+      k_scan_counts<<<1, 1024, 0, ctx->stream>>>((int)C, cnt, A.chem_off, (int*)ctx->stage);
+      int32_t total = 0, ovf = 0;
+      CK(cudaMemcpyAsync(&total, A.chem_off + C, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
+      CK(cudaMemcpyAsync(&ovf, ctx->stage, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
+      CK(cudaStreamSynchronize(ctx->stream), "scan");
+      if (ovf) return fail(ctx, RT_OOM, "adjoint: chemistry tape exceeds 2^31 attempts");
+      if ((size_t)total > A.rec_cap) {
+        if (A.rec) {
+          cudaFree(A.rec);
+          A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.rec));
+        }
+        size_t cap = std::max<size_t>((size_t)total + total / 4, 1024);
+        ChemRec* r = nullptr;
+        if ((st = aalloc(ctx, &r, cap, "chemistry tape"))) return st;
+        A.rec = r;
+        A.rec_cap = cap;
+      }
+      ca.rec = (ChemRec*)A.rec;
+      ca.record = 1;
+      ca.count = const_cast<int32_t*>(cnt);
+      CK(cudaMemsetAsync(A.tape_bad, 0, sizeof(int), ctx->stream), "tape");
+      k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
+      int bad = 0;
+      CK(cudaMemcpyAsync(&bad, A.tape_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "tape");
+      CK(cudaStreamSynchronize(ctx->stream), "tape");
+      if (!bad) break;
+      if (pass == 1) return fail(ctx, RT_CUDA, "adjoint: the chemistry tape does not repeat its own attempts");
     }
-    ca.rec = (ChemRec*)A.rec;
-    ca.record = 1;
-    k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
   }
   k_chem_adj<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
   return launched(ctx, "adjoint chemistry");
@@ -1268,6 +1289,9 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
       launch_chem(ctx, dts);
       CK(cudaMemcpyAsync(A.tp_rad_trans + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
                          ctx->stream), "tape");
+      if (ctx->cfg.chem_mode > 0)   // the attempts per cell, for the tape's layout
+        CK(cudaMemcpyAsync(A.cnt_slot + (size_t)slot * C, ctx->nsub, C * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                           ctx->stream), "tape");
       if (s + 1 == s1) break;   // the segment's end state is not needed: the reverse starts from the tapes
       launch_grad_any(ctx);
       launch_flux_any(ctx);

@@ -112,6 +112,8 @@ struct rt_ctx {
     d4 *lam_rad = nullptr, *lam_part = nullptr, *lam_in = nullptr, *lampre = nullptr, *lamr = nullptr;
     double *lam_x5 = nullptr, *lam_T = nullptr, *lam_nH = nullptr, *lam_S = nullptr, *lim_coef = nullptr;
     int32_t *lim_cell = nullptr, *count = nullptr, *chem_off = nullptr;
+    int32_t* cnt_slot = nullptr;   // [k][C] attempts per cell of each recomputed subcycle of a segment
+    int* tape_bad = nullptr;       // set by the tape when a cell's attempts differ from cnt_slot
     void* rec = nullptr;
     std::vector<void*> allocs;
   } adj;
