@@ -193,11 +193,11 @@ def test_fullsize_thesan_2M():
 
 @pytest.mark.slow
 def test_fullsize_thesan_16M():
-    """256^3 = 16,777,216 cells (the large-throughput box): mixed, element by
-    element after one subcycle (the oracle holds ~35 GB of host memory for
-    this mesh), and the invariants."""
+    """256^3 = 16,777,216 cells (the large-throughput box): FP64 and mixed,
+    element by element after one subcycle (the oracle holds ~35 GB of host
+    memory for this mesh), and the invariants (mixed)."""
     mesh, cfg, st = synth.thesan_like(256, 10, 32768, 7160.0, 256)
     if _host_gb_available() < 120:
         pytest.skip(f"element-wise check needs ~120 GB of host memory, {_host_gb_available():.0f} GB available")
-    _elementwise(mesh, cfg, st, ("mixed",), 1, 41)
+    _elementwise(mesh, cfg, st, ("fp64", "mixed"), 1, 41)
     _check(mesh, cfg, ("mixed",), 41)
