@@ -175,13 +175,17 @@ __device__ __forceinline__ void st8(f8* p, float a0, float a1, float a2, float a
 }
 
 // Gradient records.  FP64 sweep: 12 words per (cell, bin), component q's
-// gradient at q*3 + d.  FP32 sweep, cell-major: per cell four groups -- the
-// 12 gradient words as three float4, then the cell state (N, f) the
-// gradients were taken of -- each group holding the bins side by side, with
-// 3 bins padded to 4 so that a group is one aligned 64-byte block: a face
-// kernel load then touches one cache line per cell.
+// gradient at q*3 + d.  FP32 sweep, cell-major: per cell four groups g of
+// one float4 each -- the 12 gradient words as three float4, then the cell
+// state (N, f) the gradients were taken of -- for every bin, 3 bins padded
+// to 4.  Groups 0-1 of all bins fill one 128-byte line and groups 2-3 the
+// next, each bin's pair of groups adjacent (32 bytes): the gradient kernel
+// writes a (cell, bin)'s record as two whole 32-byte sectors, and a face
+// kernel load of one group for the three bins of a face stays in one line.
 __host__ __device__ constexpr int pad_bins(int B) { return B == 3 ? 4 : B; }
-__host__ __device__ inline size_t grec(int i, int g, int b, int Bp) { return ((size_t)i * 4 + g) * Bp + b; }
+__host__ __device__ inline size_t grec(int i, int g, int b, int Bp) {
+  return (size_t)i * 4 * Bp + (size_t)(g >> 1) * 2 * Bp + 2 * b + (g & 1);
+}
 
 // Mesh geometry in the sweep precision R, plus FP64 cell data.
 template <class R> struct Geo {

@@ -617,11 +617,12 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
       if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
     }
   }
+  // groups 0-1 and 2-3 as two 32-byte stores
   float4* G4 = reinterpret_cast<float4*>(G);
-  G4[grec(i, 0, b, g.Bp)] = make_float4(gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0], gr[1][0] * psi[1]);
-  G4[grec(i, 1, b, g.Bp)] = make_float4(gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
-  G4[grec(i, 2, b, g.Bp)] = make_float4(gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3], gr[3][2] * psi[3]);
-  G4[grec(i, 3, b, g.Bp)] = pi;
+  st8(reinterpret_cast<f8*>(G4 + grec(i, 0, b, g.Bp)), gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0],
+      gr[1][0] * psi[1], gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
+  st8(reinterpret_cast<f8*>(G4 + grec(i, 2, b, g.Bp)), gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3],
+      gr[3][2] * psi[3], pi.x, pi.y, pi.z, pi.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -731,7 +732,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 1) k_flux(Geo<R> g, 
   t = f * B + b;
   if constexpr (sizeof(R) == 4) {
     // FP32 sweep: one 32-byte and one 16-byte face record, then the four
-    // groups (gradients, state) of each side's cell-major record
+    // groups (gradients, state) of each side's cell-major record (16-byte
+    // loads: as two 32-byte loads they need more registers than the
+    // kernel's 32, and were measured slower)
     const f8 a = ld8(g.fa + f);
     const float4 xr = __ldg(g.fb + f);
     const float4* G4 = reinterpret_cast<const float4*>(G);
