@@ -1071,6 +1071,7 @@ __global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, fl
 __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, float4* __restrict__ shadow,
                                                    ChemWork w) {
   const int total = *(volatile int*)w.ctl;
+  if (total == 0) return;   // nothing was rejected: the worklist's counters are all zero already
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int n_warps = gridDim.x * (blockDim.x >> 5);
   // static first chunk: warp-in-block major, so that consecutive chunks lie
@@ -1176,6 +1177,7 @@ __global__ void __launch_bounds__(128) k_chem64_first(CellArgs a, ChemParams P, 
 __global__ void __launch_bounds__(128) k_chem64_rest(CellArgs a, ChemParams P, const int32_t* __restrict__ work_cell,
                                                      const double* __restrict__ work_f1, int* work_ctl) {
   const int total = *(volatile int*)work_ctl;
+  if (total == 0) return;   // nothing was rejected: the worklist's counters are all zero already
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int n_warps = gridDim.x * (blockDim.x >> 5);
   int chunk = wib * gridDim.x + blockIdx.x;
