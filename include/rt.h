@@ -198,8 +198,14 @@ rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
  * of Sec. 4.1.1, gradients and limiter on their active branch, M1 face
  * fluxes, flux application).  Starting from the context's current state it
  * runs the step (leaving the final state, as rt_step does), keeping a full
- * checkpoint every checkpoint_every subcycles, then walks back segment by
- * segment, recomputing each segment's tape.
+ * checkpoint every checkpoint_every subcycles and recording the last
+ * segment on the way, then walks back segment by segment, recording each
+ * earlier segment again from its checkpoint.  The record of a segment is the
+ * state entering each subcycle's chemistry and transport, and every
+ * chemistry attempt of the cells whose first attempt was rejected, written
+ * by the forward's own worklist pass.  The reverse of those attempts runs
+ * their cotangent-independent part in parallel over a subcycle's records,
+ * then each cell's serial chain.
  * In (cotangents of the final fields, caller layout, NULL = zero):
  *   lam_N[B*C], lam_F[3*B*C] (w.r.t. F, photons cm^-2 s^-1), lam_x5[5*C], lam_T[C].
  * Out (NULL = not wanted): dL_dQ[n_src*B] per source of the last
@@ -209,6 +215,15 @@ rt_status rt_stage_chemistry(rt_ctx *ctx, double dt);
 rt_status rt_adjoint(rt_ctx *ctx, double dt, int n_sub, int checkpoint_every, const double *lam_N,
                      const double *lam_F, const double *lam_x5, const double *lam_T, double *dL_dQ,
                      double *dL_dnH, double *lam0_N, double *lam0_F, double *lam0_x5, double *lam0_T);
+
+/* The chemistry tape of the last rt_adjoint call on ctx (all 0 before the
+ * first): max_records = the most chemistry records one segment held (one
+ * per attempt of each cell whose first attempt was rejected), capacity =
+ * the tape's size in records (176 bytes each; it grows, and stays grown,
+ * when a subcycle overflows it), redone = subcycle chemistries recorded
+ * again after the tape grew.  NULL outputs are skipped; RT_INVALID_ARG for
+ * a NULL ctx. */
+rt_status rt_adjoint_tape_info(rt_ctx *ctx, long long *max_records, long long *capacity, int *redone);
 
 /* Per-kernel timing: with profiling on, every kernel that rt_step and the
  * stage entry points launch is bracketed by CUDA events on the context's

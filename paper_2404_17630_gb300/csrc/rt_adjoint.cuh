@@ -12,11 +12,10 @@
 //   k_adj_cellsum   per (cell, bin): the least-squares right-hand side and
 //                   the limiter extremes read neighbour values; their
 //                   cotangents are gathered here from the neighbours' records
-//   k_chem_count / k_chem_record / k_chem_adj
-//                   per cell: re-run the chemistry attempts of one subcycle,
-//                   lay them out in a tape, walk back through them together
-//                   with the substep controller (Sec. 4.1.1) and the source
-//                   term.
+//   k_chem_adj      per cell: walk back through the chemistry attempts of one
+//                   subcycle, as the recompute's worklist pass recorded them
+//                   (k_chem64_rest<true>), together with the substep
+//                   controller (Sec. 4.1.1) and the source term.
 #pragma once
 #include "rt_kernels.cuh"
 
@@ -306,32 +305,6 @@ __global__ void __launch_bounds__(256) k_adj_cellsum(AdjArgs a) {
 // chemistry (FP64; isothermal or with thermal energy)
 // ---------------------------------------------------------------------------
 
-constexpr int kNv = 4 * kMaxBins + 6;
-
-struct ChemRec {
-  double s[kNv];     // state entering the attempt (N[B], f[3B], xHI, xHII, yI, yII, yIII, T)
-  double dt, rem, f;
-  int accepted, grow_is_ratio, clipped, pad;
-};
-
-__device__ __forceinline__ void pack_state(const CellState& c, int B, double* s) {
-  for (int b = 0; b < B; ++b) {
-    s[b] = c.N[b];
-    s[B + 3 * b] = c.f[b][0]; s[B + 3 * b + 1] = c.f[b][1]; s[B + 3 * b + 2] = c.f[b][2];
-  }
-  s[4 * B] = c.xHI; s[4 * B + 1] = c.xHII; s[4 * B + 2] = c.yI; s[4 * B + 3] = c.yII; s[4 * B + 4] = c.yIII;
-  s[4 * B + 5] = c.T;
-}
-
-__device__ __forceinline__ void unpack_state(const double* s, int B, CellState& c) {
-  for (int b = 0; b < B; ++b) {
-    c.N[b] = s[b];
-    c.f[b][0] = s[B + 3 * b]; c.f[b][1] = s[B + 3 * b + 1]; c.f[b][2] = s[B + 3 * b + 2];
-  }
-  c.xHI = s[4 * B]; c.xHII = s[4 * B + 1]; c.yI = s[4 * B + 2]; c.yII = s[4 * B + 3]; c.yIII = s[4 * B + 4];
-  c.T = s[4 * B + 5];
-}
-
 // Temperature derivatives of the rate fits (RateEval<false>) for the
 // reverse mode of the thermal network, from the same functions of T the
 // fits use (TFns: one logarithm, the shared Boltzmann factors).  The Hui &
@@ -402,166 +375,251 @@ __device__ CoolCoef cooling_coef(const TFns& t) {
   return c;
 }
 
-// Reverse of one attempt (photochem_attempt): lt = cotangent of the
-// output state, lf = of the substep measure; accumulates into ls (input
-// state, T included: through the rate fits, and in mode 2 the energy
-// equation), ldt, lnH.
-__device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const double* s, const double* lt, double lf,
-                            double* ls, double& ldt, double& lnH) {
-  const int B = P.B;
+// Reverse of one attempt (photochem_attempt), in two parts.  attempt_lin
+// computes what does not depend on the cotangents: the attempt's
+// intermediate values, the rate fits and their slopes in T, the cooling
+// coefficients, the quotients, and the branch the substep measure took.
+// attempt_back takes lt = cotangent of the output state and lf = of the
+// measure, and accumulates into ls (input state, T included: through the
+// rate fits, and in mode 2 the energy equation), ldt and lnH; it is linear
+// in (lt, lf).  A cell's attempts are a serial chain in the reverse as in
+// the forward, but their attempt_lin parts are independent and run in
+// parallel over a subcycle's records (k_chem_lin); the chain then runs
+// attempt_back only.  kB = the number of bins (compile-time: the state
+// arrays stay in registers).  Every quotient by one refined reciprocal of
+// its denominator (div_nr, within 0.51 ulp), as the forward FP64 path.
+struct AttemptLin {
+  double aHII, aHeII, aHeIII, bHI, bHeI, bHeII;   // the rates, zero where the flags switch them off
+  RateSlopes d;                                   // their slopes in T
+  CoolCoef cc;                                    // mode 2 with cooling
+  double kap[kMaxBins], iden[kMaxBins], Nbar[kMaxBins], is[kMaxBins];
+  double Gm0, Gm1, Gm2;
+  double ne0, aH, bH, iD1, xHI1, xHII1, ne1, A, Bb, Cc, Dd, iA, iD, idn, yII1, yI1, yIII1, m0, m1, m2;
+  double ntot0, lamc, ntot1, T1, intot1;           // mode 2
+  double f_sg, f_imm, f_span, f_sgn;               // the measure's largest term: sign of the change, 1/|base|,
+                                                   // |change| / base^2, sign of the base (0: at the floor)
+  int f_kb;                                        // which term: 0-4 abundances, 5 energy, -1 none (f = 0)
+  int pad;
+};
+
+// measure = false: the attempt's measure carries no cotangent (the last
+// attempt of a cell), so its branch is not needed.
+template <int kB>
+__device__ __forceinline__ void attempt_lin(const ChemParams& P, double nH, double dt, const double* s,
+                                            AttemptLin& L, bool measure) {
   const double c = P.c_red, yhe = P.y_he, nHe = yhe * nH;
   const bool recomb = P.flags & 1, coll = P.flags & 2;
-  const double T = s[4 * B + 5];
+  const double T = s[4 * kB + 5];
   const TFns tfn = tfns(T);
   const Rates rt = RateEval<false>::eval(tfn);
-  const double aHII = recomb ? rt.aHII : 0.0, aHeII = recomb ? rt.aHeII : 0.0, aHeIII = recomb ? rt.aHeIII : 0.0;
-  const double bHI = coll ? rt.bHI : 0.0, bHeI = coll ? rt.bHeI : 0.0, bHeII = coll ? rt.bHeII : 0.0;
-  const double xHI = s[4 * B], xHII = s[4 * B + 1], yI = s[4 * B + 2], yII = s[4 * B + 3], yIII = s[4 * B + 4];
+  L.aHII = recomb ? rt.aHII : 0.0; L.aHeII = recomb ? rt.aHeII : 0.0; L.aHeIII = recomb ? rt.aHeIII : 0.0;
+  L.bHI = coll ? rt.bHI : 0.0; L.bHeI = coll ? rt.bHeI : 0.0; L.bHeII = coll ? rt.bHeII : 0.0;
+  L.d = rate_slopes(tfn, rt);
+  const double xHI = s[4 * kB], xHII = s[4 * kB + 1], yI = s[4 * kB + 2], yII = s[4 * kB + 3],
+               yIII = s[4 * kB + 4];
   const double ns0 = nH * xHI, ns1 = nHe * yI, ns2 = nHe * yII;
-  // every quotient below by one refined reciprocal of its denominator
-  // (div_nr, within 0.51 ulp), as the forward FP64 path
-  double kap[kMaxBins], iden[kMaxBins], Nbar[kMaxBins];
   double Gm0 = 0, Gm1 = 0, Gm2 = 0;
-  for (int b = 0; b < B; ++b) {
-    kap[b] = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
-    iden[b] = div_nr(1.0, 1.0 + c * dt * kap[b]);
-    Nbar[b] = s[b] * iden[b];
-    Gm0 += c * P.sigma[b][0] * Nbar[b];
-    Gm1 += c * P.sigma[b][1] * Nbar[b];
-    Gm2 += c * P.sigma[b][2] * Nbar[b];
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
+    L.kap[b] = P.sigma[b][0] * ns0 + P.sigma[b][1] * ns1 + P.sigma[b][2] * ns2;
+    L.iden[b] = div_nr(1.0, 1.0 + c * dt * L.kap[b]);
+    L.Nbar[b] = s[b] * L.iden[b];
+    Gm0 += c * P.sigma[b][0] * L.Nbar[b];
+    Gm1 += c * P.sigma[b][1] * L.Nbar[b];
+    Gm2 += c * P.sigma[b][2] * L.Nbar[b];
+    L.is[b] = s[b] > 0 ? div_nr(1.0, s[b]) : 0.0;
   }
+  L.Gm0 = Gm0; L.Gm1 = Gm1; L.Gm2 = Gm2;
   const double ne0 = nH * xHII + nHe * (yII + 2.0 * yIII);
-  const double aH = dt * (Gm0 + bHI * ne0), bH = dt * aHII * ne0;
+  const double aH = dt * (Gm0 + L.bHI * ne0), bH = dt * L.aHII * ne0;
   const double iD1 = div_nr(1.0, 1.0 + aH + bH);
   const double xHI1 = (xHI * (1.0 + bH) + bH * xHII) * iD1;
   const double xHII1 = (xHII * (1.0 + aH) + aH * xHI) * iD1;
   const double ne1 = nH * xHII1 + nHe * (yII + 2.0 * yIII);
-  const double A = dt * (Gm1 + bHeI * ne1), Bb = dt * aHeII * ne1, Cc = dt * (Gm2 + bHeII * ne1),
-               Dd = dt * aHeIII * ne1;
+  const double A = dt * (Gm1 + L.bHeI * ne1), Bb = dt * L.aHeII * ne1, Cc = dt * (Gm2 + L.bHeII * ne1),
+               Dd = dt * L.aHeIII * ne1;
   const double iA = div_nr(1.0, 1.0 + A), iD = div_nr(1.0, 1.0 + Dd);
   const double num = yII + A * yI * iA + Dd * yIII * iD;
   const double idn = div_nr(1.0, 1.0 + Bb * iA + Cc * iD);
   const double yII1 = num * idn;
   const double yI1 = (yI + Bb * yII1) * iA;
   const double yIII1 = (yIII + Cc * yII1) * iD;
+  L.ne0 = ne0; L.aH = aH; L.bH = bH; L.iD1 = iD1; L.xHI1 = xHI1; L.xHII1 = xHII1; L.ne1 = ne1;
+  L.A = A; L.Bb = Bb; L.Cc = Cc; L.Dd = Dd; L.iA = iA; L.iD = iD; L.idn = idn;
+  L.yII1 = yII1; L.yI1 = yI1; L.yIII1 = yIII1;
   const double m0 = nH * xHI1, m1 = nHe * yI1, m2 = nHe * yII1;
-  const double in_x[5] = {xHI, xHII, yI, yII, yIII};
-  const double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
+  L.m0 = m0; L.m1 = m1; L.m2 = m2;
   // thermal energy (mode 2): e0 = 3/2 k n_tot0 T, e1 = e0 + heat - dt Lambda,
   // T1 = e1 / (3/2 k n_tot1)
   const bool thermal = P.mode == 2, cool = P.flags & 4, heat = P.flags & 8;
-  const double nsp[5] = {nH * xHI, nH * xHII, nHe * yI, nHe * yII, nHe * yIII};
-  double ntot0 = 0.0, e0 = 0.0, lamc = 0.0, e1 = 0.0, ntot1 = 0.0, T1 = T;
-  CoolCoef cc;
+  double e0 = 0.0, e1 = 0.0;
+  L.ntot0 = L.lamc = L.ntot1 = L.intot1 = 0.0;
+  L.T1 = T;
   if (thermal) {
-    ntot0 = nH * (1.0 + yhe) + ne0;
-    e0 = 1.5 * kBoltzmann * ntot0 * T;
+    const double nsp[5] = {nH * xHI, nH * xHII, nHe * yI, nHe * yII, nHe * yIII};
+    L.ntot0 = nH * (1.0 + yhe) + ne0;
+    e0 = 1.5 * kBoltzmann * L.ntot0 * T;
     if (cool) {
-      cc = cooling_coef(tfn);
-      lamc = ne0 * (cc.k[0] * nsp[0] + cc.k[1] * nsp[1] + cc.k[2] * nsp[2] + cc.k[3] * nsp[3] + cc.k[4] * nsp[4]);
+      L.cc = cooling_coef(tfn);
+      L.lamc = ne0 * (L.cc.k[0] * nsp[0] + L.cc.k[1] * nsp[1] + L.cc.k[2] * nsp[2] + L.cc.k[3] * nsp[3] +
+                      L.cc.k[4] * nsp[4]);
     }
     double heat_e = 0.0;
     if (heat)
-      for (int b = 0; b < B; ++b)
-        heat_e += c * dt * Nbar[b] * (P.eps[b][0] * P.sigma[b][0] * m0 + P.eps[b][1] * P.sigma[b][1] * m1 +
-                                      P.eps[b][2] * P.sigma[b][2] * m2);
-    e1 = e0 + heat_e - dt * lamc;
-    ntot1 = nH * (1.0 + yhe) + nH * xHII1 + nHe * (yII1 + 2.0 * yIII1);
-    T1 = div_nr(e1, 1.5 * kBoltzmann * ntot1);
+#pragma unroll
+      for (int b = 0; b < kB; ++b)
+        heat_e += c * dt * L.Nbar[b] * (P.eps[b][0] * P.sigma[b][0] * m0 + P.eps[b][1] * P.sigma[b][1] * m1 +
+                                        P.eps[b][2] * P.sigma[b][2] * m2);
+    e1 = e0 + heat_e - dt * L.lamc;
+    L.ntot1 = nH * (1.0 + yhe) + nH * xHII1 + nHe * (yII1 + 2.0 * yIII1);
+    L.T1 = div_nr(e1, 1.5 * kBoltzmann * L.ntot1);
+    L.intot1 = div_nr(1.0, L.ntot1);
   }
+  // the largest term of the substep measure and its slope's factors
+  L.f_sg = L.f_imm = L.f_span = L.f_sgn = 0.0;
+  L.f_kb = -1;
+  if (!measure) return;
+  const double in_x[5] = {xHI, xHII, yI, yII, yIII};
+  const double out_x[5] = {xHI1, xHII1, yI1, yII1, yIII1};
+  const int nk = yhe > 0 ? 5 : 2;
+  double best = -1.0;
+  int kb = -1;
+  if (thermal) {
+    best = rel_change(e0, e1, 0.0);
+    kb = 5;
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (k < nk) {
+      const double r = rel_change(in_x[k], out_x[k], P.x_floor);
+      if (r > best) { best = r; kb = k; }
+    }
+  }
+  if (best > 0 && kb == 5) {
+    const double imm = div_nr(1.0, fabs(e0));
+    L.f_kb = 5;
+    L.f_imm = imm;
+    L.f_sg = e1 > e0 ? 1.0 : -1.0;
+    L.f_span = fabs(e1 - e0) * imm * imm;
+    L.f_sgn = e0 > 0 ? 1.0 : -1.0;
+  } else if (best > 0) {
+    double av = 0.0, bo = 0.0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k == kb) { av = in_x[k]; bo = out_x[k]; }
+    const double imm = div_nr(1.0, fabs(av) > P.x_floor ? fabs(av) : P.x_floor);
+    L.f_kb = kb;
+    L.f_imm = imm;
+    L.f_sg = bo > av ? 1.0 : -1.0;
+    L.f_span = fabs(bo - av) * imm * imm;
+    L.f_sgn = fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0;
+  }
+}
+
+// lt == nullptr: the output state carries no cotangent (a rejected
+// attempt, whose result is discarded); only lf does.
+template <int kB>
+__device__ __forceinline__ void attempt_back(const ChemParams& P, double nH, double dt, const double* s,
+                                             const AttemptLin& L, const double* lt, double lf, double* ls,
+                                             double& ldt, double& lnH) {
+  const double c = P.c_red, yhe = P.y_he, nHe = yhe * nH;
+  const bool recomb = P.flags & 1, coll = P.flags & 2;
+  const double T = s[4 * kB + 5];
+  const double xHI = s[4 * kB], xHII = s[4 * kB + 1], yI = s[4 * kB + 2], yII = s[4 * kB + 3],
+               yIII = s[4 * kB + 4];
+  const double ne0 = L.ne0, aH = L.aH, bH = L.bH, iD1 = L.iD1, xHI1 = L.xHI1, xHII1 = L.xHII1, ne1 = L.ne1;
+  const double A = L.A, Bb = L.Bb, Cc = L.Cc, Dd = L.Dd, iA = L.iA, iD = L.iD, idn = L.idn;
+  const double yII1 = L.yII1, yI1 = L.yI1, yIII1 = L.yIII1, m0 = L.m0, m1 = L.m1, m2 = L.m2;
+  const bool thermal = P.mode == 2, cool = P.flags & 4, heat = P.flags & 8;
 
   double lx1[5], lxin[5] = {0, 0, 0, 0, 0};
-  for (int q = 0; q < 5; ++q) lx1[q] = lt[4 * B + q];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) lx1[q] = lt ? lt[4 * kB + q] : 0.0;
   double lT0 = 0.0, le0 = 0.0, le1 = 0.0, lne0e = 0.0;
+  const double lT1 = lt ? lt[4 * kB + 5] : 0.0;
   if (thermal) {
-    const double lT1 = lt[4 * B + 5];
-    const double intot1 = div_nr(1.0, ntot1);
-    le1 = lT1 * (1.0 / (1.5 * kBoltzmann)) * intot1;
-    const double lnt1 = -lT1 * T1 * intot1;
+    le1 = lT1 * (1.0 / (1.5 * kBoltzmann)) * L.intot1;
+    const double lnt1 = -lT1 * L.T1 * L.intot1;
     lx1[1] += lnt1 * nH;
     lx1[3] += lnt1 * nHe;
     lx1[4] += lnt1 * 2.0 * nHe;
     lnH += lnt1 * ((1.0 + yhe) + xHII1 + yhe * (yII1 + 2.0 * yIII1));
   } else {
-    lT0 += lt[4 * B + 5];
+    lT0 += lT1;
   }
-  if (lf != 0.0) {
-    const int nk = yhe > 0 ? 5 : 2;
-    double best = -1.0;
-    int kb = -1;
-    if (thermal) {
-      best = rel_change(e0, e1, 0.0);
-      kb = 5;
-    }
-    for (int k = 0; k < nk; ++k) {
-      const double r = rel_change(in_x[k], out_x[k], P.x_floor);
-      if (r > best) { best = r; kb = k; }
-    }
-    if (best > 0 && kb == 5) {
-      const double imm = div_nr(1.0, fabs(e0)), sg = e1 > e0 ? 1.0 : -1.0;
-      le1 += lf * sg * imm;
-      le0 += -lf * sg * imm - lf * (fabs(e1 - e0) * imm * imm) * (e0 > 0 ? 1.0 : -1.0);
-    } else if (best > 0) {
-      const double av = in_x[kb], bo = out_x[kb];
-      const double imm = div_nr(1.0, fabs(av) > P.x_floor ? fabs(av) : P.x_floor);
-      const double sg = bo > av ? 1.0 : -1.0;
-      lx1[kb] += lf * sg * imm;
-      lxin[kb] += -lf * sg * imm -
-                  lf * (fabs(bo - av) * imm * imm) * (fabs(av) > P.x_floor ? (av > 0 ? 1.0 : -1.0) : 0.0);
+  if (lf != 0.0 && L.f_kb >= 0) {
+    if (L.f_kb == 5) {
+      le1 += lf * L.f_sg * L.f_imm;
+      le0 += -lf * L.f_sg * L.f_imm - lf * L.f_span * L.f_sgn;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if (k == L.f_kb) {
+          lx1[k] += lf * L.f_sg * L.f_imm;
+          lxin[k] += -lf * L.f_sg * L.f_imm - lf * L.f_span * L.f_sgn;
+        }
     }
   }
   double lNbar[kMaxBins] = {0, 0, 0}, lm0 = 0, lm1 = 0, lm2 = 0;
   if (thermal) {
     le0 += le1;
-    ldt -= le1 * lamc;
+    ldt -= le1 * L.lamc;
     if (heat)
-      for (int b = 0; b < B; ++b) {
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
         const double e_0 = P.eps[b][0] * P.sigma[b][0], e_1 = P.eps[b][1] * P.sigma[b][1],
                      e_2 = P.eps[b][2] * P.sigma[b][2];
         const double ea = e_0 * m0 + e_1 * m1 + e_2 * m2;
         lNbar[b] += le1 * c * dt * ea;
-        ldt += le1 * c * Nbar[b] * ea;
-        const double w = le1 * c * dt * Nbar[b];
+        ldt += le1 * c * L.Nbar[b] * ea;
+        const double w = le1 * c * dt * L.Nbar[b];
         lm0 += w * e_0;
         lm1 += w * e_1;
         lm2 += w * e_2;
       }
     if (cool) {
+      const double nsp[5] = {nH * xHI, nH * xHII, nHe * yI, nHe * yII, nHe * yIII};
       const double ll = -le1 * dt;
       double dLdT = 0.0;
-      for (int q = 0; q < 5; ++q) dLdT += cc.dk[q] * nsp[q];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) dLdT += L.cc.dk[q] * nsp[q];
       lT0 += ll * ne0 * dLdT;
       // Lambda is linear in n_e0: its slope needs no division (n_e0 = 0 in a
       // neutral cell)
       double kn = 0.0;
-      for (int q = 0; q < 5; ++q) kn += cc.k[q] * nsp[q];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) kn += L.cc.k[q] * nsp[q];
       lne0e += ll * kn;
-      lxin[0] += ll * ne0 * cc.k[0] * nH;
-      lxin[1] += ll * ne0 * cc.k[1] * nH;
-      lxin[2] += ll * ne0 * cc.k[2] * nHe;
-      lxin[3] += ll * ne0 * cc.k[3] * nHe;
-      lxin[4] += ll * ne0 * cc.k[4] * nHe;
-      lnH += ll * ne0 * (cc.k[0] * xHI + cc.k[1] * xHII + yhe * (cc.k[2] * yI + cc.k[3] * yII + cc.k[4] * yIII));
+      lxin[0] += ll * ne0 * L.cc.k[0] * nH;
+      lxin[1] += ll * ne0 * L.cc.k[1] * nH;
+      lxin[2] += ll * ne0 * L.cc.k[2] * nHe;
+      lxin[3] += ll * ne0 * L.cc.k[3] * nHe;
+      lxin[4] += ll * ne0 * L.cc.k[4] * nHe;
+      lnH += ll * ne0 *
+             (L.cc.k[0] * xHI + L.cc.k[1] * xHII + yhe * (L.cc.k[2] * yI + L.cc.k[3] * yII + L.cc.k[4] * yIII));
     }
-    lT0 += le0 * 1.5 * kBoltzmann * ntot0;
+    lT0 += le0 * 1.5 * kBoltzmann * L.ntot0;
     const double lnt0 = le0 * 1.5 * kBoltzmann * T;
     lne0e += lnt0;
     lnH += lnt0 * (1.0 + yhe);
   }
-  for (int b = 0; b < B; ++b) {
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
     const double sm = P.sigma[b][0] * m0 + P.sigma[b][1] * m1 + P.sigma[b][2] * m2;
-    const double rem = c * dt * Nbar[b] * sm;
+    const double rem = c * dt * L.Nbar[b] * sm;
     double N1 = s[b] - rem;
     const bool clamped = N1 < 0;
     if (clamped) N1 = 0;
-    const double is = s[b] > 0 ? div_nr(1.0, s[b]) : 0.0;
+    const double is = L.is[b];
     const double scale = N1 * is;
     double lscale = 0.0;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ls[B + 3 * b + k] += lt[B + 3 * b + k] * scale;
-      lscale += lt[B + 3 * b + k] * s[B + 3 * b + k];
+      const double lf3 = lt ? lt[kB + 3 * b + k] : 0.0;
+      ls[kB + 3 * b + k] += lf3 * scale;
+      lscale += lf3 * s[kB + 3 * b + k];
     }
-    double lN1 = lt[b];
+    double lN1 = lt ? lt[b] : 0.0;
     if (s[b] > 0) {
       lN1 += lscale * is;
       ls[b] -= lscale * scale * is;
@@ -570,10 +628,10 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
       ls[b] += lN1;
       const double lrem = -lN1;
       lNbar[b] += lrem * c * dt * sm;
-      ldt += lrem * c * Nbar[b] * sm;
-      lm0 += lrem * c * dt * Nbar[b] * P.sigma[b][0];
-      lm1 += lrem * c * dt * Nbar[b] * P.sigma[b][1];
-      lm2 += lrem * c * dt * Nbar[b] * P.sigma[b][2];
+      ldt += lrem * c * L.Nbar[b] * sm;
+      lm0 += lrem * c * dt * L.Nbar[b] * P.sigma[b][0];
+      lm1 += lrem * c * dt * L.Nbar[b] * P.sigma[b][1];
+      lm2 += lrem * c * dt * L.Nbar[b] * P.sigma[b][2];
     }
   }
   lx1[0] += lm0 * nH;
@@ -605,10 +663,10 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lopD -= lnum * Dd * yIII * (iD * iD);
   lA += lopA;
   lDd += lopD;
-  ldt += lA * (Gm1 + bHeI * ne1) + lBb * aHeII * ne1 + lCc * (Gm2 + bHeII * ne1) + lDd * aHeIII * ne1;
+  ldt += lA * (L.Gm1 + L.bHeI * ne1) + lBb * L.aHeII * ne1 + lCc * (L.Gm2 + L.bHeII * ne1) + lDd * L.aHeIII * ne1;
   double lG0 = 0.0;
   const double lG1 = lA * dt, lG2 = lCc * dt;
-  const double lne1 = lA * dt * bHeI + lBb * dt * aHeII + lCc * dt * bHeII + lDd * dt * aHeIII;
+  const double lne1 = lA * dt * L.bHeI + lBb * dt * L.aHeII + lCc * dt * L.bHeII + lDd * dt * L.aHeIII;
   const double lxHII1 = lx1[1] + lne1 * nH;
   const double lxHI1 = lx1[0];
   lnH += lne1 * (xHII1 + yhe * (yII + 2.0 * yIII));
@@ -619,28 +677,26 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lxin[0] += lxHII1 * aH * iD1 + lxHI1 * (1.0 + bH) * iD1;
   const double laH = lxHII1 * (xHII + xHI) * iD1 + lD1;
   const double lbH = lxHI1 * (xHI + xHII) * iD1 + lD1;
-  ldt += laH * (Gm0 + bHI * ne0) + lbH * aHII * ne0;
+  ldt += laH * (L.Gm0 + L.bHI * ne0) + lbH * L.aHII * ne0;
   lG0 += laH * dt;
-  const double lne0 = laH * dt * bHI + lbH * dt * aHII;
+  const double lne0 = laH * dt * L.bHI + lbH * dt * L.aHII;
   lxin[1] += lne0 * nH;
   lnH += lne0 * (xHII + yhe * (yII + 2.0 * yIII));
   lxin[3] += lne0 * nHe;
   lxin[4] += lne0 * 2.0 * nHe;
-  {
-    const RateSlopes d = rate_slopes(tfn, rt);
-    if (coll) lT0 += laH * dt * d.bHI * ne0 + lA * dt * d.bHeI * ne1 + lCc * dt * d.bHeII * ne1;
-    if (recomb) lT0 += lbH * dt * d.aHII * ne0 + lBb * dt * d.aHeII * ne1 + lDd * dt * d.aHeIII * ne1;
-    lxin[1] += lne0e * nH;
-    lxin[3] += lne0e * nHe;
-    lxin[4] += lne0e * 2.0 * nHe;
-    lnH += lne0e * (xHII + yhe * (yII + 2.0 * yIII));
-  }
+  if (coll) lT0 += laH * dt * L.d.bHI * ne0 + lA * dt * L.d.bHeI * ne1 + lCc * dt * L.d.bHeII * ne1;
+  if (recomb) lT0 += lbH * dt * L.d.aHII * ne0 + lBb * dt * L.d.aHeII * ne1 + lDd * dt * L.d.aHeIII * ne1;
+  lxin[1] += lne0e * nH;
+  lxin[3] += lne0e * nHe;
+  lxin[4] += lne0e * 2.0 * nHe;
+  lnH += lne0e * (xHII + yhe * (yII + 2.0 * yIII));
   double lns0 = 0, lns1 = 0, lns2 = 0;
-  for (int b = 0; b < B; ++b) {
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
     lNbar[b] += c * (P.sigma[b][0] * lG0 + P.sigma[b][1] * lG1 + P.sigma[b][2] * lG2);
-    ls[b] += lNbar[b] * iden[b];
-    const double lden = -lNbar[b] * Nbar[b] * iden[b];
-    ldt += lden * c * kap[b];
+    ls[b] += lNbar[b] * L.iden[b];
+    const double lden = -lNbar[b] * L.Nbar[b] * L.iden[b];
+    ldt += lden * c * L.kap[b];
     const double lkap = lden * c * dt;
     lns0 += lkap * P.sigma[b][0];
     lns1 += lkap * P.sigma[b][1];
@@ -650,20 +706,22 @@ __device__ void attempt_vjp(const ChemParams& P, double nH, double dt, const dou
   lxin[2] += lns1 * nHe;
   lxin[3] += lns2 * nHe;
   lnH += lns0 * xHI + lns1 * yhe * yI + lns2 * yhe * yII;
-  for (int q = 0; q < 5; ++q) ls[4 * B + q] += lxin[q];
-  ls[4 * B + 5] += lT0;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) ls[4 * kB + q] += lxin[q];
+  ls[4 * kB + 5] += lT0;
 }
 
 struct ChemAdjArgs {
   int C, B;
-  const d4* rad;          // tape: radiation after the source term, before chemistry
-  const double* x5;       // tape: abundances before chemistry
+  const d4* rad;          // recorded radiation entering the subcycle's chemistry (before the source term)
+  const double* x5;       // recorded abundances entering the chemistry
   const double* T;
   const double* nH;
   const double* vol;
-  const int32_t* off;     // C+1 attempt offsets into rec
-  int32_t* count;         // C attempts per cell
-  ChemRec* rec;
+  const ChemRec* rec;     // the segment's tape
+  const int32_t* last;    // C: this subcycle's last record of each cell, -1 for one accepted attempt
+  const AttemptLin* lin;  // attempt_lin of this subcycle's records [rec_lo, rec_hi)
+  long long rec_lo, rec_hi;
   d4* lam_rad;            // in/out: cotangent of the cell's radiation
   double* lam_x5;         // in/out
   double* lam_T;          // in/out
@@ -675,153 +733,123 @@ struct ChemAdjArgs {
   double dt;              // subcycle length
   double lu3;
   int do_inject, do_chem;
-  int record;             // 0: count only, 1: write records (at most count[i] per cell)
-  int* bad;               // record: set to 1 if a cell's attempts differ from count[i]
 };
 
-__device__ __forceinline__ void load_cell(const ChemAdjArgs& a, int i, CellState& s) {
-  const int B = a.B;
-  for (int b = 0; b < B; ++b) {
-    const d4 v = a.rad[(size_t)i * B + b];
-    s.N[b] = v.x; s.f[b][0] = v.y; s.f[b][1] = v.z; s.f[b][2] = v.w;
-  }
+// The state entering the chemistry, packed: the recorded one plus the
+// source term, exactly as in k_chem64_first.
+template <int kB>
+__device__ __forceinline__ void load_cell(const ChemAdjArgs& a, int i, double* s) {
   const size_t C = a.C;
-  s.xHI = a.x5[i]; s.xHII = a.x5[C + i]; s.yI = a.x5[2 * C + i]; s.yII = a.x5[3 * C + i];
-  s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
-  if (a.do_inject) {   // the source term, exactly as in k_chem
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
+    const d4 v = a.rad[(size_t)i * kB + b];
+    s[b] = v.x; s[kB + 3 * b] = v.y; s[kB + 3 * b + 1] = v.z; s[kB + 3 * b + 2] = v.w;
+  }
+  s[4 * kB] = a.x5[i]; s[4 * kB + 1] = a.x5[C + i]; s[4 * kB + 2] = a.x5[2 * C + i];
+  s[4 * kB + 3] = a.x5[3 * C + i]; s[4 * kB + 4] = a.x5[4 * C + i]; s[4 * kB + 5] = a.T[i];
+  if (a.do_inject) {
     const int si = a.src_idx[i];
     if (si >= 0) {
       const double vcm3 = a.vol[i] * a.lu3;
-      for (int b = 0; b < B; ++b) s.N[b] += (a.src_rate[(size_t)si * B + b] * a.dt) / vcm3;
+#pragma unroll
+      for (int b = 0; b < kB; ++b) s[b] += (a.src_rate[(size_t)si * kB + b] * a.dt) / vcm3;
     }
   }
 }
 
-// Re-run the attempts of the forward chemistry (the same attempt and the
-// same controller arithmetic as chemistry() of the forward FP64 path); count
-// them, or write their records.  Recording writes at most count[i] records
-// (the count the forward recompute made) and flags a cell whose attempts
-// differ from it.
-__global__ void __launch_bounds__(128) k_chem_tape(ChemAdjArgs a, ChemParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.C) return;
-  CellState s, t;
-  load_cell(a, i, s);
-  const double nH = a.nH[i];
-  double rem = a.dt, dt = a.dt;
-  int n = 0;
-  ChemRec* out = a.record ? a.rec + a.off[i] : nullptr;
-  const int cap = a.record ? a.count[i] : 0;
-  while (rem > 0) {
-    if (n >= P.max_sub) { atomicOr(a.status, kStChemSubsteps); break; }
-    ChemRec* o = out && n < cap ? out + n : nullptr;
-    if (o) {
-      pack_state(s, a.B, o->s);
-      o->dt = dt;
-      o->rem = rem;
-    }
-    const double f = photochem_attempt(P, nH, dt, s, t);
-    if (o) o->f = f;
-    ++n;
-    if (f > P.f_max) {
-      if (o) { o->accepted = 0; o->grow_is_ratio = 0; o->clipped = 0; }
-      dt = dt * div_nr(P.f_s, f);
-      continue;
-    }
-    s = t;
-    rem = (dt == rem) ? 0.0 : rem - dt;
-    double grow = (f > 0) ? div_nr(P.f_s, f) : 2.0;
-    const int ratio = f > 0 && grow <= 2.0;
-    if (grow > 2.0) grow = 2.0;
-    const double dtn = dt * grow;
-    const int clipped = dtn > rem;
-    dt = clipped ? rem : dtn;
-    if (o) { o->accepted = 1; o->grow_is_ratio = ratio; o->clipped = clipped; }
-  }
-  if (!a.record) a.count[i] = n;
-  else if (n != cap) atomicOr(a.bad, 1);
+// attempt_lin of every recorded attempt of one subcycle, one thread per
+// record; the reverse chain then runs attempt_back only.
+template <int kB>
+__global__ void __launch_bounds__(128) k_chem_lin(ChemAdjArgs a, ChemParams P, AttemptLin* __restrict__ lin) {
+  const long long j = a.rec_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.rec_hi) return;
+  const ChemRec& r = a.rec[j];
+  AttemptLin L;
+  attempt_lin<kB>(P, a.nH[r.cell], r.dt, r.s, L, true);
+  lin[j - a.rec_lo] = L;
 }
 
-// Reverse over the recorded attempts of one cell, then the source term.
+// Reverse over the attempts of one cell, last to first, then the source
+// term.  Each attempt's cotangent flows to its entering state and, through
+// the controller, to its length, which the previous attempt's measure set.
+// A cell with one attempt (accepted, over the whole subcycle) has no record:
+// its entering state is the recorded one, and no later attempt's length
+// depends on its measure.
+template <int kB>
 __global__ void __launch_bounds__(128) k_chem_adj(ChemAdjArgs a, ChemParams P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.C) return;
-  const int B = a.B, nv = 4 * B + 6;
+  constexpr int nv = 4 * kB + 6;
   const size_t C = a.C;
-  double lt[kNv], ls[kNv];
-  for (int b = 0; b < B; ++b) {
-    const d4 v = a.lam_rad[(size_t)i * B + b];
-    lt[b] = v.x; lt[B + 3 * b] = v.y; lt[B + 3 * b + 1] = v.z; lt[B + 3 * b + 2] = v.w;
+  double lt[nv], ls[nv];
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
+    const d4 v = a.lam_rad[(size_t)i * kB + b];
+    lt[b] = v.x; lt[kB + 3 * b] = v.y; lt[kB + 3 * b + 1] = v.z; lt[kB + 3 * b + 2] = v.w;
   }
-  for (int q = 0; q < 5; ++q) lt[4 * B + q] = a.lam_x5[q * C + i];
-  lt[4 * B + 5] = a.lam_T[i];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) lt[4 * kB + q] = a.lam_x5[q * C + i];
+  lt[4 * kB + 5] = a.lam_T[i];
   const double nH = a.nH[i];
-  double ldt = 0.0, lrem = 0.0, lnH = 0.0;
-  const ChemRec* rec = a.do_chem ? a.rec + a.off[i] : nullptr;
-  const int n = a.do_chem ? a.off[i + 1] - a.off[i] : 0;
-  for (int k = n - 1; k >= 0; --k) {
-    const ChemRec& r = rec[k];
+  double lnH = 0.0;
+  int idx = a.do_chem ? a.last[i] : -1;
+  if (a.do_chem && idx < 0) {
+    double sv[nv];
+    load_cell<kB>(a, i, sv);
+    AttemptLin L;
+    attempt_lin<kB>(P, nH, a.dt, sv, L, false);
+#pragma unroll
     for (int q = 0; q < nv; ++q) ls[q] = 0.0;
     double cdt = 0.0;
-    if (r.accepted) {
-      const double grow = r.grow_is_ratio ? P.f_s / r.f : 2.0;
+    attempt_back<kB>(P, nH, a.dt, sv, L, lt, 0.0, ls, cdt, lnH);
+#pragma unroll
+    for (int q = 0; q < nv; ++q) lt[q] = ls[q];
+  }
+  double ldt = 0.0, lrem = 0.0;
+  while (idx >= 0) {
+    if (idx < a.rec_lo || idx >= a.rec_hi) {   // not reached: a cell's records lie in its subcycle's range
+      atomicOr(a.status, kStNonFinite);
+      break;
+    }
+    const ChemRec& r = a.rec[idx];
+    const AttemptLin& L = a.lin[idx - a.rec_lo];
+#pragma unroll
+    for (int q = 0; q < nv; ++q) ls[q] = 0.0;
+    double cdt = 0.0;
+    if (r.flags & kRecAccepted) {
+      const bool ratio = r.flags & kRecRatio;
+      const double grow = ratio ? P.f_s / r.f : 2.0;
       double ldtg = 0.0;
-      if (r.clipped) lrem += ldt;
+      if (r.flags & kRecClipped) lrem += ldt;
       else ldtg = ldt;
       double ldtk = ldtg * grow;
       const double lg = ldtg * r.dt;
-      const double lf = r.grow_is_ratio ? -lg * P.f_s / (r.f * r.f) : 0.0;
+      const double lf = ratio ? -lg * P.f_s / (r.f * r.f) : 0.0;
       ldtk -= lrem;
-      attempt_vjp(P, nH, r.dt, r.s, lt, lf, ls, cdt, lnH);
+      attempt_back<kB>(P, nH, r.dt, r.s, L, lt, lf, ls, cdt, lnH);
+#pragma unroll
       for (int q = 0; q < nv; ++q) lt[q] = ls[q];
       ldt = ldtk + cdt;
     } else {
       const double ldtk = ldt * P.f_s / r.f;
       const double lf = -ldt * r.dt * P.f_s / (r.f * r.f);
-      double zero[kNv];
-      for (int q = 0; q < nv; ++q) zero[q] = 0.0;
-      attempt_vjp(P, nH, r.dt, r.s, zero, lf, ls, cdt, lnH);
+      attempt_back<kB>(P, nH, r.dt, r.s, L, nullptr, lf, ls, cdt, lnH);
+#pragma unroll
       for (int q = 0; q < nv; ++q) lt[q] += ls[q];
       ldt = ldtk + cdt;
     }
+    idx = r.prev;
   }
-  for (int b = 0; b < B; ++b) {
-    a.lam_rad[(size_t)i * B + b] = make_d4(lt[b], lt[B + 3 * b], lt[B + 3 * b + 1], lt[B + 3 * b + 2]);
+#pragma unroll
+  for (int b = 0; b < kB; ++b) {
+    a.lam_rad[(size_t)i * kB + b] = make_d4(lt[b], lt[kB + 3 * b], lt[kB + 3 * b + 1], lt[kB + 3 * b + 2]);
     // source term N_b += S_b dt / (V lu^3)
     a.lam_S[(size_t)b * C + i] += lt[b] * a.dt / (a.vol[i] * a.lu3);
   }
-  for (int q = 0; q < 5; ++q) a.lam_x5[q * C + i] = lt[4 * B + q];
-  a.lam_T[i] = lt[4 * B + 5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) a.lam_x5[q * C + i] = lt[4 * kB + q];
+  a.lam_T[i] = lt[4 * kB + 5];
   a.lam_nH[i] += lnH;
-}
-
-// Exclusive scan of per-cell counts into offsets (one block of 1024 threads,
-// serial chunks per thread): off[0] = 0, off[i+1] = off[i] + count[i].
-__global__ void __launch_bounds__(1024) k_scan_counts(int C, const int32_t* __restrict__ count, int32_t* off,
-                                                      int* overflow) {
-  __shared__ long long part[1024];
-  const int tid = threadIdx.x;
-  const int chunk = (C + 1023) / 1024;
-  const int b0 = tid * chunk, b1 = min(C, b0 + chunk);
-  long long s = 0;
-  for (int i = b0; i < b1; ++i) s += count[i];
-  part[tid] = s;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    long long v = tid >= d ? part[tid - d] : 0;
-    __syncthreads();
-    part[tid] += v;
-    __syncthreads();
-  }
-  long long base = tid > 0 ? part[tid - 1] : 0;
-  for (int i = b0; i < b1; ++i) {
-    off[i] = (int32_t)base;
-    base += count[i];
-  }
-  if (tid == 1023) {
-    off[C] = (int32_t)part[1023];
-    if (part[1023] > 0x7fffffffLL) *overflow = 1;
-  }
 }
 
 }  // namespace m1rt

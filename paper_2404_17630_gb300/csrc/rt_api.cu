@@ -316,7 +316,7 @@ void launch_gather(rt_ctx* ctx, double dt, int stage = 0) {
     launch_gather_k<true>(ctx, a, n, in_l2);
 }
 
-void launch_chem(rt_ctx* ctx, double dt) {
+void launch_chem(rt_ctx* ctx, double dt, const ChemTape* tape = nullptr) {
   ProfScope ps(ctx, RT_KERNEL_CHEM);
   CellArgs a = cell_args(ctx, dt, 0, 1, 1);
   ChemParams P = chem_params(ctx);
@@ -329,7 +329,11 @@ void launch_chem(rt_ctx* ctx, double dt) {
     if (!a.do_chem) return;
     ctx->launches++;
     const int nb = (int)std::min<long long>(nblk(nc, t), ctx->n_sm);
-    k_chem64_rest<<<nb, t, 0, ctx->stream>>>(a, P, ctx->work_cell, ctx->work_f1d, ctx->work_ctl);
+    if (tape)
+      k_chem64_rest<true><<<nb, t, 0, ctx->stream>>>(a, P, ctx->work_cell, ctx->work_f1d, ctx->work_ctl, *tape);
+    else
+      k_chem64_rest<false><<<nb, t, 0, ctx->stream>>>(a, P, ctx->work_cell, ctx->work_f1d, ctx->work_ctl,
+                                                       ChemTape{});
     return;
   }
   // first attempt of every cell, then the rejected cells (a persistent grid
@@ -1091,6 +1095,45 @@ void adj_free(rt_ctx* ctx) {
   ctx->adj = rt_ctx::Adj();
 }
 
+// The chemistry tape: room for n records, keeping the first `keep`.
+rt_status tape_grow(rt_ctx* ctx, long long n, long long keep) {
+  auto& A = ctx->adj;
+  if (n <= A.rec_cap) return RT_OK;
+  if (n > 0x7fffffffLL) return fail(ctx, RT_OOM, "adjoint: a segment's chemistry tape exceeds 2^31 attempts");
+  ChemRec* r = nullptr;
+  rt_status st = aalloc(ctx, &r, (size_t)n, "chemistry tape");
+  if (st) return st;
+  if (A.rec) {
+    if (keep > 0)
+      CK(cudaMemcpyAsync(r, A.rec, (size_t)keep * sizeof(ChemRec), cudaMemcpyDeviceToDevice, ctx->stream), "tape");
+    CK(cudaStreamSynchronize(ctx->stream), "tape");
+    cudaFree(A.rec);
+    A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.rec));
+  }
+  A.rec = r;
+  A.rec_cap = n;
+  return RT_OK;
+}
+
+// Room for attempt_lin of n records.
+rt_status lin_reserve(rt_ctx* ctx, long long n) {
+  auto& A = ctx->adj;
+  if (n <= A.lin_cap) return RT_OK;
+  if (A.lin) {
+    CK(cudaStreamSynchronize(ctx->stream), "tape");
+    cudaFree(A.lin);
+    A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.lin));
+    A.lin = nullptr;
+    A.lin_cap = 0;
+  }
+  AttemptLin* l = nullptr;
+  rt_status st = aalloc(ctx, &l, (size_t)n, "chemistry linearisation");
+  if (st) return st;
+  A.lin = l;
+  A.lin_cap = n;
+  return RT_OK;
+}
+
 rt_status adj_prepare(rt_ctx* ctx, int nseg, int k) {
   auto& A = ctx->adj;
   if (A.nseg >= nseg && A.k >= k && A.lam_rad) return RT_OK;
@@ -1098,14 +1141,16 @@ rt_status adj_prepare(rt_ctx* ctx, int nseg, int k) {
   const size_t C = ctx->C, F = ctx->F, B = ctx->B;
   rt_status st;
 #define AA(p, n) if ((st = aalloc(ctx, &(p), (n), #p))) return st
-  AA(A.ck_rad, nseg * C * B); AA(A.ck_x5, nseg * 5 * C); AA(A.ck_T, nseg * C);
+  // checkpoints of every segment but the last, which the forward records
+  AA(A.ck_rad, (nseg - 1) * C * B); AA(A.ck_x5, (nseg - 1) * 5 * C); AA(A.ck_T, (nseg - 1) * C);
   AA(A.tp_rad_chem, k * C * B); AA(A.tp_rad_trans, k * C * B); AA(A.tp_x5, k * 5 * C); AA(A.tp_T, k * C);
   AA(A.fin_rad, C * B); AA(A.fin_x5, 5 * C); AA(A.fin_T, C);
   AA(A.lam_rad, C * B); AA(A.lam_part, C * B); AA(A.lam_in, C * B); AA(A.lampre, F * B * 2); AA(A.lamr, C * B * 3);
   AA(A.lam_x5, 5 * C); AA(A.lam_T, C); AA(A.lam_nH, C); AA(A.lam_S, B * C); AA(A.lim_coef, C * B * 4);
-  AA(A.lim_cell, C * B * 4); AA(A.count, C); AA(A.chem_off, C + 1);
-  AA(A.cnt_slot, (size_t)k * C); AA(A.tape_bad, 1);
+  AA(A.lim_cell, C * B * 4);
+  AA(A.tape_last, (size_t)k * C); AA(A.tape_used, 1);
 #undef AA
+  if ((st = tape_grow(ctx, std::max<long long>(4096, (long long)C / 4), 0))) return st;
   A.nseg = nseg;
   A.k = k;
   return RT_OK;
@@ -1141,7 +1186,7 @@ AdjArgs adj_args(rt_ctx* ctx, const d4* rad, double dt) {
 ChemAdjArgs chem_adj_args(rt_ctx* ctx, const d4* rad, const double* x5, const double* T, double dt) {
   ChemAdjArgs a;
   a.C = ctx->C; a.B = ctx->B; a.rad = rad; a.x5 = x5; a.T = T; a.nH = ctx->nH; a.vol = ctx->vol;
-  a.off = ctx->adj.chem_off; a.count = ctx->adj.count; a.rec = (ChemRec*)ctx->adj.rec;
+  a.rec = (const ChemRec*)ctx->adj.rec; a.last = nullptr; a.lin = nullptr; a.rec_lo = a.rec_hi = 0;
   a.lam_rad = ctx->adj.lam_rad; a.lam_x5 = ctx->adj.lam_x5; a.lam_T = ctx->adj.lam_T; a.lam_nH = ctx->adj.lam_nH;
   a.lam_S = ctx->adj.lam_S; a.status = ctx->status; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
   a.dt = dt;
@@ -1149,13 +1194,12 @@ ChemAdjArgs chem_adj_args(rt_ctx* ctx, const d4* rad, const double* x5, const do
   a.lu3 = lu * lu * lu;
   a.do_inject = ctx->n_src_cells > 0;
   a.do_chem = ctx->cfg.chem_mode > 0;
-  a.record = 0;
-  a.bad = ctx->adj.tape_bad;
   return a;
 }
 
 // Reverse of one subcycle: transport (from the recorded pre-transport
-// radiation), then chemistry and sources (from the recorded pre-chemistry state).
+// radiation), then chemistry and sources (from the recorded pre-chemistry
+// state and the recorded attempts).
 rt_status adj_subcycle(rt_ctx* ctx, int slot, double dts) {
   auto& A = ctx->adj;
   const size_t C = ctx->C, B = ctx->B;
@@ -1172,58 +1216,94 @@ rt_status adj_subcycle(rt_ctx* ctx, int slot, double dts) {
   std::swap(A.lam_rad, A.lam_in);
   rt_status st = launched(ctx, "adjoint transport");
   if (st) return st;
-  // chemistry tape: count, offsets, records, reverse
+  // chemistry, from the records of the segment's recompute
   const d4* pc_rad = A.tp_rad_chem + slot * C * B;
   const double* pc_x5 = A.tp_x5 + slot * 5 * C;
   const double* pc_T = A.tp_T + slot * C;
   ChemParams P = chem_params(ctx);
   ChemAdjArgs ca = chem_adj_args(ctx, pc_rad, pc_x5, pc_T, dts);
+  ca.last = A.tape_last + (size_t)slot * C;
+  ca.lin = (const AttemptLin*)A.lin;
+  ca.rec_lo = A.slot_rec[slot];
+  ca.rec_hi = A.slot_rec[slot + 1];
   const int t = 128;
-  if (ca.do_chem) {
-    // offsets from the attempt counts of the recompute's chemistry of this
-    // subcycle, records written by the tape (the same attempts); should a
-    // cell's attempts differ from that count, the tape is laid out again
-    // from a counting pass of its own
-    for (int pass = 0; pass < 2; ++pass) {
-      const int32_t* cnt = A.cnt_slot + (size_t)slot * C;
-      if (pass == 1) {
-        ca.record = 0;
-        ca.count = A.count;
-        k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
-        cnt = A.count;
-      }
-      CK(cudaMemsetAsync(ctx->stage, 0, sizeof(int), ctx->stream), "scan");
-      k_scan_counts<<<1, 1024, 0, ctx->stream>>>((int)C, cnt, A.chem_off, (int*)ctx->stage);
-      int32_t total = 0, ovf = 0;
-      CK(cudaMemcpyAsync(&total, A.chem_off + C, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
-      CK(cudaMemcpyAsync(&ovf, ctx->stage, 4, cudaMemcpyDeviceToHost, ctx->stream), "scan");
-      CK(cudaStreamSynchronize(ctx->stream), "scan");
-      if (ovf) return fail(ctx, RT_OOM, "adjoint: chemistry tape exceeds 2^31 attempts");
-      if ((size_t)total > A.rec_cap) {
-        if (A.rec) {
-          cudaFree(A.rec);
-          A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), A.rec));
-        }
-        size_t cap = std::max<size_t>((size_t)total + total / 4, 1024);
-        ChemRec* r = nullptr;
-        if ((st = aalloc(ctx, &r, cap, "chemistry tape"))) return st;
-        A.rec = r;
-        A.rec_cap = cap;
-      }
-      ca.rec = (ChemRec*)A.rec;
-      ca.record = 1;
-      ca.count = const_cast<int32_t*>(cnt);
-      CK(cudaMemsetAsync(A.tape_bad, 0, sizeof(int), ctx->stream), "tape");
-      k_chem_tape<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
-      int bad = 0;
-      CK(cudaMemcpyAsync(&bad, A.tape_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "tape");
-      CK(cudaStreamSynchronize(ctx->stream), "tape");
-      if (!bad) break;
-      if (pass == 1) return fail(ctx, RT_CUDA, "adjoint: the chemistry tape does not repeat its own attempts");
-    }
+  const long long nrec = ca.rec_hi - ca.rec_lo;
+  switch (B) {
+#define CHEM_ADJ(KB)                                                                                      \
+  case KB:                                                                                                \
+    if (nrec > 0) k_chem_lin<KB><<<nblk(nrec, t), t, 0, ctx->stream>>>(ca, P, (AttemptLin*)A.lin);        \
+    k_chem_adj<KB><<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);                                             \
+    break;
+    CHEM_ADJ(1)
+    CHEM_ADJ(2)
+    CHEM_ADJ(3)
+#undef CHEM_ADJ
+    default:
+      return fail(ctx, RT_INVALID_ARG, "adjoint: %d bins", (int)B);
   }
-  k_chem_adj<<<nblk(C, t), t, 0, ctx->stream>>>(ca, P);
   return launched(ctx, "adjoint chemistry");
+}
+
+// Run the subcycles [s0, s1) of a segment forward from the context's state
+// and record them for the reverse mode: the states entering each subcycle's
+// chemistry and transport, and the worklist's chemistry attempts.  The
+// transport of the segment's last subcycle runs only if `finish` (the
+// forward pass needs the end state, a recompute does not).  The host reads
+// the record counter after each subcycle's chemistry (the subcycle's range
+// of records); should the tape have overflowed, it grows, keeping the
+// earlier subcycles' records, and that subcycle's chemistry runs again
+// from its recorded entering state.
+rt_status adj_record_segment(rt_ctx* ctx, int s0, int s1, double dts, bool finish) {
+  auto& A = ctx->adj;
+  const size_t C = ctx->C, B = ctx->B;
+  const bool chem = ctx->cfg.chem_mode > 0;
+  const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+  A.slot_rec.assign(s1 - s0 + 1, 0);
+  CK(cudaMemsetAsync(A.tape_used, 0, sizeof(unsigned long long), ctx->stream), "tape");
+  CK(cudaMemsetAsync(A.tape_last, 0xff, (size_t)(s1 - s0) * C * sizeof(int32_t), ctx->stream), "tape");
+  long long widest = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int slot = s - s0;
+    d4* r_chem = A.tp_rad_chem + slot * C * B;
+    double* x_chem = A.tp_x5 + slot * 5 * C;
+    double* T_chem = A.tp_T + slot * C;
+    CK(cudaMemcpyAsync(r_chem, ctx->rad, C * B * sizeof(d4), d2d, ctx->stream), "tape");
+    CK(cudaMemcpyAsync(x_chem, ctx->x5, 5 * C * 8, d2d, ctx->stream), "tape");
+    CK(cudaMemcpyAsync(T_chem, ctx->T, C * 8, d2d, ctx->stream), "tape");
+    long long used = A.slot_rec[slot];
+    for (int tries = 0;; ++tries) {
+      const ChemTape tape{(ChemRec*)A.rec, A.rec_cap, A.tape_used, A.tape_last + (size_t)slot * C};
+      launch_chem(ctx, dts, chem ? &tape : nullptr);
+      if (!chem) break;
+      unsigned long long u = 0;
+      CK(cudaMemcpyAsync(&u, A.tape_used, sizeof(u), cudaMemcpyDeviceToHost, ctx->stream), "tape");
+      CK(cudaStreamSynchronize(ctx->stream), "tape");
+      used = (long long)u;
+      if (used <= A.rec_cap) break;
+      if (tries > 0) return fail(ctx, RT_CUDA, "adjoint: a subcycle's chemistry tape does not repeat itself");
+      rt_status st = tape_grow(ctx, std::max(2 * A.rec_cap, used + used / 4 + 1024), A.slot_rec[slot]);
+      if (st) return st;
+      const unsigned long long back = (unsigned long long)A.slot_rec[slot];
+      CK(cudaMemcpyAsync(A.tape_used, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->stream), "tape");
+      CK(cudaMemsetAsync(A.tape_last + (size_t)slot * C, 0xff, C * sizeof(int32_t), ctx->stream), "tape");
+      CK(cudaMemcpyAsync(ctx->rad, r_chem, C * B * sizeof(d4), d2d, ctx->stream), "tape");
+      CK(cudaMemcpyAsync(ctx->x5, x_chem, 5 * C * 8, d2d, ctx->stream), "tape");
+      CK(cudaMemcpyAsync(ctx->T, T_chem, C * 8, d2d, ctx->stream), "tape");
+      CK(cudaStreamSynchronize(ctx->stream), "tape");   // `back` is read before it goes out of scope
+      A.redone++;
+    }
+    A.slot_rec[slot + 1] = used;
+    widest = std::max(widest, used - A.slot_rec[slot]);
+    CK(cudaMemcpyAsync(A.tp_rad_trans + slot * C * B, ctx->rad, C * B * sizeof(d4), d2d, ctx->stream), "tape");
+    if (s + 1 == s1 && !finish) break;
+    launch_grad_any(ctx);
+    launch_flux_any(ctx);
+    launch_gather(ctx, dts);
+  }
+  A.tape_max = std::max(A.tape_max, A.slot_rec[s1 - s0]);
+  rt_status st = lin_reserve(ctx, std::max<long long>(widest, 1));
+  if (st) return st;
+  return launched(ctx, "adjoint record");
 }
 
 }  // namespace
@@ -1248,9 +1328,12 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
   if ((st = adj_prepare(ctx, nseg, k))) return st;
   auto& A = ctx->adj;
   const size_t C = ctx->C, B = ctx->B;
+  A.tape_max = 0;
+  A.redone = 0;
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream), "status");
-  // forward with checkpoints
-  for (int s = 0; s < n_sub; ++s) {
+  // forward with checkpoints; the last segment is recorded on the way
+  const int s_last = (nseg - 1) * k;
+  for (int s = 0; s < s_last; ++s) {
     if (s % k == 0 && (st = adj_copy_state(ctx, A.ck_rad + (s / k) * C * B, A.ck_x5 + (s / k) * 5 * C,
                                            A.ck_T + (s / k) * C, true)))
       return st;
@@ -1260,6 +1343,7 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
     launch_gather(ctx, dts);
   }
   if ((st = launched(ctx, "adjoint forward"))) return st;
+  if ((st = adj_record_segment(ctx, s_last, n_sub, dts, true))) return st;
   if ((st = adj_copy_state(ctx, A.fin_rad, A.fin_x5, A.fin_T, true))) return st;
   // cotangents of the final state
   double* sN = ctx->stage;
@@ -1275,27 +1359,14 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
   if (lam_T && (st = copy_in(ctx, A.lam_T, lam_T, C * 8))) return st;
   CK(cudaMemsetAsync(A.lam_nH, 0, C * 8, ctx->stream), "adjoint");
   CK(cudaMemsetAsync(A.lam_S, 0, B * C * 8, ctx->stream), "adjoint");
-  // reverse, segment by segment
+  // reverse, segment by segment; every segment but the last is recorded
+  // again from its checkpoint
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int s0 = seg * k, s1 = std::min(n_sub, s0 + k);
-    if ((st = adj_copy_state(ctx, A.ck_rad + seg * C * B, A.ck_x5 + seg * 5 * C, A.ck_T + seg * C, false)))
-      return st;
-    for (int s = s0; s < s1; ++s) {
-      const int slot = s - s0;
-      CK(cudaMemcpyAsync(A.tp_rad_chem + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
-                         ctx->stream), "tape");
-      CK(cudaMemcpyAsync(A.tp_x5 + slot * 5 * C, ctx->x5, 5 * C * 8, cudaMemcpyDeviceToDevice, ctx->stream), "tape");
-      CK(cudaMemcpyAsync(A.tp_T + slot * C, ctx->T, C * 8, cudaMemcpyDeviceToDevice, ctx->stream), "tape");
-      launch_chem(ctx, dts);
-      CK(cudaMemcpyAsync(A.tp_rad_trans + slot * C * B, ctx->rad, C * B * sizeof(d4), cudaMemcpyDeviceToDevice,
-                         ctx->stream), "tape");
-      if (ctx->cfg.chem_mode > 0)   // the attempts per cell, for the tape's layout
-        CK(cudaMemcpyAsync(A.cnt_slot + (size_t)slot * C, ctx->nsub, C * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                           ctx->stream), "tape");
-      if (s + 1 == s1) break;   // the segment's end state is not needed: the reverse starts from the tapes
-      launch_grad_any(ctx);
-      launch_flux_any(ctx);
-      launch_gather(ctx, dts);
+    if (seg < nseg - 1) {
+      if ((st = adj_copy_state(ctx, A.ck_rad + seg * C * B, A.ck_x5 + seg * 5 * C, A.ck_T + seg * C, false)))
+        return st;
+      if ((st = adj_record_segment(ctx, s0, s1, dts, false))) return st;
     }
     for (int s = s1 - 1; s >= s0; --s)
       if ((st = adj_subcycle(ctx, s - s0, dts))) return st;
@@ -1328,6 +1399,14 @@ rt_status rt_adjoint(rt_ctx* ctx, double dt, int n_sub, int checkpoint_every, co
   if (h & kStChemSubsteps) return fail(ctx, RT_CHEM_SUBSTEPS, "a cell reached max_substeps");
   if (h & kStNonFinite) return fail(ctx, RT_NONFINITE, "non-finite photon density");
   return launched(ctx, "adjoint");
+}
+
+rt_status rt_adjoint_tape_info(rt_ctx* ctx, long long* max_records, long long* capacity, int* redone) {
+  if (!ctx) return fail(nullptr, RT_INVALID_ARG, "null context");
+  if (max_records) *max_records = ctx->adj.tape_max;
+  if (capacity) *capacity = ctx->adj.rec_cap;
+  if (redone) *redone = ctx->adj.redone;
+  return RT_OK;
 }
 
 const char* rt_last_error(const rt_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }

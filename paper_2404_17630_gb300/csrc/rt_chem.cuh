@@ -471,9 +471,19 @@ __device__ bool chemistry_mixed_first(const ChemParams& P, double nH, double dt_
 
 // Adaptive substeps of the FP64 path (the oracle's arithmetic).  The loop
 // can resume after a rejected first attempt (two-pass chemistry): dt0 = the
-// next attempt's length, n0 = attempts already made.
-__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped, double dt0,
-                         int n0) {
+// next attempt's length, n0 = attempts already made.  The reverse mode
+// records the attempts through `tape`: begin() sees each attempt's entering
+// state, length and remaining time, end() its measure and the controller's
+// branches (accepted; growth by the ratio f_s / f rather than the cap 2;
+// next length clipped to the remaining time).  NoTape records nothing.
+struct NoTape {
+  __device__ __forceinline__ void begin(const CellState&, double, double) {}
+  __device__ __forceinline__ void end(double, bool, bool, bool) {}
+};
+
+template <class Tape>
+__device__ __forceinline__ int chemistry_loop(const ChemParams& P, double nH, double dt_sub, CellState& s,
+                                              bool* capped, double dt0, int n0, Tape& tape) {
   double rem = dt_sub, dt = dt0;
   int n = n0;
   CellState t;
@@ -481,22 +491,29 @@ __device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellStat
   while (rem > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;
+    tape.begin(s, dt, rem);
     double f = photochem_attempt(P, nH, dt, s, t);
     if (f > P.f_max) {
+      tape.end(f, false, false, false);
       dt = dt * div_nr(P.f_s, f);
       continue;
     }
     s = t;
     rem = (dt == rem) ? 0.0 : rem - dt;
     double grow = (f > 0) ? div_nr(P.f_s, f) : 2.0;
+    const bool ratio = f > 0 && grow <= 2.0;
     if (grow > 2.0) grow = 2.0;
     dt = dt * grow;
-    if (dt > rem) dt = rem;
+    const bool clipped = dt > rem;
+    if (clipped) dt = rem;
+    tape.end(f, true, ratio, clipped);
   }
   return n;
 }
-__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped) {
-  return chemistry(P, nH, dt_sub, s, capped, dt_sub, 0);
+__device__ int chemistry(const ChemParams& P, double nH, double dt_sub, CellState& s, bool* capped, double dt0,
+                         int n0) {
+  NoTape none;
+  return chemistry_loop(P, nH, dt_sub, s, capped, dt0, n0, none);
 }
 
 // First attempt of the FP64 chemistry over the whole subcycle.  Accepted

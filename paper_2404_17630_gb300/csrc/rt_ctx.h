@@ -106,15 +106,20 @@ struct rt_ctx {
   // adjoint buffers (allocated on first use)
   struct Adj {
     int nseg = 0, k = 0;
-    size_t rec_cap = 0;
+    long long rec_cap = 0;
     d4 *ck_rad = nullptr, *tp_rad_chem = nullptr, *tp_rad_trans = nullptr, *fin_rad = nullptr;
     double *ck_x5 = nullptr, *ck_T = nullptr, *tp_x5 = nullptr, *tp_T = nullptr, *fin_x5 = nullptr, *fin_T = nullptr;
     d4 *lam_rad = nullptr, *lam_part = nullptr, *lam_in = nullptr, *lampre = nullptr, *lamr = nullptr;
     double *lam_x5 = nullptr, *lam_T = nullptr, *lam_nH = nullptr, *lam_S = nullptr, *lim_coef = nullptr;
-    int32_t *lim_cell = nullptr, *count = nullptr, *chem_off = nullptr;
-    int32_t* cnt_slot = nullptr;   // [k][C] attempts per cell of each recomputed subcycle of a segment
-    int* tape_bad = nullptr;       // set by the tape when a cell's attempts differ from cnt_slot
-    void* rec = nullptr;
+    int32_t* lim_cell = nullptr;
+    int32_t* tape_last = nullptr;              // [k][C] last chemistry record of each cell, per subcycle
+    unsigned long long* tape_used = nullptr;   // records handed out in the segment being recorded
+    void* rec = nullptr;                       // chemistry records (ChemRec) of one segment
+    std::vector<long long> slot_rec;           // [k+1]: subcycle s of the segment holds records [s, s+1)
+    void* lin = nullptr;                       // attempt_lin (AttemptLin) of one subcycle's records
+    long long lin_cap = 0;
+    long long tape_max = 0;                    // last rt_adjoint: the most records a segment held
+    int redone = 0;                            // last rt_adjoint: subcycle chemistries recorded again
     std::vector<void*> allocs;
   } adj;
 };

@@ -1143,6 +1143,71 @@ __device__ __forceinline__ void chem_store64(const CellArgs& a, int i, const Cel
   if (bad) atomicOr(a.status, kStNonFinite);
 }
 
+// Tape of the reverse mode: one record per chemistry attempt of the cells
+// whose first attempt was rejected (the worklist's cells), written by the
+// forward's own worklist pass while the reverse mode recomputes a segment.
+// A cell's records are linked backwards (prev); last[i] is the index of its
+// last record, or -1 for a cell whose one attempt was accepted over the
+// whole subcycle (its entering state is the recorded pre-chemistry state,
+// and nothing downstream depends on its measure).  Records are handed out
+// by one counter, so a subcycle's records are one contiguous range; past
+// the capacity nothing is written, and the host, which reads the counter
+// after each subcycle's chemistry, grows the tape and records that
+// subcycle's chemistry again.
+constexpr int kNv = 4 * kMaxBins + 6;
+
+struct ChemRec {
+  double s[kNv];     // state entering the attempt (N[B], f[3B], xHI, xHII, yI, yII, yIII, T)
+  double dt, f;      // its length and measure
+  int cell;
+  int flags;         // kRecAccepted | kRecRatio (growth by f_s / f, not the cap) | kRecClipped (next length cut)
+  int prev;          // the cell's previous record, -1 for its first
+  int pad;
+};
+constexpr int kRecAccepted = 1, kRecRatio = 2, kRecClipped = 4;
+
+struct ChemTape {
+  ChemRec* rec;
+  long long cap;
+  unsigned long long* used;   // records handed out (may pass cap)
+  int32_t* last;              // C, this subcycle's
+};
+
+__device__ __forceinline__ void pack_state(const CellState& c, int B, double* s) {
+  for (int b = 0; b < B; ++b) {
+    s[b] = c.N[b];
+    s[B + 3 * b] = c.f[b][0]; s[B + 3 * b + 1] = c.f[b][1]; s[B + 3 * b + 2] = c.f[b][2];
+  }
+  s[4 * B] = c.xHI; s[4 * B + 1] = c.xHII; s[4 * B + 2] = c.yI; s[4 * B + 3] = c.yII; s[4 * B + 4] = c.yIII;
+  s[4 * B + 5] = c.T;
+}
+
+// Records the attempts of one cell (the Tape of chemistry_loop).
+struct TapeWriter {
+  ChemTape t;
+  int B, cell;
+  int prev = -1;
+  long long cur = 0;
+  __device__ __forceinline__ void begin(const CellState& s, double dt, double) {
+    cur = (long long)atomicAdd(t.used, 1ull);
+    if (cur < t.cap) {
+      ChemRec& r = t.rec[cur];
+      pack_state(s, B, r.s);
+      r.dt = dt;
+    }
+  }
+  __device__ __forceinline__ void end(double f, bool accepted, bool ratio, bool clipped) {
+    if (cur < t.cap) {
+      ChemRec& r = t.rec[cur];
+      r.f = f;
+      r.cell = cell;
+      r.flags = (accepted ? kRecAccepted : 0) | (ratio ? kRecRatio : 0) | (clipped ? kRecClipped : 0);
+      r.prev = prev;
+    }
+    prev = cur < t.cap ? (int)cur : -1;
+  }
+};
+
 // Sources and thermochemistry of the FP64 path in two passes, as the mixed
 // path (Sec. 6.2's remedy for the divergence of the substep loop): the first
 // attempt of every cell, then the rejected cells from a worklist.  The
@@ -1174,8 +1239,12 @@ __global__ void __launch_bounds__(128) k_chem64_first(CellArgs a, ChemParams P, 
 }
 
 // The FP64 worklist, handed out as k_chem_rest hands out the mixed one.
+// kTape: also record every attempt of these cells, the rejected first one
+// included, for the reverse mode.
+template <bool kTape>
 __global__ void __launch_bounds__(128) k_chem64_rest(CellArgs a, ChemParams P, const int32_t* __restrict__ work_cell,
-                                                     const double* __restrict__ work_f1, int* work_ctl) {
+                                                     const double* __restrict__ work_f1, int* work_ctl,
+                                                     ChemTape tape) {
   const int total = *(volatile int*)work_ctl;
   if (total == 0) return;   // nothing was rejected: the worklist's counters are all zero already
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1190,7 +1259,16 @@ __global__ void __launch_bounds__(128) k_chem64_rest(CellArgs a, ChemParams P, c
       chem_load64(a, i, s, false);
       bool capped;
       const double dt0 = a.dt * div_nr(P.f_s, work_f1[k]);
-      const int n = chemistry(P, a.nH[i], a.dt, s, &capped, dt0, 1);
+      int n;
+      if constexpr (kTape) {
+        TapeWriter tw{tape, a.B, i};
+        tw.begin(s, a.dt, a.dt);   // the first attempt, made and rejected by k_chem64_first
+        tw.end(work_f1[k], false, false, false);
+        n = chemistry_loop(P, a.nH[i], a.dt, s, &capped, dt0, 1, tw);
+        tape.last[i] = tw.prev;
+      } else {
+        n = chemistry(P, a.nH[i], a.dt, s, &capped, dt0, 1);
+      }
       a.nsub[i] = n;
       if (capped) atomicOr(a.status, kStChemSubsteps);
       chem_store64(a, i, s, true);

@@ -130,6 +130,8 @@ def load():
                 "rt_launch_count": [vp, ctypes.POINTER(i64)],
                 "rt_selftest_wait_timeout": [vp, ctypes.c_uint32],
                 "rt_adjoint": [vp, dbl, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+                "rt_adjoint_tape_info": [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_int)],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -355,6 +357,14 @@ def rt_adjoint(ctx, dt, n_sub, checkpoint_every, lam_N=None, lam_F=None, lam_x5=
                                            o(dL_dQ), o(dL_dnH), o(lam0_N), o(lam0_F), o(lam0_x5), o(lam0_T)))
 
 
+def rt_adjoint_tape_info(ctx):
+    """The last rt_adjoint's chemistry tape: {max_records, capacity, redone}."""
+    lib = load()
+    m, c, r = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+    _check(lib, ctx, lib.rt_adjoint_tape_info(ctx, ctypes.byref(m), ctypes.byref(c), ctypes.byref(r)))
+    return dict(max_records=m.value, capacity=c.value, redone=r.value)
+
+
 RT_KERNEL_NAMES = ("k_chem", "k_grad", "k_flux", "k_gather")
 
 
@@ -473,6 +483,9 @@ class RT:
         rt_adjoint(self.ctx, dt, n_sub, checkpoint_every, lam_N, lam_F, lam_x5, lam_T,
                    out["dQ"] if n_src else None, out["dnH"], out["N"], out["F"], out["x5"], out["T"])
         return out
+
+    def adjoint_tape_info(self):
+        return rt_adjoint_tape_info(self.ctx)
 
     def transport(self, dt):
         rt_stage_transport(self.ctx, dt)

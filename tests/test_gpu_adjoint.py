@@ -30,6 +30,21 @@ def rel(a, b):
     return np.abs(a - b).max() / (s if s > 0 else 1.0)
 
 
+def oracle_tape_records(mesh, cfg, st, dt, n_sub, k):
+    """Chemistry records per segment of k subcycles as the oracle's forward
+    counts them: every attempt of each cell that made more than one."""
+    o = make_oracle(mesh, cfg, st)
+    per = []
+    for _ in range(n_sub):
+        o.step(dt / n_sub, 1)
+        ns = np.asarray(o.substeps())
+        per.append(int(ns[ns > 1].sum()))
+    return [sum(per[i:i + k]) for i in range(0, n_sub, k)]
+
+
+TAPE_INITIAL = 4096   # the tape's first capacity, max(4096, C / 4) records, for these 512-cell meshes
+
+
 @pytest.mark.parametrize("chem_mode,k", [(1, 4), (1, 2), (0, 3), (2, 4), (2, 1)])
 def test_adjoint_matches_oracle(chem_mode, k):
     """Modes 0-2; in mode 2 the loss also weighs the final temperature, so
@@ -58,6 +73,13 @@ def test_adjoint_matches_oracle(chem_mode, k):
     # the forward part left the same final state as a plain step
     N1, _ = o.radiation()
     assert rel(rt.radiation()[0], N1) < 1e-12
+    # the tape held the oracle's attempts; a subcycle that overflowed the
+    # first capacity was recorded again (the mode-1 and mode-2 cases do)
+    segs = oracle_tape_records(mesh, cfg, st, dt, n_sub, k)
+    info = rt.adjoint_tape_info()
+    assert info["max_records"] == max(segs), (info, segs)
+    assert info["max_records"] <= info["capacity"]
+    assert (info["redone"] > 0) == (max(segs) > TAPE_INITIAL), (info, segs)
 
 
 def test_adjoint_finite_for_tiny_radiation():
