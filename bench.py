@@ -819,13 +819,20 @@ def measure_config5(dev, fp64pk, n=256, n_sub=200, adj_sub=20, k=20, adjoint=Tru
     lx = np.zeros((5, C))
     lx[1] = state["nH"] * mesh.volume / (state["nH"] * mesh.volume).sum()
     t1 = time.perf_counter()
-    res = rt.adjoint(dta, adj_sub, k, lam_x5=torch.as_tensor(lx, device=dev), n_src=len(state["cells"]))
+    try:
+        res = rt.adjoint(dta, adj_sub, k, lam_x5=torch.as_tensor(lx, device=dev), n_src=len(state["cells"]))
+    except rtb.RTError as e:   # e.g. device memory: report it, keep the rest of the line
+        out["adjoint_fp64"] = {"error": str(e), "n_sub": adj_sub, "checkpoint_every": k,
+                               "tape": rt.adjoint_tape_info()}
+        del rt
+        return out
     torch.cuda.synchronize(dev)
     adj_s = time.perf_counter() - t1
     free2, _ = torch.cuda.mem_get_info(dev)
     out["adjoint_fp64"] = {"value": C * adj_sub / adj_s, "unit": UNIT, "seconds": round(adj_s, 2),
                            "n_sub": adj_sub, "checkpoint_every": k,
                            "device_GB_in_use": round((free0 - free2) / 1e9, 1),
+                           "tape": rt.adjoint_tape_info(),
                            "dL_dQ_finite": bool(np.isfinite(res["dQ"]).all())}
     del rt
     return out
@@ -871,6 +878,7 @@ def measure_adjoint(dev, n=64, n_sub=50, k=10):
                         f"checkpoint every {k}", "forward_value": C * n_sub / fwd, "adjoint_value": C * n_sub / adj,
             "unit": UNIT, "forward_s": round(fwd, 4), "adjoint_s": round(adj, 4),
             "adjoint_over_forward": round(adj / fwd, 2), "dL_dQ": out["dQ"].sum(axis=1).tolist(),
+            "tape": rt.adjoint_tape_info(),
             "device_mem_used_GB": round((total - free) / 1e9, 2)}
 
 

@@ -1095,13 +1095,20 @@ void adj_free(rt_ctx* ctx) {
   ctx->adj = rt_ctx::Adj();
 }
 
-// The chemistry tape: room for n records, keeping the first `keep`.
-rt_status tape_grow(rt_ctx* ctx, long long n, long long keep) {
+// The chemistry tape: room for `want` records (at least `need`, should
+// `want` not fit in device memory), keeping the first `keep`.
+rt_status tape_grow(rt_ctx* ctx, long long want, long long need, long long keep) {
   auto& A = ctx->adj;
-  if (n <= A.rec_cap) return RT_OK;
-  if (n > 0x7fffffffLL) return fail(ctx, RT_OOM, "adjoint: a segment's chemistry tape exceeds 2^31 attempts");
+  if (need <= A.rec_cap) return RT_OK;
+  if (need > 0x7fffffffLL) return fail(ctx, RT_OOM, "adjoint: a segment's chemistry tape exceeds 2^31 attempts");
+  long long n = std::min<long long>(std::max(want, need), 0x7fffffffLL);
   ChemRec* r = nullptr;
   rt_status st = aalloc(ctx, &r, (size_t)n, "chemistry tape");
+  if (st && n > need) {
+    cudaGetLastError();   // an allocation failure is not sticky: try the exact need
+    n = need;
+    st = aalloc(ctx, &r, (size_t)n, "chemistry tape");
+  }
   if (st) return st;
   if (A.rec) {
     if (keep > 0)
@@ -1150,7 +1157,8 @@ rt_status adj_prepare(rt_ctx* ctx, int nseg, int k) {
   AA(A.lim_cell, C * B * 4);
   AA(A.tape_last, (size_t)k * C); AA(A.tape_used, 1);
 #undef AA
-  if ((st = tape_grow(ctx, std::max<long long>(4096, (long long)C / 4), 0))) return st;
+  const long long first = std::max<long long>(4096, (long long)C / 4);
+  if ((st = tape_grow(ctx, first, first, 0))) return st;
   A.nseg = nseg;
   A.k = k;
   return RT_OK;
@@ -1281,7 +1289,7 @@ rt_status adj_record_segment(rt_ctx* ctx, int s0, int s1, double dts, bool finis
       used = (long long)u;
       if (used <= A.rec_cap) break;
       if (tries > 0) return fail(ctx, RT_CUDA, "adjoint: a subcycle's chemistry tape does not repeat itself");
-      rt_status st = tape_grow(ctx, std::max(2 * A.rec_cap, used + used / 4 + 1024), A.slot_rec[slot]);
+      rt_status st = tape_grow(ctx, std::max(2 * A.rec_cap, used + used / 4 + 1024), used, A.slot_rec[slot]);
       if (st) return st;
       const unsigned long long back = (unsigned long long)A.slot_rec[slot];
       CK(cudaMemcpyAsync(A.tape_used, &back, sizeof(back), cudaMemcpyHostToDevice, ctx->stream), "tape");
