@@ -722,7 +722,7 @@ template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0,
 
 // flux[f*B + b] = A (Phi_N, Phi_F) / c_red, global Lax-Friedrichs at c_red.
 template <class R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 1) k_flux(Geo<R> g, const R4<R>* __restrict__ rad, const R* __restrict__ G,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) k_flux(Geo<R> g, const R4<R>* __restrict__ rad, const R* __restrict__ G,
                                               R4<R>* __restrict__ flux) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int B = g.B;
@@ -732,18 +732,28 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 1) k_flux(Geo<R> g, 
   t = f * B + b;
   if constexpr (sizeof(R) == 4) {
     // FP32 sweep: one 32-byte and one 16-byte face record, then the four
-    // groups (gradients, state) of each side's cell-major record (16-byte
-    // loads: as two 32-byte loads they need more registers than the
-    // kernel's 32, and were measured slower)
+    // groups (gradients, state) of each side's cell-major record as two
+    // 32-byte loads (groups 0-1 and 2-3 are adjacent in the paired layout);
+    // with the registers of 6 blocks per SM, 6 % faster than four 16-byte
+    // loads at 2e5 cells and 4 % at 2.1M (8 blocks: 3 % and 6 %)
     const f8 a = ld8(g.fa + f);
     const float4 xr = __ldg(g.fb + f);
     const float4* G4 = reinterpret_cast<const float4*>(G);
     const int cL = __float_as_int(a.v[7]), cR = __float_as_int(xr.w), Bp = g.Bp;
     float4 l[4], r[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) l[v] = __ldg(G4 + grec(cL, v, b, Bp));
-#pragma unroll
-    for (int v = 0; v < 4; ++v) r[v] = __ldg(G4 + grec(cR, v, b, Bp));
+    {
+      const f8* G8 = reinterpret_cast<const f8*>(G4);
+      const f8 l01 = ld8(G8 + (size_t)cL * 2 * Bp + b), l23 = ld8(G8 + (size_t)cL * 2 * Bp + Bp + b);
+      const f8 r01 = ld8(G8 + (size_t)cR * 2 * Bp + b), r23 = ld8(G8 + (size_t)cR * 2 * Bp + Bp + b);
+      l[0] = make_float4(l01.v[0], l01.v[1], l01.v[2], l01.v[3]);
+      l[1] = make_float4(l01.v[4], l01.v[5], l01.v[6], l01.v[7]);
+      l[2] = make_float4(l23.v[0], l23.v[1], l23.v[2], l23.v[3]);
+      l[3] = make_float4(l23.v[4], l23.v[5], l23.v[6], l23.v[7]);
+      r[0] = make_float4(r01.v[0], r01.v[1], r01.v[2], r01.v[3]);
+      r[1] = make_float4(r01.v[4], r01.v[5], r01.v[6], r01.v[7]);
+      r[2] = make_float4(r23.v[0], r23.v[1], r23.v[2], r23.v[3]);
+      r[3] = make_float4(r23.v[4], r23.v[5], r23.v[6], r23.v[7]);
+    }
     float vL[4], vR[4], PL[3], PR[3];
     face_state_rec(l, a.v[4], a.v[5], a.v[6], vL);
     face_state_rec(r, xr.x, xr.y, xr.z, vR);
@@ -819,18 +829,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Flux application, one thread per (cell, bin): the cell's stored face
-// fluxes are summed in CSR order (ascending face index, + where the cell is
-// the left cell, - where it is the right cell) and U <- U - c dt / V * sum in
-// FP64.  Comp (mixed precision): the FP32 terms are summed as an unevaluated
-// FP32 pair hi + lo (error-free two_sum), widened to FP64 once; otherwise
-// each term is widened and summed in FP64.  Writes the FP32 shadow if given.
-// Pred: the face loads in batches of four with a predicated last batch (no
-// serial tail of single loads) -- faster where the flux array is held in L2,
-// slower where the loads go to HBM and the extra registers cost occupancy.
-// Heun: the kernel handles Heun's stages (a.heun); the plain update is its
-// own instantiation, without the stages' code (which the compiler would
-// otherwise issue as predicated FP64 instructions on every launch).
 // The flux application's sum for (cell i, bin b): the cell's stored face
 // fluxes in CSR order, + where the cell is the left cell, - where it is the
 // right cell.  Comp (mixed precision): the FP32 terms summed as an
@@ -838,7 +836,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // otherwise each term widened and summed in FP64.  Pred: the face loads in
 // batches of four with a predicated last batch (no serial tail of single
 // loads) -- faster where the flux array is held in L2, slower where the
-// loads go to HBM and the extra registers cost occupancy. 
+// loads go to HBM and the extra registers cost occupancy.
 template <class R, bool Comp, bool Pred>
 __device__ __forceinline__ void flux_sum(const CellArgs& a, const R4<R>* __restrict__ flux, int i, int b,
                                          double acc[4]) {
