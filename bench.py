@@ -764,9 +764,9 @@ def measure_config5(dev, fp64pk, n=256, n_sub=200, adj_sub=20, k=20, adjoint=Tru
     7.16 Mpc, exp(GRF) density as the THESAN-like box, 32768 peak sources,
     c_red = 0.2 c).  Mixed forward of one step of n_sub subcycles (after one
     warm-up step); then the FP64 reverse mode over adj_sub subcycles with a
-    checkpoint every k (the reverse mode over all 200 subcycles takes ~15
-    minutes at the measured rate, beyond a bench run).  Reports cell-updates/s
-    and the device memory in use (cudaMemGetInfo) at the end of each part."""
+    checkpoint every k (over all 200 subcycles it takes ~4 minutes, so the
+    default run takes 20).  Reports cell-updates/s and the device memory in
+    use (cudaMemGetInfo) at the end of each part."""
     import torch
     import synth
     from paper_2404_17630_gb300 import RT, make_config
@@ -898,6 +898,9 @@ def main():
                     help="skip the 16.8M-cell box (mixed forward and a 20-subcycle FP64 reverse mode; ~190 GB of "
                          "device memory)")
     ap.add_argument("--config5-no-adjoint", action="store_true", help="the 16.8M-cell box without the reverse mode")
+    ap.add_argument("--config5-adjoint-sub", type=int, default=20,
+                    help="subcycles of the 16.8M-cell box's reverse mode (checkpoint every 20); 200 is the "
+                         "full step (~4 minutes, ~211 GB of device memory)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -944,7 +947,8 @@ def main():
     adjoint = None if args.no_adjoint else measure_adjoint(dev)
     hii = None if args.no_hii else measure_hii(3, 1, dev)
     timebins = None if args.no_hii else measure_timebins(dev)
-    config5 = None if args.no_config5 else measure_config5(dev, fp64pk, adjoint=not args.config5_no_adjoint)
+    config5 = None if args.no_config5 else measure_config5(dev, fp64pk, adj_sub=args.config5_adjoint_sub,
+                                                           adjoint=not args.config5_no_adjoint)
     if rank != 0:
         return
     C, F = res["C"], res["F"]
