@@ -9,8 +9,8 @@ from tests.test_gpu_parity import make_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _setup(n=8, chem_mode=1, n_src=2):
-    mesh, cfg, st = voronoi_case(n=n, n_bins=3, chem_mode=chem_mode, n_src=n_src)
+def _setup(n=8, chem_mode=1, n_src=2, n_bins=3):
+    mesh, cfg, st = voronoi_case(n=n, n_bins=n_bins, chem_mode=chem_mode, n_src=n_src)
     st["N"] *= 0.1
     st["fr"] *= 0.1
     c = mesh.centroids()
@@ -80,6 +80,30 @@ def test_adjoint_matches_oracle(chem_mode, k):
     assert info["max_records"] == max(segs), (info, segs)
     assert info["max_records"] <= info["capacity"]
     assert (info["redone"] > 0) == (max(segs) > TAPE_INITIAL), (info, segs)
+
+
+@pytest.mark.parametrize("n_bins", [1, 2])
+def test_adjoint_matches_oracle_fewer_bins(n_bins):
+    """The reverse chemistry is compiled per bin count (its state arrays in
+    registers): one and two bins against the oracle, full thermal network."""
+    mesh, cfg, st, R = _setup(chem_mode=2, n_bins=n_bins)
+    n_sub, k = 4, 2
+    lx = _loss_cot(mesh, st, R)
+    lN = np.zeros((n_bins, mesh.n_cells))
+    lN[:, R] = mesh.volume[R]
+    lT = lx[1] * 1e-4
+    o = make_oracle(mesh, cfg, st)
+    dt = o.max_dt() * n_sub
+    ref = o.adjoint(dt, n_sub, lam_N=lN, lam_x5=lx, lam_T=lT)
+    assert ref["status"] == 0
+    rt = make_gpu(mesh, cfg, st)
+    got = rt.adjoint(dt, n_sub, k, lam_N=lN, lam_x5=lx, lam_T=lT, n_src=len(st["cells"]))
+    gQ_ref = ref["g_src"][:, st["cells"]].T
+    e = {"dQ": rel(got["dQ"], gQ_ref), "dnH": rel(got["dnH"], ref["g_nH"]), "N": rel(got["N"], ref["lam0"]["N"]),
+         "F": rel(got["F"], ref["lam0"]["fr"] / cfg["c_red"]), "x5": rel(got["x5"], ref["lam0"]["x5"]),
+         "T": rel(got["T"], ref["lam0"]["T"])}
+    assert max(e.values()) < 1e-9, e
+    assert rt.adjoint_tape_info()["max_records"] > 0   # the chains ran through the tape
 
 
 def test_adjoint_finite_for_tiny_radiation():
