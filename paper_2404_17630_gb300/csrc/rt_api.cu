@@ -196,6 +196,7 @@ ChemParams chem_params(const rt_ctx* ctx) {
 CellArgs cell_args(rt_ctx* ctx, double dt, int gather, int inject, int chem) {
   CellArgs a;
   a.C = ctx->C; a.B = ctx->B; a.divB = make_divb(ctx->B); a.off = ctx->off; a.csr = ctx->csr; a.vol = ctx->vol; a.ivol = ctx->ivol; a.rad = ctx->rad;
+  a.radN = ctx->radN;
   a.nH = ctx->nH; a.x5 = ctx->x5; a.T = ctx->T; a.src_idx = ctx->src_idx; a.src_rate = ctx->src_rate;
   a.nsub = ctx->nsub; a.status = ctx->status;
   a.lam = ctx->cfg.c_red * dt / ctx->cfg.unit_length_cm;
@@ -364,10 +365,17 @@ void transport(rt_ctx* ctx, double dt) {
   launch_gather(ctx, dt, 2);
 }
 
+// Mixed precision: the state (radN, FP32 sweep records) from the interface
+// records in ctx->rad, and back.
 void refresh_shadow(rt_ctx* ctx) {
   if (!mixed(ctx)) return;
   long long n = (long long)ctx->C * ctx->B;
-  k_shadow_rad<float><<<nblk(n), kThreads, 0, ctx->stream>>>((int)n, ctx->rad, ctx->shadow);
+  k_split_rad<<<nblk(n), kThreads, 0, ctx->stream>>>((int)n, ctx->rad, ctx->radN, ctx->shadow);
+}
+void join_state(rt_ctx* ctx) {
+  if (!mixed(ctx)) return;
+  long long n = (long long)ctx->C * ctx->B;
+  k_join_rad<<<nblk(n), kThreads, 0, ctx->stream>>>((int)n, ctx->radN, ctx->shadow, ctx->rad);
 }
 
 rt_status launched(rt_ctx* ctx, const char* what) {
@@ -536,6 +544,7 @@ rt_status rt_init_mesh(rt_ctx* ctx, const rt_cells* cells, const rt_faces* faces
     AL(ctx->fa32, F); AL(ctx->fb32, F); AL(ctx->minv32, 6 * (size_t)C); AL(ctx->ivol, C);
     AL(ctx->work_f1, C);
     AL(ctx->shadow, (size_t)C * B);
+    AL(ctx->radN, (size_t)C * B);
   } else {
     AL(ctx->work_f1d, C);
   }
@@ -917,6 +926,7 @@ rt_status rt_get_fields(rt_ctx* ctx, uint32_t mask, double* const* out) {
   if (mask & (RT_FIELD_N | RT_FIELD_F)) {
     double* sN = ctx->stage;
     double* sF = ctx->stage + B * C;
+    join_state(ctx);
     k_unpack_rad<<<nblk((long long)B * C), kThreads, 0, ctx->stream>>>((int)C, (int)B, ctx->cfg.c_red, ctx->rad,
                                                                         sN, sF);
     if ((st = launched(ctx, "get fields"))) return st;

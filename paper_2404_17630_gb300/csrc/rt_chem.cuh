@@ -284,18 +284,21 @@ __device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
 // unit: divisions become FP64 reciprocals (one per distinct denominator),
 // the photon removal uses N_b' = N_b (1 - tau'_b / (1 + tau_b)) instead of a
 // division by N_b, and the substep-control measure f (which only steers step
-// lengths and the accept test) is formed in FP32.  State, rates products and
-// all updates stay FP64.  The reduced flux does not enter the chemistry: an
-// attempt only reports the factor sc_b that scales bin b's photons (and, by
-// kappa_F = kappa_E, its flux); the caller applies the product of the
-// accepted factors to the flux once.
+// lengths and the accept test) is formed in FP32.  The absorber densities,
+// the attenuation, the photoionisation rates, the abundance and photon
+// updates stay FP64; n_e (which only multiplies the FP32 rate coefficients)
+// and the change of n_e in the temperature update are formed in FP32.  The
+// reduced flux does not enter the chemistry: an attempt only reports, in
+// FP32, the factor sc_b that scales bin b's photons (and, by kappa_F =
+// kappa_E, its FP32 flux); the caller applies the product of the accepted
+// factors to the flux once.
 struct GasState {
   double N[kMaxBins];
   double xHI, xHII, yI, yII, yIII, T;
 };
 
 __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const GasState& s,
-                                         GasState& t, double sc_out[kMaxBins]) {
+                                         GasState& t, float sc_out[kMaxBins]) {
   const int B = P.B;
   const double c = P.c_red;
   const double cdt = c * dt;
@@ -325,15 +328,21 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
     }
   }
   const double G0 = Gs[0], G1 = Gs[1], G2 = Gs[2];
-  const double ne0 = nH * s.xHII + nHe * (s.yII + 2.0 * s.yIII);
-  const float ne0f = d2f_int(ne0);
+  // n_e enters only the FP32 products with the rate coefficients (and the
+  // FP32 cooling): formed in FP32 from the FP32 images of the densities
+  const float nHf = d2f_int(nH), nHef = d2f_int(nHe);
+  const float ne_he = nHef * fmaf(2.0f, d2f_int(s.yIII), d2f_int(s.yII));
+  const float ne0f = fmaf(nHf, d2f_int(s.xHII), ne_he);
   const double aH = coll ? fma(dt, f2d_int(r.bHI * ne0f), cdt * G0) : cdt * G0;
   const double bH = recomb ? dt * f2d_int(r.aHII * ne0f) : 0.0;
   const double iden = rcp64(1.0 + aH + bH);
-  t.xHI = (s.xHI * (1.0 + bH) + bH * s.xHII) * iden;
-  t.xHII = (s.xHII * (1.0 + aH) + aH * s.xHI) * iden;
-  const double ne1 = nH * t.xHII + nHe * (s.yII + 2.0 * s.yIII);
-  const float ne1f = d2f_int(ne1);
+  // backward Euler for (x_HI, x_HII): x_HI' = (x_HI + bH (x_HI + x_HII)) / (1
+  // + aH + bH), and the same for x_HII with aH -- the two-state solve with
+  // the sum of both fractions shared
+  const double xs = s.xHI + s.xHII;
+  t.xHI = fma(bH, xs, s.xHI) * iden;
+  t.xHII = fma(aH, xs, s.xHII) * iden;
+  const float ne1f = fmaf(nHf, d2f_int(t.xHII), ne_he);
   const double A = coll ? fma(dt, f2d_int(r.bHeI * ne1f), cdt * G1) : cdt * G1;
   const double Bb = recomb ? dt * f2d_int(r.aHeII * ne1f) : 0.0;
   const double Cc = coll ? fma(dt, f2d_int(r.bHeII * ne1f), cdt * G2) : cdt * G2;
@@ -361,7 +370,9 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
         if (P.smask & (1 << (3 * b + sp))) suma = fma(P.sigma[b][sp], m[sp], suma);
       const double taup = cdt * suma;
       double sc = fma(-taup, inv1pt[b], 1.0);
-      sc = sc > 0.0 ? sc : 0.0;
+      // sc <- max(sc, 0) on the integer pipe (a double's bits order like
+      // the value where it is positive)
+      sc = __double_as_longlong(sc) > 0 ? sc : 0.0;
       if (heat) {
         float ea = 0.0f;
 #pragma unroll
@@ -370,7 +381,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
         hsum = fmaf(d2f_int(Nbar[b]), ea, hsum);
       }
       t.N[b] = s.N[b] * sc;
-      sc_out[b] = sc;
+      sc_out[b] = d2f_int(sc);
     }
   }
 
@@ -382,15 +393,16 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
     // change of n_e is FP64 and the increment is formed in FP32
     float lam_s = 0.0f;
     if (cool) {
-      const float nHf = d2f_int(nH), nHef = d2f_int(nHe);
       lam_s = RateEval<true>::cooling_scaled(s.T, ne0f, nHf * d2f_int(s.xHI), nHf * d2f_int(s.xHII),
                                              nHef * d2f_int(s.yI), nHef * d2f_int(s.yII), nHef * d2f_int(s.yIII));
     }
     const float de = fmaf(heat ? d2f_int(cdt * kHeatScale) : 0.0f, hsum, -(d2f_int(dt * kCoolScale) * lam_s));
-    const double dne = nH * (t.xHII - s.xHII) + nHe * ((t.yII - s.yII) + 2.0 * (t.yIII - s.yIII));
-    const float dnef = d2f_int(dne);
+    // the change of n_e from the FP64 differences of the fractions (they
+    // cancel), combined in FP32
+    const float dnef = fmaf(nHf, d2f_int(t.xHII - s.xHII),
+                            nHef * fmaf(2.0f, d2f_int(t.yIII - s.yIII), d2f_int(t.yII - s.yII)));
     const float T0 = d2f_int(s.T);
-    const float ntot0 = d2f_int(nH) * (1.0f + (float)P.y_he) + ne0f;
+    const float ntot0 = nHf * (1.0f + (float)P.y_he) + ne0f;
     const float ntot1 = ntot0 + dnef;
     constexpr float kInv15k = (float)(1.0 / (1.5 * kBoltzmann));
     t.T = s.T + f2d_int(__fdividef(fmaf(de, kInv15k, -T0 * dnef), ntot1));
@@ -417,15 +429,16 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 // factor are FP32; dt and the remaining time stay FP64 (the subcycle is
 // covered exactly).  Both are >= 0, where the order of the bit patterns is
 // the numeric order: the comparisons run on the integer pipe.  S_b returns
-// the product of the accepted attempts' photon factors (the flux scale).
+// the product of the accepted attempts' photon factors (the flux scale, in
+// FP32 like the flux it scales).
 // The loop can resume after a rejected first attempt (two-pass chemistry):
 // dt0 = the next attempt's length, n0 = attempts already made.
 __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, GasState& s,
-                               double S[kMaxBins], bool* capped, double dt0, int n0) {
+                               float S[kMaxBins], bool* capped, double dt0, int n0) {
   double rem = dt_sub, dt = dt0;
   int n = n0, acc = 0;
   GasState t;
-  double sc[kMaxBins];
+  float sc[kMaxBins];
   *capped = false;
   const float fmax = (float)P.f_max, fs = (float)P.f_s;
   while (__double_as_longlong(rem) > 0) {
@@ -447,7 +460,7 @@ __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, Ga
   }
   if (acc == 0) {
 #pragma unroll
-    for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0;
+    for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0f;
   }
   return n;
 }
@@ -457,9 +470,9 @@ __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, Ga
 // s is unchanged and *f1 holds the attempt's measure, from which the loop
 // resumes with dt_sub * fs / f1 (chemistry_mixed with n0 = 1).
 __device__ bool chemistry_mixed_first(const ChemParams& P, double nH, double dt_sub, GasState& s,
-                                      double S[kMaxBins], float* f1) {
+                                      float S[kMaxBins], float* f1) {
   GasState t;
-  double sc[kMaxBins];
+  float sc[kMaxBins];
   const float f = photochem_attempt_mixed(P, nH, dt_sub, s, t, sc);
   *f1 = f;
   if (f > (float)P.f_max) return false;

@@ -114,6 +114,12 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// x is infinite or NaN: all exponent bits set (an integer test; the FP64
+// pipe's comparison is left free).
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7FF00000u) == 0x7FF00000u;
+}
+
 // Hardware reciprocal approximation (MUFU; relative error ~1 ulp).
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;

@@ -34,8 +34,9 @@ struct rt_ctx {
   float4* fb32 = nullptr;      // FP32 face records (x_f - s_R, right)
   float* minv32 = nullptr;
   // state
-  d4* rad = nullptr;      // master [C][B]
-  float4* shadow = nullptr;    // FP32 sweep copy [C][B] (mixed)
+  d4* rad = nullptr;      // [C][B] (N, F / c): the FP64 state; mixed precision: the interface records only
+  double* radN = nullptr;      // mixed precision: N [C][B] in FP64
+  float4* shadow = nullptr;    // mixed precision: FP32 sweep records [C][B] (N rounded, F / c: the flux state)
   double *nH = nullptr, *x5 = nullptr, *T = nullptr;
   int32_t* src_idx = nullptr;
   double* src_rate = nullptr;

@@ -187,14 +187,23 @@ __global__ void k_unpack_rad(int C, int B, double c, const d4* __restrict__ rad,
   }
 }
 
-// sweep copy of the radiation in precision R
-template <class R> __global__ void k_shadow_rad(int n, const d4* __restrict__ rad, R4<R>* out) {
+// Mixed precision keeps the photon density N of each (cell, bin) in FP64
+// (radN) and the reduced flux in FP32, as lanes 1-3 of the FP32 sweep record
+// (N rounded to FP32, f_x, f_y, f_z) that the gradient and flux kernels read.
+// k_split_rad forms both from interleaved FP64 records, k_join_rad the FP64
+// records (the flux widened exactly) from them.
+__global__ void k_split_rad(int n, const d4* __restrict__ rad, double* __restrict__ radN, float4* __restrict__ sh) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  d4 v = rad[k];
-  R4<R> o;
-  o.x = (R)v.x; o.y = (R)v.y; o.z = (R)v.z; o.w = (R)v.w;
-  out[k] = o;
+  const d4 v = rad[k];
+  radN[k] = v.x;
+  sh[k] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+}
+__global__ void k_join_rad(int n, const double* __restrict__ radN, const float4* __restrict__ sh, d4* rad) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float4 v = sh[k];
+  rad[k] = make_d4(radN[k], (double)v.y, (double)v.z, (double)v.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -468,6 +477,108 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
   }
 }
 
+// Three-input FP32 maximum and minimum (one instruction on sm_100 and
+// later); exact, like fmaxf / fminf of two.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// lim_extremes with the faces taken two at a time by three-input extremes:
+// the same extremes (max and min are exact), half the compare instructions.
+__device__ __forceinline__ void lim_extremes_pairs(const float4* __restrict__ xs, int k0, int k1,
+                                                   const float gr[4][3], const float eg[4], float X, float dpos[4],
+                                                   float dneg[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.0f;
+  int k = k0;
+#pragma unroll 2
+  for (; k + 2 <= k1; k += 2) {
+    const float4 xa = xs[k], xb = xs[k + 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float da = gr[q][0] * xa.x + gr[q][1] * xa.y + gr[q][2] * xa.z;
+      const float db = gr[q][0] * xb.x + gr[q][1] * xb.y + gr[q][2] * xb.z;
+      dpos[q] = max3f(dpos[q], da, db);
+      dneg[q] = min3f(dneg[q], da, db);
+    }
+  }
+  if (k < k1) {
+    const float4 x = xs[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+      dpos[q] = fmaxf(dpos[q], dphi);
+      dneg[q] = fminf(dneg[q], dphi);
+    }
+  }
+  bool exact = true;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float t = eg[q] * X;
+    exact = exact && (dpos[q] == 0.0f || dpos[q] > t) && (dneg[q] == 0.0f || -dneg[q] > t);
+  }
+  if (exact) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dpos[q] = dneg[q] = 0.0f;
+  for (k = k0; k < k1; ++k) {
+    const float4 x = xs[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dphi = gr[q][0] * x.x + gr[q][1] * x.y + gr[q][2] * x.z;
+      const float dm = fabsf(dphi) > eg[q] * x.w ? dphi : 0.0f;
+      dpos[q] = fmaxf(dpos[q], dm);
+      dneg[q] = fminf(dneg[q], dm);
+    }
+  }
+}
+
+// The FP32 gradients' last part, from the least-squares right-hand sides r
+// and the neighbour extremes: g = M^-1 r, the limiter factors (extremes of
+// g . x_f over the offset records xs[k0, k1): lim_extremes_pairs where
+// Pairs, else lim_extremes), and the record of (cell i, bin b) written as
+// two 32-byte stores (groups 0-1 and 2-3).
+template <bool Pairs>
+__device__ __forceinline__ void grad_tail_fp32(const Geo<float>& g, float* __restrict__ G, int i, int b,
+                                               const float4& pi, const float r[4][3], const float mx[4],
+                                               const float mn[4], float m00, float m01, float m02, float m11,
+                                               float m12, float m22, float xm, const float4* __restrict__ shx,
+                                               int k0, int k1, int limiter, float lim_eps2) {
+  float gr[4][3], psi[4], eg[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    gr[q][0] = m00 * r[q][0] + m01 * r[q][1] + m02 * r[q][2];
+    gr[q][1] = m01 * r[q][0] + m11 * r[q][1] + m12 * r[q][2];
+    gr[q][2] = m02 * r[q][0] + m12 * r[q][1] + m22 * r[q][2];
+    eg[q] = sqrtf(lim_eps2 * (gr[q][0] * gr[q][0] + gr[q][1] * gr[q][1] + gr[q][2] * gr[q][2]));
+    psi[q] = 1.f;
+  }
+  if (limiter) {
+    float dpos[4], dneg[4];
+    if constexpr (Pairs) lim_extremes_pairs(shx, k0, k1, gr, eg, xm, dpos, dneg);
+    else lim_extremes(shx, k0, k1, gr, eg, xm, dpos, dneg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float vi = comp<float>(pi, q);
+      if (dpos[q] > 0.f) psi[q] = fminf(psi[q], (mx[q] - vi) / dpos[q]);
+      if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
+    }
+  }
+  // groups 0-1 and 2-3 as two 32-byte stores
+  float4* G4 = reinterpret_cast<float4*>(G);
+  st8(reinterpret_cast<f8*>(G4 + grec(i, 0, b, g.Bp)), gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0],
+      gr[1][0] * psi[1], gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
+  st8(reinterpret_cast<f8*>(G4 + grec(i, 2, b, g.Bp)), gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3],
+      gr[3][2] * psi[3], pi.x, pi.y, pi.z, pi.w);
+}
+
+
 // The same gradients and limiter for the FP32 sweep with the half-edge
 // records staged in shared memory.  A block owns kGradCells cells: in block
 // mode kGradCells consecutive cells, whose records are one contiguous range
@@ -576,53 +687,38 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
     r[q][0] = r[q][1] = r[q][2] = 0.f;
     mx[q] = mn[q] = comp<float>(pi, q);
   }
-  auto acc_face = [&](const float4& hw, const float4& pj) {
+  auto acc_rhs = [&](const float4& hw, const float4& pj) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float vj = comp<float>(pj, q), dphi = vj - comp<float>(pi, q);
+      const float dphi = comp<float>(pj, q) - comp<float>(pi, q);
       r[q][0] += hw.x * dphi;
       r[q][1] += hw.y * dphi;
       r[q][2] += hw.z * dphi;
-      mx[q] = fmaxf(mx[q], vj);
-      mn[q] = fminf(mn[q], vj);
     }
   };
   // neighbour states NB at a time, the last batch predicated (no serial
-  // tail of single loads); the sums still run in CSR order
+  // tail of single loads); the sums still run in CSR order.  The extremes
+  // take the batch by three-input max / min, the entries past the cell's
+  // last face filled with its own state (the extremes start from it).
+  static_assert(NB % 2 == 0, "neighbour batches in pairs");
   for (int k = k0; k < k1; k += NB) {
     float4 pj[NB];
 #pragma unroll
     for (int u = 0; u < NB; ++u)
-      pj[u] = k + u < k1 ? __ldg(rad + (size_t)bits_id(shw[k + u].w) * B + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+      pj[u] = k + u < k1 ? __ldg(rad + (size_t)bits_id(shw[k + u].w) * B + b) : pi;
 #pragma unroll
     for (int u = 0; u < NB; ++u)
-      if (k + u < k1) acc_face(shw[k + u], pj[u]);
-  }
-  float gr[4][3], psi[4], eg[4];
+      if (k + u < k1) acc_rhs(shw[k + u], pj[u]);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    gr[q][0] = m00 * r[q][0] + m01 * r[q][1] + m02 * r[q][2];
-    gr[q][1] = m01 * r[q][0] + m11 * r[q][1] + m12 * r[q][2];
-    gr[q][2] = m02 * r[q][0] + m12 * r[q][1] + m22 * r[q][2];
-    eg[q] = sqrtf(lim_eps2 * (gr[q][0] * gr[q][0] + gr[q][1] * gr[q][1] + gr[q][2] * gr[q][2]));
-    psi[q] = 1.f;
-  }
-  if (limiter) {
-    float dpos[4], dneg[4];
-    lim_extremes(shx, k0, k1, gr, eg, xm, dpos, dneg);
+    for (int u = 0; u < NB; u += 2)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float vi = comp<float>(pi, q);
-      if (dpos[q] > 0.f) psi[q] = fminf(psi[q], (mx[q] - vi) / dpos[q]);
-      if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
-    }
+      for (int q = 0; q < 4; ++q) {
+        mx[q] = max3f(mx[q], comp<float>(pj[u], q), comp<float>(pj[u + 1], q));
+        mn[q] = min3f(mn[q], comp<float>(pj[u], q), comp<float>(pj[u + 1], q));
+      }
   }
-  // groups 0-1 and 2-3 as two 32-byte stores
-  float4* G4 = reinterpret_cast<float4*>(G);
-  st8(reinterpret_cast<f8*>(G4 + grec(i, 0, b, g.Bp)), gr[0][0] * psi[0], gr[0][1] * psi[0], gr[0][2] * psi[0],
-      gr[1][0] * psi[1], gr[1][1] * psi[1], gr[1][2] * psi[1], gr[2][0] * psi[2], gr[2][1] * psi[2]);
-  st8(reinterpret_cast<f8*>(G4 + grec(i, 2, b, g.Bp)), gr[2][2] * psi[2], gr[3][0] * psi[3], gr[3][1] * psi[3],
-      gr[3][2] * psi[3], pi.x, pi.y, pi.z, pi.w);
+  grad_tail_fp32<true>(g, G, i, b, pi, r, mx, mn, m00, m01, m02, m11, m12, m22, xm, shx, k0, k1, limiter,
+                       lim_eps2);
 }
 
 // ---------------------------------------------------------------------------
@@ -806,7 +902,8 @@ struct CellArgs {
   const int32_t* csr;
   const double* vol;       // V_i (L_u^3)
   const double* ivol;      // 1 / V_i (mixed precision only)
-  d4* rad;            // master radiation (FP64)
+  d4* rad;                 // FP64 sweep: radiation records (N, f) per (cell, bin)
+  double* radN;            // mixed precision: N per (cell, bin) in FP64 (the flux is in the FP32 sweep records)
   double* nH;
   double* x5;              // 5*C
   double* T;
@@ -831,107 +928,104 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 // The flux application's sum for (cell i, bin b): the cell's stored face
 // fluxes in CSR order, + where the cell is the left cell, - where it is the
-// right cell.  Comp (mixed precision): the FP32 terms summed as an
-// unevaluated FP32 pair hi + lo (error-free two_sum), widened to FP64 once;
-// otherwise each term widened and summed in FP64.  Pred: the face loads in
-// batches of four with a predicated last batch (no serial tail of single
-// loads) -- faster where the flux array is held in L2, slower where the
-// loads go to HBM and the extra registers cost occupancy.
-template <class R, bool Comp, bool Pred>
-__device__ __forceinline__ void flux_sum(const CellArgs& a, const R4<R>* __restrict__ flux, int i, int b,
-                                         double acc[4]) {
+// right cell.  flux_sum_pair (mixed precision): the FP32 terms summed as an
+// unevaluated FP32 pair hi + lo (error-free two_sum).  flux_sum: each term
+// widened and summed in FP64.  Pred: the face loads in batches of four with
+// a predicated last batch (no serial tail of single loads) -- faster where
+// the flux array is held in L2, slower where the loads go to HBM and the
+// extra registers cost occupancy.
+template <bool Pred>
+__device__ __forceinline__ void flux_sum_pair(const CellArgs& a, const float4* __restrict__ flux, int i, int b,
+                                              float hi[4], float lo[4]) {
   const int B = a.B;
   const int k0 = a.off[i], k1 = a.off[i + 1];
-  if (Comp) {
-    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    auto add = [&](int e, const R4<R>& v) {
-      const float sg = (e & 1) ? -1.0f : 1.0f;
-      const float tv[4] = {sg * (float)v.x, sg * (float)v.y, sg * (float)v.z, sg * (float)v.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float sum, err;
-        two_sum(hi[q], tv[q], sum, err);
-        hi[q] = sum;
-        lo[q] += err;
-      }
-    };
-    if constexpr (Pred) {
-      for (int k = k0; k < k1; k += 4) {
-        int e[4];
-        R4<R> v[4];
+  for (int q = 0; q < 4; ++q) hi[q] = lo[q] = 0.f;
+  auto add = [&](int e, const float4& v) {
+    const float sg = (e & 1) ? -1.0f : 1.0f;
+    const float tv[4] = {sg * v.x, sg * v.y, sg * v.z, sg * v.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? __ldg(a.csr + k + u) : 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (k + u < k1) v[u] = ld4<R>(flux + (size_t)(e[u] >> 1) * B + b);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (k + u < k1) add(e[u], v[u]);
-      }
-    } else {
-      int k = k0;
-      // batches of four faces: all index and flux loads issued before use;
-      // the terms are still added in CSR order
-      for (; k + 4 <= k1; k += 4) {
-        const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
-                  e3 = __ldg(a.csr + k + 3);
-        const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
-                    v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
-        add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
-      }
-      for (; k < k1; ++k) {
-        const int e = __ldg(a.csr + k);
-        add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
-      }
+    for (int q = 0; q < 4; ++q) {
+      float sum, err;
+      two_sum(hi[q], tv[q], sum, err);
+      hi[q] = sum;
+      lo[q] += err;
     }
+  };
+  if constexpr (Pred) {
+    for (int k = k0; k < k1; k += 4) {
+      int e[4];
+      float4 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = f2d_int(hi[q]) + f2d_int(lo[q]);
+      for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? __ldg(a.csr + k + u) : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k + u < k1) v[u] = __ldg(flux + (size_t)(e[u] >> 1) * B + b);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k + u < k1) add(e[u], v[u]);
+    }
   } else {
-    acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-    // acc +- v as one fused multiply-add by +-1 (exact product, one
-    // rounding: the same sum as the add or subtract, without predicated
-    // copies of both)
-    auto add = [&](int e, const R4<R>& v) {
-      const double sg = (e & 1) ? -1.0 : 1.0;
-      acc[0] = fma(sg, (double)v.x, acc[0]);
-      acc[1] = fma(sg, (double)v.y, acc[1]);
-      acc[2] = fma(sg, (double)v.z, acc[2]);
-      acc[3] = fma(sg, (double)v.w, acc[3]);
-    };
     int k = k0;
+    // batches of four faces: all index and flux loads issued before use;
+    // the terms are still added in CSR order
     for (; k + 4 <= k1; k += 4) {
       const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
                 e3 = __ldg(a.csr + k + 3);
-      const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
-                  v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
+      const float4 v0 = __ldg(flux + (size_t)(e0 >> 1) * B + b), v1 = __ldg(flux + (size_t)(e1 >> 1) * B + b),
+                   v2 = __ldg(flux + (size_t)(e2 >> 1) * B + b), v3 = __ldg(flux + (size_t)(e3 >> 1) * B + b);
       add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
     }
     for (; k < k1; ++k) {
       const int e = __ldg(a.csr + k);
-      add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
+      add(e, __ldg(flux + (size_t)(e >> 1) * B + b));
     }
   }
 }
 
-// U <- U - c dt / V * sum (FP32 sweep: lam (1/V) with 1/V formed once per
-// mesh, one FP64 multiply instead of a division per subcycle; the FP64 sweep
-// divides as defined).
-template <class R> __device__ __forceinline__ double gather_kfac(const CellArgs& a, int i) {
-  return sizeof(R) == 4 ? a.lam * __ldg(a.ivol + i) : a.lam / a.vol[i];
-}
-__device__ __forceinline__ void sub_flux(d4& u, double kfac, const double acc[4]) {
-  u.x -= kfac * acc[0];
-  u.y -= kfac * acc[1];
-  u.z -= kfac * acc[2];
-  u.w -= kfac * acc[3];
+template <class R>
+__device__ __forceinline__ void flux_sum(const CellArgs& a, const R4<R>* __restrict__ flux, int i, int b,
+                                         double acc[4]) {
+  const int B = a.B;
+  const int k0 = a.off[i], k1 = a.off[i + 1];
+  acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+  // acc +- v as one fused multiply-add by +-1 (exact product, one
+  // rounding: the same sum as the add or subtract, without predicated
+  // copies of both)
+  auto add = [&](int e, const R4<R>& v) {
+    const double sg = (e & 1) ? -1.0 : 1.0;
+    acc[0] = fma(sg, (double)v.x, acc[0]);
+    acc[1] = fma(sg, (double)v.y, acc[1]);
+    acc[2] = fma(sg, (double)v.z, acc[2]);
+    acc[3] = fma(sg, (double)v.w, acc[3]);
+  };
+  int k = k0;
+  for (; k + 4 <= k1; k += 4) {
+    const int e0 = __ldg(a.csr + k), e1 = __ldg(a.csr + k + 1), e2 = __ldg(a.csr + k + 2),
+              e3 = __ldg(a.csr + k + 3);
+    const R4<R> v0 = ld4<R>(flux + (size_t)(e0 >> 1) * B + b), v1 = ld4<R>(flux + (size_t)(e1 >> 1) * B + b),
+                v2 = ld4<R>(flux + (size_t)(e2 >> 1) * B + b), v3 = ld4<R>(flux + (size_t)(e3 >> 1) * B + b);
+    add(e0, v0); add(e1, v1); add(e2, v2); add(e3, v3);
+  }
+  for (; k < k1; ++k) {
+    const int e = __ldg(a.csr + k);
+    add(e, ld4<R>(flux + (size_t)(e >> 1) * B + b));
+  }
 }
 
 // Flux application, one thread per (cell, bin): U <- U - c dt / V * sum of
-// the cell's stored face fluxes (flux_sum) in FP64.  Writes the FP32 shadow
-// if given.  Heun: the kernel handles Heun's stages (a.heun); the plain
-// update is its own instantiation, without the stages' code (which the
-// compiler would otherwise issue as predicated FP64 instructions on every
-// launch).
+// the cell's stored face fluxes.  Heun: the kernel handles Heun's stages
+// (a.heun); the plain update is its own instantiation, without the stages'
+// code (which the compiler would otherwise issue as predicated FP64
+// instructions on every launch).
+//
+// FP64 sweep (R = double): the interleaved FP64 records, c dt / V divided
+// as defined.  Mixed precision (R = float): c dt (1/V) with 1/V formed once
+// per mesh (one FP64 multiply instead of a division per subcycle); N is
+// updated in FP64 (radN) and the reduced flux in FP32 in the sweep record,
+// whose N lane is then refreshed.  Comp: the face terms summed as an FP32
+// pair (flux_sum_pair) and widened to FP64 once for N; otherwise summed in
+// FP64 (flux_sum).
 template <class R, bool Comp, bool Pred = false, bool Heun = false>
 __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restrict__ flux,
                                                 float4* __restrict__ shadow) {
@@ -941,22 +1035,67 @@ __global__ void __launch_bounds__(256) k_gather(CellArgs a, const R4<R>* __restr
   const int ii = divb(t, a.divB), b = t - ii * B;
   const int i = a.list ? __ldg(a.list + ii) : ii;
   t = i * B + b;
-  double acc[4];
-  flux_sum<R, Comp, Pred>(a, flux, i, b, acc);
-  const double kfac = gather_kfac<R>(a, i);
-  d4 u = a.rad[t];
-  if (Heun && a.heun == 1) a.rad0[t] = u;
-  sub_flux(u, kfac, acc);
-  if (Heun && a.heun == 2) {
-    const d4 u0 = a.rad0[t];
-    u.x = 0.5 * u0.x + 0.5 * u.x;
-    u.y = 0.5 * u0.y + 0.5 * u.y;
-    u.z = 0.5 * u0.z + 0.5 * u.z;
-    u.w = 0.5 * u0.w + 0.5 * u.w;
+  if constexpr (sizeof(R) == 4) {
+    // the state is loaded after the face sum (fewer registers live across
+    // the loop)
+    double N;
+    float4 u;
+    if constexpr (Comp) {
+      float hi[4], lo[4];
+      flux_sum_pair<Pred>(a, flux, i, b, hi, lo);
+      const double kfac = a.lam * __ldg(a.ivol + i);
+      N = a.radN[t];
+      u = shadow[t];
+      if (Heun && a.heun == 1) a.rad0[t] = make_d4(N, f2d_int(u.y), f2d_int(u.z), f2d_int(u.w));
+      N -= kfac * (f2d_int(hi[0]) + f2d_int(lo[0]));
+      const float kf = d2f_int(kfac);
+      u.y = fmaf(-kf, hi[1], fmaf(-kf, lo[1], u.y));
+      u.z = fmaf(-kf, hi[2], fmaf(-kf, lo[2], u.z));
+      u.w = fmaf(-kf, hi[3], fmaf(-kf, lo[3], u.w));
+    } else {
+      double acc[4];
+      flux_sum<float>(a, flux, i, b, acc);
+      const double kfac = a.lam * __ldg(a.ivol + i);
+      N = a.radN[t];
+      u = shadow[t];
+      if (Heun && a.heun == 1) a.rad0[t] = make_d4(N, f2d_int(u.y), f2d_int(u.z), f2d_int(u.w));
+      N -= kfac * acc[0];
+      u.y = d2f_int(f2d_int(u.y) - kfac * acc[1]);
+      u.z = d2f_int(f2d_int(u.z) - kfac * acc[2]);
+      u.w = d2f_int(f2d_int(u.w) - kfac * acc[3]);
+    }
+    if (Heun && a.heun == 2) {
+      const d4 u0 = a.rad0[t];
+      N = 0.5 * u0.x + 0.5 * N;
+      u.y = d2f_int(0.5 * u0.y + 0.5 * f2d_int(u.y));
+      u.z = d2f_int(0.5 * u0.z + 0.5 * f2d_int(u.z));
+      u.w = d2f_int(0.5 * u0.w + 0.5 * f2d_int(u.w));
+    }
+    a.radN[t] = N;
+    if (nonfinite_bits(N)) atomicOr(a.status, kStNonFinite);
+    u.x = d2f_int(N);
+    shadow[t] = u;
+    return;
+  } else {
+    double acc[4];
+    flux_sum<R>(a, flux, i, b, acc);
+    const double kfac = a.lam / a.vol[i];
+    d4 u = a.rad[t];
+    if (Heun && a.heun == 1) a.rad0[t] = u;
+    u.x -= kfac * acc[0];
+    u.y -= kfac * acc[1];
+    u.z -= kfac * acc[2];
+    u.w -= kfac * acc[3];
+    if (Heun && a.heun == 2) {
+      const d4 u0 = a.rad0[t];
+      u.x = 0.5 * u0.x + 0.5 * u.x;
+      u.y = 0.5 * u0.y + 0.5 * u.y;
+      u.z = 0.5 * u0.z + 0.5 * u.z;
+      u.w = 0.5 * u0.w + 0.5 * u.w;
+    }
+    a.rad[t] = u;
+    if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
   }
-  a.rad[t] = u;
-  if (!isfinite(u.x)) atomicOr(a.status, kStNonFinite);
-  if (shadow) shadow[t] = make_float4(d2f_int(u.x), d2f_int(u.y), d2f_int(u.z), d2f_int(u.w));
 }
 
 __global__ void k_reciprocal(int n, const double* __restrict__ in, double* out) {
@@ -995,7 +1134,7 @@ __device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasSta
   const int B = a.B;
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b)
-    if (b < B) s.N[b] = a.rad[(size_t)i * B + b].x;
+    if (b < B) s.N[b] = a.radN[(size_t)i * B + b];
   if (inject) {
     const int si = a.src_idx[i];
     if (si >= 0) inject_cell(a, i, si, s.N);
@@ -1005,22 +1144,23 @@ __device__ __forceinline__ void chem_load_mixed(const CellArgs& a, int i, GasSta
   s.yIII = a.x5[4 * C + i]; s.T = a.T[i];
 }
 
-// Final state of a cell: radiation (flux scaled by S), shadow, gas, count.
-// The flux is read from u_in (the cell's master records, or a copy of them).
+// Final state of a cell: N (FP64), the FP32 sweep record (N rounded, the
+// reduced flux scaled by S in FP32), gas, attempt count.
 __device__ __forceinline__ void chem_store_mixed(const CellArgs& a, int i, const GasState& s,
-                                                 const double S[kMaxBins], int n, bool gas,
-                                                 float4* __restrict__ shadow, const d4* u_in = nullptr) {
+                                                 const float S[kMaxBins], int n, bool gas,
+                                                 float4* __restrict__ shadow) {
   const int B = a.B;
   bool bad = false;
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
     if (b < B) {
-      d4* r = a.rad + (size_t)i * B + b;
-      const d4 u = u_in ? u_in[b] : *r;
-      const d4 o = make_d4(s.N[b], u.y * S[b], u.z * S[b], u.w * S[b]);
-      *r = o;
-      if (!isfinite(o.x)) bad = true;
-      if (shadow) shadow[(size_t)i * B + b] = make_float4(d2f_int(o.x), d2f_int(o.y), d2f_int(o.z), d2f_int(o.w));
+      const size_t t = (size_t)i * B + b;
+      a.radN[t] = s.N[b];
+      float4 u = shadow[t];
+      u.x = d2f_int(s.N[b]);
+      u.y *= S[b]; u.z *= S[b]; u.w *= S[b];
+      shadow[t] = u;
+      if (nonfinite_bits(s.N[b])) bad = true;
     }
   }
   if (bad) atomicOr(a.status, kStNonFinite);
@@ -1032,15 +1172,15 @@ __device__ __forceinline__ void chem_store_mixed(const CellArgs& a, int i, const
   }
 }
 
-__global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, float4* __restrict__ shadow,
+__global__ void __launch_bounds__(128, 6) k_chem_first(CellArgs a, ChemParams P, float4* __restrict__ shadow,
                                                     ChemWork w) {
   const int ii = blockIdx.x * blockDim.x + threadIdx.x;
   if (ii >= (a.list ? a.n : a.C)) return;
   const int i = a.list ? __ldg(a.list + ii) : ii;
   GasState s;
-  double S[kMaxBins];
+  float S[kMaxBins];
 #pragma unroll
-  for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0;
+  for (int b = 0; b < kMaxBins; ++b) S[b] = 1.0f;
   chem_load_mixed(a, i, s, a.do_inject);
   if (!a.do_chem) {
     chem_store_mixed(a, i, s, S, 0, false, shadow);
@@ -1054,7 +1194,7 @@ __global__ void __launch_bounds__(128) k_chem_first(CellArgs a, ChemParams P, fl
   // rejected: keep the injected photons, hand the cell to the second pass
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b)
-    if (b < a.B) a.rad[(size_t)i * a.B + b].x = s.N[b];
+    if (b < a.B) a.radN[(size_t)i * a.B + b] = s.N[b];
   const int k = atomicAdd(w.ctl, 1);
   w.cell[k] = i;
   w.f1[k] = f1;
@@ -1081,7 +1221,7 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
     if (k < total) {
       const int i = w.cell[k];
       GasState s;
-      double S[kMaxBins];
+      float S[kMaxBins];
       chem_load_mixed(a, i, s, false);
       bool capped;
       const double dt0 = a.dt * f2d_int(__fdividef((float)P.f_s, w.f1[k]));
