@@ -115,10 +115,26 @@ struct RatesF {
   float aHII, aHeII, aHeIII, bHI, bHeI, bHeII;
 };
 
+// Precision conversions of the mixed chemistry.  IntCvt: assembled on the
+// integer pipe (d2f_int, f2d_int), for the first pass over every cell, where
+// the FP64 pipe bounds the kernel; otherwise the hardware's conversions, for
+// the worklist pass, where a few stiff cells run long serial chains of
+// attempts and an attempt's latency counts: one instruction instead of ten.
+// The two round alike (to nearest) but for exact ties and subnormal values.
+template <bool IntCvt> __device__ __forceinline__ float to_f(double x) {
+  if constexpr (IntCvt) return d2f_int(x);
+  else return __double2float_rn(x);
+}
+template <bool IntCvt> __device__ __forceinline__ double to_d(float x) {
+  if constexpr (IntCvt) return f2d_int(x);
+  else return (double)x;
+}
+
 template <> struct RateEval<true> {
   // the rate fits in FP32
+  template <bool IntCvt = true>
   __device__ static RatesF eval_f(double Td) {
-    const float T = d2f_int(Td);
+    const float T = to_f<IntCvt>(Td);
     const float iT = __frcp_rn(T);
     RatesF r;
     const float lH = 315614.0f * iT;
@@ -139,9 +155,10 @@ template <> struct RateEval<true> {
   // FP32 images of the densities (the coefficients, ~1e-27..1e-19, times
   // 1/kCoolScale lie in the FP32 normal range together with the densities'
   // products); it only enters the energy increment.
+  template <bool IntCvt = true>
   __device__ static float cooling_scaled(double Td, float ne, float nHI, float nHII, float nHeI, float nHeII,
                                          float nHeIII) {
-    const float T = d2f_int(Td), iT = __frcp_rn(T);
+    const float T = to_f<IntCvt>(Td), iT = __frcp_rn(T);
     const float sT = sqrtf(T), tf = 1.0f / (1.0f + sqrtf(T * 1e-5f));
     const float ex1 = fexp(-157809.1f * iT), ex2 = fexp(-285335.4f * iT), ex3 = fexp(-631515.0f * iT);
     // coefficients of the KWH96 fits times 1/kCoolScale = 1e27
@@ -263,10 +280,11 @@ __device__ double photochem_attempt(const ChemParams& P, double nH, double dt, c
 // FP64 reciprocal: FP32 hardware seed (~22 bits) refined by one Newton step
 // in FP64 (~44 bits, relative error below 1e-13), for x in the FP32 normal
 // range, which every denominator of the chemistry step lies in.
+template <bool IntCvt = true>
 __device__ __forceinline__ double rcp64(double x) {
-  const float xf = d2f_int(x);
+  const float xf = to_f<IntCvt>(x);
   if (!(fabsf(xf) < 1e30f && fabsf(xf) > 1e-30f)) return 1.0 / x;
-  const double y = f2d_int(rcp_approx(xf));
+  const double y = to_d<IntCvt>(rcp_approx(xf));
   return fma(y, fma(-x, y, 1.0), y);   // one Newton step: ~2^-44 relative
 }
 
@@ -274,8 +292,9 @@ __device__ __forceinline__ double rcp64(double x) {
 // a and b: it only steers substep lengths and the 10% test, and the FP32
 // cancellation for nearly equal a, b changes f by ~1e-7, far below both
 // the 0.1 threshold and the growth cap's switch point.
+template <bool IntCvt = true>
 __device__ __forceinline__ float rel_change_f(double a, double b, float fl) {
-  const float af = d2f_int(a), bf = d2f_int(b);
+  const float af = to_f<IntCvt>(a), bf = to_f<IntCvt>(b);
   const float m = fmaxf(fabsf(af), fl);
   return __fdividef(fabsf(bf - af), m);
 }
@@ -297,6 +316,7 @@ struct GasState {
   double xHI, xHII, yI, yII, yIII, T;
 };
 
+template <bool IntCvt>
 __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double dt, const GasState& s,
                                          GasState& t, float sc_out[kMaxBins]) {
   const int B = P.B;
@@ -306,7 +326,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   const bool recomb = P.flags & 1, coll = P.flags & 2, cool = P.flags & 4, heat = P.flags & 8;
   // rate coefficients and their products with n_e in FP32 (the fits carry
   // FP32 accuracy already); the photoionisation terms and the updates FP64
-  const RatesF r = RateEval<true>::eval_f(s.T);
+  const RatesF r = RateEval<true>::template eval_f<IntCvt>(s.T);
 
   const double ns[3] = {nH * s.xHI, nHe * s.yI, nHe * s.yII};
   double inv1pt[kMaxBins], Nbar[kMaxBins];
@@ -320,7 +340,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 #pragma unroll
       for (int sp = 0; sp < 3; ++sp)
         if (P.smask & (1 << (3 * b + sp))) kap = fma(P.sigma[b][sp], ns[sp], kap);
-      inv1pt[b] = rcp64(fma(cdt, kap, 1.0));
+      inv1pt[b] = rcp64<IntCvt>(fma(cdt, kap, 1.0));
       Nbar[b] = s.N[b] * inv1pt[b];
 #pragma unroll
       for (int sp = 0; sp < 3; ++sp)
@@ -330,25 +350,25 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   const double G0 = Gs[0], G1 = Gs[1], G2 = Gs[2];
   // n_e enters only the FP32 products with the rate coefficients (and the
   // FP32 cooling): formed in FP32 from the FP32 images of the densities
-  const float nHf = d2f_int(nH), nHef = d2f_int(nHe);
-  const float ne_he = nHef * fmaf(2.0f, d2f_int(s.yIII), d2f_int(s.yII));
-  const float ne0f = fmaf(nHf, d2f_int(s.xHII), ne_he);
-  const double aH = coll ? fma(dt, f2d_int(r.bHI * ne0f), cdt * G0) : cdt * G0;
-  const double bH = recomb ? dt * f2d_int(r.aHII * ne0f) : 0.0;
-  const double iden = rcp64(1.0 + aH + bH);
+  const float nHf = to_f<IntCvt>(nH), nHef = to_f<IntCvt>(nHe);
+  const float ne_he = nHef * fmaf(2.0f, to_f<IntCvt>(s.yIII), to_f<IntCvt>(s.yII));
+  const float ne0f = fmaf(nHf, to_f<IntCvt>(s.xHII), ne_he);
+  const double aH = coll ? fma(dt, to_d<IntCvt>(r.bHI * ne0f), cdt * G0) : cdt * G0;
+  const double bH = recomb ? dt * to_d<IntCvt>(r.aHII * ne0f) : 0.0;
+  const double iden = rcp64<IntCvt>(1.0 + aH + bH);
   // backward Euler for (x_HI, x_HII): x_HI' = (x_HI + bH (x_HI + x_HII)) / (1
   // + aH + bH), and the same for x_HII with aH -- the two-state solve with
   // the sum of both fractions shared
   const double xs = s.xHI + s.xHII;
   t.xHI = fma(bH, xs, s.xHI) * iden;
   t.xHII = fma(aH, xs, s.xHII) * iden;
-  const float ne1f = fmaf(nHf, d2f_int(t.xHII), ne_he);
-  const double A = coll ? fma(dt, f2d_int(r.bHeI * ne1f), cdt * G1) : cdt * G1;
-  const double Bb = recomb ? dt * f2d_int(r.aHeII * ne1f) : 0.0;
-  const double Cc = coll ? fma(dt, f2d_int(r.bHeII * ne1f), cdt * G2) : cdt * G2;
-  const double D = recomb ? dt * f2d_int(r.aHeIII * ne1f) : 0.0;
-  const double iA = rcp64(1.0 + A), iD = rcp64(1.0 + D);
-  t.yII = (s.yII + A * s.yI * iA + D * s.yIII * iD) * rcp64(1.0 + Bb * iA + Cc * iD);
+  const float ne1f = fmaf(nHf, to_f<IntCvt>(t.xHII), ne_he);
+  const double A = coll ? fma(dt, to_d<IntCvt>(r.bHeI * ne1f), cdt * G1) : cdt * G1;
+  const double Bb = recomb ? dt * to_d<IntCvt>(r.aHeII * ne1f) : 0.0;
+  const double Cc = coll ? fma(dt, to_d<IntCvt>(r.bHeII * ne1f), cdt * G2) : cdt * G2;
+  const double D = recomb ? dt * to_d<IntCvt>(r.aHeIII * ne1f) : 0.0;
+  const double iA = rcp64<IntCvt>(1.0 + A), iD = rcp64<IntCvt>(1.0 + D);
+  t.yII = (s.yII + A * s.yI * iA + D * s.yIII * iD) * rcp64<IntCvt>(1.0 + Bb * iA + Cc * iD);
   t.yI = (s.yI + Bb * t.yII) * iA;
   t.yIII = (s.yIII + Cc * t.yII) * iD;
 
@@ -359,7 +379,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
   float hsum = 0.0f;
   float mf[3] = {0.0f, 0.0f, 0.0f};
   if (heat) {
-    mf[0] = d2f_int(m[0]); mf[1] = d2f_int(m[1]); mf[2] = d2f_int(m[2]);
+    mf[0] = to_f<IntCvt>(m[0]); mf[1] = to_f<IntCvt>(m[1]); mf[2] = to_f<IntCvt>(m[2]);
   }
 #pragma unroll
   for (int b = 0; b < kMaxBins; ++b) {
@@ -378,10 +398,10 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 #pragma unroll
         for (int sp = 0; sp < 3; ++sp)
           if (P.emask & P.smask & (1 << (3 * b + sp))) ea = fmaf(P.heat_f[b][sp], mf[sp], ea);
-        hsum = fmaf(d2f_int(Nbar[b]), ea, hsum);
+        hsum = fmaf(to_f<IntCvt>(Nbar[b]), ea, hsum);
       }
       t.N[b] = s.N[b] * sc;
-      sc_out[b] = d2f_int(sc);
+      sc_out[b] = to_f<IntCvt>(sc);
     }
   }
 
@@ -393,30 +413,30 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
     // change of n_e is FP64 and the increment is formed in FP32
     float lam_s = 0.0f;
     if (cool) {
-      lam_s = RateEval<true>::cooling_scaled(s.T, ne0f, nHf * d2f_int(s.xHI), nHf * d2f_int(s.xHII),
-                                             nHef * d2f_int(s.yI), nHef * d2f_int(s.yII), nHef * d2f_int(s.yIII));
+      lam_s = RateEval<true>::template cooling_scaled<IntCvt>(s.T, ne0f, nHf * to_f<IntCvt>(s.xHI), nHf * to_f<IntCvt>(s.xHII),
+                                             nHef * to_f<IntCvt>(s.yI), nHef * to_f<IntCvt>(s.yII), nHef * to_f<IntCvt>(s.yIII));
     }
-    const float de = fmaf(heat ? d2f_int(cdt * kHeatScale) : 0.0f, hsum, -(d2f_int(dt * kCoolScale) * lam_s));
+    const float de = fmaf(heat ? to_f<IntCvt>(cdt * kHeatScale) : 0.0f, hsum, -(to_f<IntCvt>(dt * kCoolScale) * lam_s));
     // the change of n_e from the FP64 differences of the fractions (they
     // cancel), combined in FP32
-    const float dnef = fmaf(nHf, d2f_int(t.xHII - s.xHII),
-                            nHef * fmaf(2.0f, d2f_int(t.yIII - s.yIII), d2f_int(t.yII - s.yII)));
-    const float T0 = d2f_int(s.T);
+    const float dnef = fmaf(nHf, to_f<IntCvt>(t.xHII - s.xHII),
+                            nHef * fmaf(2.0f, to_f<IntCvt>(t.yIII - s.yIII), to_f<IntCvt>(t.yII - s.yII)));
+    const float T0 = to_f<IntCvt>(s.T);
     const float ntot0 = nHf * (1.0f + (float)P.y_he) + ne0f;
     const float ntot1 = ntot0 + dnef;
     constexpr float kInv15k = (float)(1.0 / (1.5 * kBoltzmann));
-    t.T = s.T + f2d_int(__fdividef(fmaf(de, kInv15k, -T0 * dnef), ntot1));
+    t.T = s.T + to_d<IntCvt>(__fdividef(fmaf(de, kInv15k, -T0 * dnef), ntot1));
     // the measure |e' - e| / |e| = |de| / (3/2 k n_tot T)
     f = __fdividef(fabsf(de) * kInv15k, ntot0 * T0);
   } else {
     t.T = s.T;
   }
-  f = fmaxf(f, rel_change_f(s.xHI, t.xHI, fl));
-  f = fmaxf(f, rel_change_f(s.xHII, t.xHII, fl));
+  f = fmaxf(f, rel_change_f<IntCvt>(s.xHI, t.xHI, fl));
+  f = fmaxf(f, rel_change_f<IntCvt>(s.xHII, t.xHII, fl));
   if (P.y_he > 0) {
-    f = fmaxf(f, rel_change_f(s.yI, t.yI, fl));
-    f = fmaxf(f, rel_change_f(s.yII, t.yII, fl));
-    f = fmaxf(f, rel_change_f(s.yIII, t.yIII, fl));
+    f = fmaxf(f, rel_change_f<IntCvt>(s.yI, t.yI, fl));
+    f = fmaxf(f, rel_change_f<IntCvt>(s.yII, t.yII, fl));
+    f = fmaxf(f, rel_change_f<IntCvt>(s.yIII, t.yIII, fl));
   }
   return f;
 }
@@ -433,6 +453,7 @@ __device__ float photochem_attempt_mixed(const ChemParams& P, double nH, double 
 // FP32 like the flux it scales).
 // The loop can resume after a rejected first attempt (two-pass chemistry):
 // dt0 = the next attempt's length, n0 = attempts already made.
+template <bool IntCvt>
 __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, GasState& s,
                                float S[kMaxBins], bool* capped, double dt0, int n0) {
   double rem = dt_sub, dt = dt0;
@@ -444,9 +465,9 @@ __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, Ga
   while (__double_as_longlong(rem) > 0) {
     if (n >= P.max_sub) { *capped = true; break; }
     ++n;
-    const float f = photochem_attempt_mixed(P, nH, dt, s, t, sc);
+    const float f = photochem_attempt_mixed<IntCvt>(P, nH, dt, s, t, sc);
     if (f > fmax) {
-      dt = dt * f2d_int(__fdividef(fs, f));
+      dt = dt * to_d<IntCvt>(__fdividef(fs, f));
       continue;
     }
     s = t;
@@ -455,7 +476,7 @@ __device__ int chemistry_mixed(const ChemParams& P, double nH, double dt_sub, Ga
     ++acc;
     rem = (__double_as_longlong(dt) == __double_as_longlong(rem)) ? 0.0 : rem - dt;
     const float grow = f > 0.0f ? fminf(__fdividef(fs, f), 2.0f) : 2.0f;
-    dt = dt * f2d_int(grow);
+    dt = dt * to_d<IntCvt>(grow);
     if (__double_as_longlong(dt) > __double_as_longlong(rem)) dt = rem;
   }
   if (acc == 0) {
@@ -473,7 +494,7 @@ __device__ bool chemistry_mixed_first(const ChemParams& P, double nH, double dt_
                                       float S[kMaxBins], float* f1) {
   GasState t;
   float sc[kMaxBins];
-  const float f = photochem_attempt_mixed(P, nH, dt_sub, s, t, sc);
+  const float f = photochem_attempt_mixed<true>(P, nH, dt_sub, s, t, sc);
   *f1 = f;
   if (f > (float)P.f_max) return false;
   s = t;

@@ -1109,10 +1109,14 @@ __global__ void k_reciprocal(int n, const double* __restrict__ in, double* out) 
 // divergence of the substep loop): k_chem_first makes the first attempt of
 // every cell over the whole subcycle -- one attempt per lane, no divergence
 // -- and finishes the cells it accepts; the cells it rejects go to a
-// worklist that k_chem_rest works through with the adaptive loop.  The
-// attempts of each cell, and so its result, are those of one pass.  The
-// attempts carry N and the gas only; the flux is read at the end and
-// scaled by the product of the accepted photon factors.
+// worklist that k_chem_rest works through with the adaptive loop.  Each
+// cell makes the attempts one pass would make: the first pass converts
+// between FP32 and FP64 on the integer pipe (it is bound by the FP64 pipe),
+// the worklist pass with the hardware's conversions (a few stiff cells run
+// long serial chains of attempts there, bound by an attempt's latency); the
+// two round alike but for exact ties and subnormal values.  The attempts
+// carry N and the gas only; the flux is read at the end and scaled by the
+// product of the accepted photon factors.
 
 // Worklist of the cells whose first attempt was rejected.
 struct ChemWork {
@@ -1225,7 +1229,7 @@ __global__ void __launch_bounds__(128) k_chem_rest(CellArgs a, ChemParams P, flo
       chem_load_mixed(a, i, s, false);
       bool capped;
       const double dt0 = a.dt * f2d_int(__fdividef((float)P.f_s, w.f1[k]));
-      const int n = chemistry_mixed(P, a.nH[i], a.dt, s, S, &capped, dt0, 1);
+      const int n = chemistry_mixed<false>(P, a.nH[i], a.dt, s, S, &capped, dt0, 1);
       if (capped) atomicOr(a.status, kStChemSubsteps);
       chem_store_mixed(a, i, s, S, n, true, shadow);
     }
