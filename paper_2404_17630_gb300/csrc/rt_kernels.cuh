@@ -566,8 +566,10 @@ __device__ __forceinline__ void grad_tail_fp32(const Geo<float>& g, float* __res
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float vi = comp<float>(pi, q);
-      if (dpos[q] > 0.f) psi[q] = fminf(psi[q], (mx[q] - vi) / dpos[q]);
-      if (dneg[q] < 0.f) psi[q] = fminf(psi[q], (mn[q] - vi) / dneg[q]);
+      // approximate quotients (2 ulp): a limiter factor needs no
+      // correctly rounded division
+      if (dpos[q] > 0.f) psi[q] = fminf(psi[q], __fdividef(mx[q] - vi, dpos[q]));
+      if (dneg[q] < 0.f) psi[q] = fminf(psi[q], __fdividef(mn[q] - vi, dneg[q]));
     }
   }
   // groups 0-1 and 2-3 as two 32-byte stores
@@ -953,17 +955,24 @@ __device__ __forceinline__ void flux_sum_pair(const CellArgs& a, const float4* _
     }
   };
   if constexpr (Pred) {
-    for (int k = k0; k < k1; k += 4) {
-      int e[4];
-      float4 v[4];
+    // the next batch's CSR entries are loaded while this batch's fluxes are
+    // in flight (one round trip less per batch)
+    int e[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) e[u] = k + u < k1 ? __ldg(a.csr + k + u) : 0;
+    for (int u = 0; u < 4; ++u) e[u] = k0 + u < k1 ? __ldg(a.csr + k0 + u) : 0;
+    for (int k = k0; k < k1; k += 4) {
+      float4 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (k + u < k1) v[u] = __ldg(flux + (size_t)(e[u] >> 1) * B + b);
+      int en[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) en[u] = k + 4 + u < k1 ? __ldg(a.csr + k + 4 + u) : 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (k + u < k1) add(e[u], v[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = en[u];
     }
   } else {
     int k = k0;
