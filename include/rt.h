@@ -138,7 +138,10 @@ rt_status rt_init_mesh(rt_ctx *ctx, const rt_cells *cells, const rt_faces *faces
 rt_status rt_set_gas(rt_ctx *ctx, const double *nH, const double *x5, const double *T);
 
 /* Radiation: N[B*C] photon number densities (cm^-3); F[3*B*C] photon
- * fluxes (cm^-2 s^-1), stored internally as F / c_red.  F may be NULL (zero). */
+ * fluxes (cm^-2 s^-1), stored internally as F / c_red.  F may be NULL (zero).
+ * RT_FP64 keeps both in FP64.  RT_MIXED keeps N in FP64 and F / c_red in
+ * FP32 (the state the FP32 sweep reads), so rt_get_fields returns F / c_red
+ * rounded to FP32, times c_red. */
 rt_status rt_set_radiation(rt_ctx *ctx, const double *N, const double *F);
 
 /* Point sources: source k emits Q[k*B + b] photons/s in bin b into cell

@@ -330,6 +330,25 @@ def test_step_equals_separate_stages(splitting, time_order, gather_sum):
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_radiation_round_trip(precision):
+    """rt_set_radiation then rt_get_fields without a step: N comes back
+    exactly in both precisions; F exactly in FP64, and in mixed precision as
+    F / c_red rounded to FP32 (the flux state of the FP32 sweep), times
+    c_red."""
+    mesh, cfg, st = voronoi_case(n=10)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    g = rt.fields()
+    assert np.array_equal(g["N"], st["N"])
+    fr = st["fr"]
+    if precision == "fp64":
+        assert np.allclose(g["F"] / cfg["c_red"], fr, rtol=1e-15, atol=0)
+    else:
+        c = cfg["c_red"]
+        f32 = ((fr * c) * (1.0 / c)).astype(np.float32)   # as the library scales and rounds it
+        assert np.array_equal(g["F"], f32.astype(np.float64) * c)
+
+
 @pytest.mark.parametrize("n_bins", [1, 2])
 def test_mixed_step_fewer_bins(n_bins):
     """One and two frequency bins in the mixed path (gradient records with
