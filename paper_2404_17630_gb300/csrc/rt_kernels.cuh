@@ -541,10 +541,9 @@ __device__ __forceinline__ void lim_extremes_pairs(const float4* __restrict__ xs
 
 // The FP32 gradients' last part, from the least-squares right-hand sides r
 // and the neighbour extremes: g = M^-1 r, the limiter factors (extremes of
-// g . x_f over the offset records xs[k0, k1): lim_extremes_pairs where
-// Pairs, else lim_extremes), and the record of (cell i, bin b) written as
-// two 32-byte stores (groups 0-1 and 2-3).
-template <bool Pairs>
+// g . x_f over the offset records xs[k0, k1) by lim_extremes_pairs), and the
+// record of (cell i, bin b) written as two 32-byte stores (groups 0-1 and
+// 2-3).
 __device__ __forceinline__ void grad_tail_fp32(const Geo<float>& g, float* __restrict__ G, int i, int b,
                                                const float4& pi, const float r[4][3], const float mx[4],
                                                const float mn[4], float m00, float m01, float m02, float m11,
@@ -561,8 +560,7 @@ __device__ __forceinline__ void grad_tail_fp32(const Geo<float>& g, float* __res
   }
   if (limiter) {
     float dpos[4], dneg[4];
-    if constexpr (Pairs) lim_extremes_pairs(shx, k0, k1, gr, eg, xm, dpos, dneg);
-    else lim_extremes(shx, k0, k1, gr, eg, xm, dpos, dneg);
+    lim_extremes_pairs(shx, k0, k1, gr, eg, xm, dpos, dneg);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float vi = comp<float>(pi, q);
@@ -719,8 +717,7 @@ __global__ void __launch_bounds__(kGradCells* kMaxBins)
         mn[q] = min3f(mn[q], comp<float>(pj[u], q), comp<float>(pj[u + 1], q));
       }
   }
-  grad_tail_fp32<true>(g, G, i, b, pi, r, mx, mn, m00, m01, m02, m11, m12, m22, xm, shx, k0, k1, limiter,
-                       lim_eps2);
+  grad_tail_fp32(g, G, i, b, pi, r, mx, mn, m00, m01, m02, m11, m12, m22, xm, shx, k0, k1, limiter, lim_eps2);
 }
 
 // ---------------------------------------------------------------------------
