@@ -232,6 +232,17 @@ __device__ __forceinline__ double neg_from_bits(long long m) {
   return __longlong_as_double(m ? (m | (long long)0x8000000000000000ULL) : 0LL);
 }
 
+// FP64 comparisons on the integer pipe, exact for the values they are used
+// on: a > b for a, b >= +0 (the bit patterns order like the values), and
+// x < 0 (negative, not -0, not NaN).
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool lt_zero(double x) {
+  const long long b = __double_as_longlong(x), m = b & 0x7FFFFFFFFFFFFFFFLL;
+  return b < 0 && m != 0 && m <= 0x7FF0000000000000LL;
+}
+
 // Limiter extremes of one (cell, bin) over its faces k0..k1-1: dpos =
 // max(0, max g.x_f) and dneg = min(0, min g.x_f) over the faces that pass
 // the regularisation test |g.x_f| > eps |g| |x_f|.  First one pass without
@@ -439,17 +450,26 @@ __global__ void __launch_bounds__(256) k_grad(Geo<R> g, const R4<R>* __restrict_
         up = mx[q] - vi;
         dn = mn[q] - vi;
       }
-      if (dpos[q] > R(0)) {
-        R lim;
-        if constexpr (sizeof(R) == 8) lim = div_nr(up, dpos[q]);
-        else lim = up / dpos[q];
-        psi[q] = lim < psi[q] ? lim : psi[q];
-      }
-      if (dneg[q] < R(0)) {
-        R lim;
-        if constexpr (sizeof(R) == 8) lim = div_nr(dn, dneg[q]);
-        else lim = dn / dneg[q];
-        psi[q] = lim < psi[q] ? lim : psi[q];
+      if constexpr (sizeof(R) == 8) {
+        // dpos >= +0, dneg = -magnitude or +0, the factors >= +0: the
+        // tests on the integer pipe
+        if (gt_nonneg(dpos[q], 0.0)) {
+          const R lim = div_nr(up, dpos[q]);
+          psi[q] = gt_nonneg(psi[q], lim) ? lim : psi[q];
+        }
+        if (__double_as_longlong(dneg[q]) != 0) {
+          const R lim = div_nr(dn, dneg[q]);
+          psi[q] = gt_nonneg(psi[q], lim) ? lim : psi[q];
+        }
+      } else {
+        if (dpos[q] > R(0)) {
+          const R lim = up / dpos[q];
+          psi[q] = lim < psi[q] ? lim : psi[q];
+        }
+        if (dneg[q] < R(0)) {
+          const R lim = dn / dneg[q];
+          psi[q] = lim < psi[q] ? lim : psi[q];
+        }
       }
     }
   }
@@ -737,7 +757,11 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
     R d = Gc[3 * q] * x.x + Gc[3 * q + 1] * x.y + Gc[3 * q + 2] * x.z;
     v[q] = comp<R>(p, q) + d;
   }
-  if (v[0] < R(0)) v[0] = R(0);
+  if constexpr (sizeof(R) == 4) {
+    if (v[0] < R(0)) v[0] = R(0);
+  } else {
+    if (lt_zero(v[0])) v[0] = R(0);
+  }
   if constexpr (sizeof(R) == 4) {
     // FP32 sweep: |F| <= c N tested on squares, scale by rsqrt (a branch:
     // the clamp is rare and the rsqrt and products are then skipped)
@@ -747,9 +771,10 @@ __device__ __forceinline__ void face_state(const R4<R>& p, const R* __restrict__
       v[1] *= s; v[2] *= s; v[3] *= s;
     }
   } else {
-    // |F| > c N tested on squares; the square root only where it clamps
+    // |F| > c N tested on squares (on the integer pipe); the square root
+    // only where it clamps
     const R fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-    if (fl2 > v[0] * v[0]) {
+    if (gt_nonneg(fl2, v[0] * v[0])) {
       const R s = v[0] / sqrt(fl2);
       v[1] *= s; v[2] *= s; v[3] *= s;
     }
@@ -798,9 +823,10 @@ template <class R> __device__ __forceinline__ void m1_normal(const R v[4], R n0,
   // three quotients (div_nr) and one square root per state instead of five
   // divisions and two square roots
   const R fl2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-  if (v[0] > R(0) && fl2 > R(0)) {
+  // the tests on the integer pipe (v[0] >= 0 after the face-state clamp)
+  if (gt_nonneg(v[0], 0.0) && gt_nonneg(fl2, 0.0)) {
     R f2 = div_nr(fl2, v[0] * v[0]);
-    f2 = f2 > R(1) ? R(1) : f2;
+    f2 = gt_nonneg(f2, 1.0) ? R(1) : f2;
     const R p = R(3) + R(4) * f2, q = R(5) + R(2) * sqrt(R(4) - R(3) * f2);
     const R r = div_nr(0.5, q);
     const R a = (q - p) * r;
