@@ -391,7 +391,7 @@ def e2e_measure(precision, mesh, cfg, state, steps, warmup, dev):
 # the `alu` rooflines; re-measured after each change of these kernels.
 FP64_FLOP = {
     "mixed": {"k_chem": (159.0, "attempt")},
-    "fp64": {"k_chem": (1238.0, "attempt"), "k_grad": (2762.4, "cell"), "k_flux": (5578.0, "cell"),
+    "fp64": {"k_chem": (1238.0, "attempt"), "k_grad": (2762.4, "cell"), "k_flux": (5673.8, "cell"),
              "k_gather": (439.4, "cell")},
 }
 # FP64-pipe instructions (thread instructions on the FP64 pipe, ncu
@@ -401,7 +401,7 @@ FP64_FLOP = {
 # rate against the stream's (peak FLOP / 2 per DFMA) is the pipe's use.
 FP64_INST = {
     "mixed": {"k_chem": (109.1, "attempt")},
-    "fp64": {"k_chem": (801.0, "attempt"), "k_grad": (1993.0, "cell"), "k_flux": (3920.0, "cell"),
+    "fp64": {"k_chem": (801.0, "attempt"), "k_grad": (1944.5, "cell"), "k_flux": (3803.6, "cell"),
              "k_gather": (282.0, "cell")},
 }
 # Fallback FP64 peak from unit counts and clock, used only when the
