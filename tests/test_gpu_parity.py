@@ -413,6 +413,68 @@ def test_no_cell_active(precision):
     compare_state(rt, o, TOL64 if precision == "fp64" else 1e-4)
 
 
+def _edge_radiation(st, C):
+    """The closure's limits side by side: a third of the cells free
+    streaming (|F| = c N, reduced flux f = 1: chi = 1, the face states
+    clamped where the extrapolation overshoots), a third isotropic (F = 0:
+    chi = 1/3), the rest as drawn, and every seventh cell empty (N = 0,
+    F = 0) in every bin."""
+    st = dict(st)
+    N, fr = st["N"].copy(), st["fr"].copy()
+    idx = np.arange(C)
+    direc = fr / np.maximum(np.linalg.norm(fr, axis=1, keepdims=True), 1e-300)
+    free = idx % 3 == 0
+    fr[:, :, free] = direc[:, :, free] * N[:, None, free]
+    fr[:, :, idx % 3 == 1] = 0.0
+    empty = idx % 7 == 0
+    N[:, empty] = 0.0
+    fr[:, :, empty] = 0.0
+    st["N"], st["fr"] = N, fr
+    return st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_free_streaming_isotropic_and_empty_cells(precision):
+    """The M1 closure at f = 1 and f = 0 and cells with no radiation, with
+    sources and the full chemistry, over three subcycles on a ragged 12^3
+    mesh (Sec. 2.3.2-2.3.3).  FP64 at 1e-12 on both metrics; mixed at the
+    mixed path's per-field bound."""
+    mesh, cfg, st = voronoi_case(n=12, n_src=3)
+    st = _edge_radiation(st, mesh.n_cells)
+    assert np.all(np.linalg.norm(st["fr"], axis=1) <= st["N"] * (1 + 1e-15))
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+    dt = o.max_dt()
+    assert o.step(3 * dt, 3) == 0
+    rt.step(3 * dt, 3)
+    assert rt.sync() == 0
+    g = rt.fields()
+    assert all(np.isfinite(g[k]).all() for k in ("N", "F", "x5", "T"))
+    assert (g["N"] >= 0).all()
+    if precision == "fp64":
+        compare_state(rt, o, TOL64, cell_tol=TOL64)
+    else:
+        compare_state(rt, o, 1e-4)
+
+
+@pytest.mark.parametrize("chem_mode", [0, 1])
+def test_mixed_step_chemistry_modes(chem_mode):
+    """The mixed path without chemistry (transport and sources only) and
+    with the isothermal network, whole steps against the oracle on a
+    ragged 11^3 mesh."""
+    mesh, cfg, st = voronoi_case(n=11, n_src=3, chem_mode=chem_mode)
+    o = make_oracle(mesh, cfg, st)
+    rt = make_gpu(mesh, cfg, st, precision="mixed", gather_sum=1)
+    dt = o.max_dt()
+    assert o.step(3 * dt, 3) == 0
+    rt.step(3 * dt, 3)
+    assert rt.sync() == 0
+    compare_state(rt, o, 1e-4)
+    if chem_mode == 0:
+        g = rt.fields()
+        assert np.array_equal(g["x5"], st["x5"]) and np.array_equal(g["T"], st["T"])
+
+
 @pytest.mark.parametrize("gather_sum", [0, 1])
 def test_mixed_step_errors(gather_sum):
     """FP32 sweep: per-field error against the FP64 oracle after a few
