@@ -33,10 +33,11 @@
  * The rate fits are pinned by tests/test_oracle_rate_pins.py to independent
  * atomic data: activation temperatures (NIST energies), cooling per
  * collisional ionisation and per dielectronic recombination, case-B tables,
- * an independent collisional-ionisation fit and the bremsstrahlung Gaunt
- * range.  "Parity unpinned": the prefactors of collisional-excitation and
- * radiative-recombination cooling, and the shape of KWH96's high-temperature
- * factor 1 / (1 + (T / 1e5)^(1/2)).
+ * an independent collisional-ionisation fit, the bremsstrahlung Gaunt
+ * range and, loosely (25 %), the case-A recombination cooling of HII and
+ * HeIII.  "Parity unpinned": the prefactors of collisional-excitation
+ * cooling and of the He II recombination cooling, and the shape of KWH96's
+ * high-temperature factor 1 / (1 + (T / 1e5)^(1/2)).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * arithmetic is the literal sequence written here).  The same source is also
