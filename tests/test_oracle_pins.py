@@ -211,6 +211,18 @@ def test_eddington_factor_is_a_boosted_isotropic_field():
         chi = (1 + 3 * beta * beta) / (3 + beta * beta)
         fl = _two_cell(1.0, [f, 0, 0], 1.0, [f, 0, 0])
         assert fl[1] == pytest.approx(chi, rel=1e-13), f
+    # an oblique field, equal on both sides (no Lax-Friedrichs dissipation):
+    # the flux of F/c through n is N D n with the M1 tensor D = (1 - chi)/2 I
+    # + (3 chi - 1)/2 u u, whose u (u.n) part the beams along and across n
+    # cannot tell from a (u.n) n
+    for f, ang in ((1.0, np.pi / 4), (0.5, np.pi / 3), (0.8, 2.0)):
+        u = np.array([np.cos(ang), np.sin(ang), 0.0])
+        beta = (2.0 - np.sqrt(4.0 - 3.0 * f * f)) / f
+        chi = (1 + 3 * beta * beta) / (3 + beta * beta)
+        N = 1.7
+        fl = _two_cell(N, N * f * u, N, N * f * u)
+        Dn = (1 - chi) / 2 * np.array([1.0, 0, 0]) + (3 * chi - 1) / 2 * u[0] * u
+        np.testing.assert_allclose(fl, [N * f * u[0], *(N * Dn)], rtol=1e-13, atol=1e-15)
     # Kershaw's chi = (1 + 2 f^2) / 3 has the same end points and differs
     # from the boosted field by more than the tolerance in between
     f = 0.5
