@@ -271,6 +271,51 @@ def test_photon_number_and_flux_conserved_transport_only():
     assert np.abs(N1 - N0).max() > 1e-3 * N0.max()  # something did move
 
 
+def _photoionisation_decay(f_s, Gt=2.0):
+    """Hydrogen only, isothermal, photoionisation alone (recombination,
+    collisions, cooling and heating off) in a uniform one-bin field so thin
+    (n_H = 1e-8 against N = 1e-3) that absorption leaves the rate Gamma =
+    c sigma N constant: x_HI(t) = x_HI(0) exp(-Gamma t) exactly.  One
+    thermochemistry call over Gamma t = Gt with the substep rule at f_s and
+    f_max = 2 f_s.  Returns (relative error of x_HI, substeps)."""
+    sigma, N0, x0 = 3e-18, 1e-3, 0.99
+    mesh = synth.cartesian_mesh(2, 2.0)
+    C = mesh.n_cells
+    cfg = base_config(box=2.0, n_bins=1, chem_mode=1, chem_flags=0, y_he=0.0, f_s=f_s, f_max=2 * f_s,
+                      max_substeps=100000, sigma=[[sigma, 0, 0], [0, 0, 0], [0, 0, 0]],
+                      eps=[[0, 0, 0], [0, 0, 0], [0, 0, 0]])
+    x5 = np.zeros((5, C))
+    x5[0], x5[1], x5[2] = x0, 1 - x0, 1.0
+    st = dict(N=np.full((1, C), N0), fr=np.zeros((1, 3, C)), nH=np.full(C, 1e-8), x5=x5, T=np.full(C, 1e4),
+              cells=np.zeros(0, np.int64), Q=np.zeros((0, 1)))
+    o = make_oracle(mesh, cfg, st)
+    assert o.thermochemistry(Gt / (cfg["c_red"] * sigma * N0)) == 0
+    x, _ = o.gas()
+    assert np.all(x[0] == x[0, 0])
+    exact = x0 * np.exp(-Gt)
+    return (x[0, 0] - exact) / exact, int(o.substeps()[0])
+
+
+def test_adaptive_substeps_converge_first_order():
+    """The semi-implicit update under the 10 % substep rule (Sec. 4.1.1)
+    against the exact exponential decay of photoionisation: backward Euler
+    over-predicts what remains (1 / (1 + a) > exp(-a)), and with the rule's
+    target f_s halved the error halves while the substeps double -- first
+    order, as a controller that really sets the step from the relative
+    change gives.  The Richardson extrapolation of the two finest runs then
+    agrees with exp(-Gamma t) to 1e-4, which also pins Gamma = c sigma N."""
+    runs = [_photoionisation_decay(f) for f in (0.05, 0.025, 0.0125)]
+    errs = [e for e, _ in runs]
+    subs = [n for _, n in runs]
+    assert all(e > 0 for e in errs)
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2, errs
+    for a, b in zip(subs, subs[1:]):
+        assert 1.7 < b / a < 2.3, subs
+    assert errs[0] < 0.1                               # ~ Gamma t f_s
+    assert abs(2 * errs[2] - errs[1]) < 1e-4, errs
+
+
 def test_photoheating_energy_budget():
     """Thermal energy (Sec. 2.3.1, reading 10 v) against the ionisation
     count: hydrogen only, one bin, photoheating on and recombination,
