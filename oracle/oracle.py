@@ -269,6 +269,9 @@ class Oracle:
         return G
 
     def face_fluxes(self, G=None):
+        """Face fluxes [F, B, 4] (area times flux per unit area) from the
+        gradients G [C, B, 4, 3]; with G None, from the gradients the last
+        gradients() or transport() call left (zero before the first)."""
         out = np.empty((self.F, self.B, 4))
         if G is None:
             self._lib.orc_face_fluxes(self._h, None, _d(out))

@@ -91,6 +91,36 @@ def test_lsq_gradient_exact_for_linear_field():
     np.testing.assert_allclose(G[~wrap], np.broadcast_to(a, G[~wrap].shape), rtol=0, atol=1e-11)
 
 
+def test_linear_field_reaches_every_face_exactly():
+    """Second-order reconstruction on a Voronoi mesh (Sec. 2.3.2-2.3.3): for
+    a linear N with F = 0 and no limiter the least-squares gradient is exact,
+    so both sides extrapolate to the same N(x_f) at every face centroid; the
+    Lax-Friedrichs dissipation then vanishes and each face carries exactly the
+    Eddington-limit flux N(x_f)/3 n of F and no N (faces of cells next to
+    the periodic boundary, where the field jumps, excluded)."""
+    mesh = synth.voronoi_mesh(9, 10.0, 0.3, seed=11)
+    C = mesh.n_cells
+    a = np.array([0.07, -0.11, 0.05])
+    c = mesh.centroids()
+    N = 5.0 + c @ a
+    cfg = base_config(box=10.0, n_bins=1, limiter=0, chem_mode=0)
+    st = dict(N=N[None, :], fr=np.zeros((1, 3, C)), **dict(zip(("nH", "x5", "T"), neutral_gas(C, 1e-3))))
+    o = make_oracle(mesh, cfg, st)
+    fl = o.face_fluxes(o.gradients())[:, 0, :] / mesh.area[:, None]
+    d = c[mesh.right] - c[mesh.left]
+    crosses = np.any(np.abs(d) > 5.0, axis=1)
+    wrap = np.zeros(C, bool)
+    wrap[mesh.left[crosses]] = True
+    wrap[mesh.right[crosses]] = True
+    inner = ~wrap[mesh.left] & ~wrap[mesh.right]
+    xf = np.stack([mesh.fx, mesh.fy, mesh.fz], 1)
+    assert inner.sum() > 500
+    Nf = 5.0 + xf[inner] @ a
+    n = np.stack([mesh.nx, mesh.ny, mesh.nz], 1)[inner]
+    np.testing.assert_allclose(fl[inner, 0], 0.0, atol=1e-12)
+    np.testing.assert_allclose(fl[inner, 1:], Nf[:, None] * n / 3, rtol=0, atol=1e-12)
+
+
 def test_limiter_bounds_face_values():
     """With the limiter, the value extrapolated to every face centre lies
     within [min, max] of the cell and its neighbours (Sec. 2.3.2) -- up to
