@@ -301,6 +301,51 @@ def test_photon_number_and_flux_conserved_transport_only():
     assert np.abs(N1 - N0).max() > 1e-3 * N0.max()  # something did move
 
 
+@pytest.mark.parametrize("T0", [1.5e4, 6e4, 3e5, 3e6])
+def test_cooling_energy_budget(T0):
+    """Cooling alone (Sec. 2.3.1, the explicit thermal-energy update):
+    without radiation, recombination or collisional ionisation the
+    abundances stay fixed, so over one short accepted substep the thermal
+    energy 3/2 k n_tot T falls by exactly dt Lambda(T0), with Lambda = n_e
+    sum_t K_t n_(t) assembled from the separately written per-term
+    coefficients (collisional excitation on n_HI and n_HeII, collisional
+    ionisation on n_HI, n_HeI, n_HeII, recombination on n_HII, n_HeII,
+    n_HeIII, dielectronic on n_HeII, free-free on n_HII + n_HeII + 4
+    n_HeIII).  A coefficient on the wrong species, a dropped n_e or a sign
+    fails here."""
+    import oracle
+    kB = 1.380649e-16
+    mesh = synth.cartesian_mesh(2, 2.0)
+    C = mesh.n_cells
+    cfg = base_config(box=2.0, n_bins=1, chem_mode=2, chem_flags=4)
+    rng = np.random.default_rng(int(T0))
+    xHII = rng.uniform(0.2, 0.8, C)
+    yII = rng.uniform(0.1, 0.4, C)
+    yIII = rng.uniform(0.1, 0.4, C)
+    x5 = np.stack([1 - xHII, xHII, 1 - yII - yIII, yII, yIII])
+    nH = rng.uniform(0.5e-3, 2e-3, C)
+    st = dict(N=np.zeros((1, C)), fr=np.zeros((1, 3, C)), nH=nH, x5=x5, T=np.full(C, T0),
+              cells=np.zeros(0, np.int64), Q=np.zeros((0, 1)))
+    yhe = cfg["y_he"]
+    nHe = yhe * nH
+    ne = nH * xHII + nHe * (yII + 2 * yIII)
+    dens = dict(ce_HI=nH * (1 - xHII), ce_HeII=nHe * yII, ci_HI=nH * (1 - xHII), ci_HeI=nHe * (1 - yII - yIII),
+                ci_HeII=nHe * yII, rc_HII=nH * xHII, rc_HeII=nHe * yII, rc_HeIII=nHe * yIII, diel_HeII=nHe * yII,
+                ff=nH * xHII + nHe * yII + 4 * nHe * yIII)
+    K = oracle.cooling_coeffs(T0)
+    assert set(K) == set(dens)
+    lam = ne * sum(K[t] * dens[t] for t in K)
+    e0 = 1.5 * kB * (nH + nHe + ne) * T0
+    dt = 1e-3 * float(np.min(e0 / lam))
+    o = make_oracle(mesh, cfg, st)
+    assert o.thermochemistry(dt) == 0
+    x1, T1 = o.gas()
+    np.testing.assert_array_equal(x1, x5)
+    assert np.all(o.substeps() == 1)
+    e1 = 1.5 * kB * (nH + nHe + ne) * T1
+    np.testing.assert_allclose(e1 - e0, -dt * lam, rtol=1e-9)
+
+
 def _photoionisation_decay(f_s, Gt=2.0):
     """Hydrogen only, isothermal, photoionisation alone (recombination,
     collisions, cooling and heating off) in a uniform one-bin field so thin
