@@ -507,6 +507,62 @@ def test_neutral_fraction_near_1e5_per_cell(precision):
         compare_state(rt, o, 1e-4, cell_tol={"N": 1e-4, "fr": 1e-3, "xHI": 1e-5, "T": 1e-5})
 
 
+def _uniform_chem_case(T0, chem_mode, chem_flags, N0, x_HII, f_s=0.05, seed=0, **kw):
+    """2^3 cells, no transport work (the chemistry stage alone), partly
+    ionised H and He at T0 with per-cell densities and abundances drawn from
+    `seed`, one bin at N0."""
+    mesh = synth.cartesian_mesh(2, 2.0)
+    C = mesh.n_cells
+    cfg = base_config(box=2.0, n_bins=1, chem_mode=chem_mode, chem_flags=chem_flags, f_s=f_s, f_max=2 * f_s,
+                      max_substeps=100000, **kw)
+    rng = np.random.default_rng(seed)
+    xHII = np.full(C, x_HII) if np.isscalar(x_HII) else x_HII
+    yII, yIII = rng.uniform(0.1, 0.4, C), rng.uniform(0.1, 0.4, C)
+    x5 = np.stack([1 - xHII, xHII, 1 - yII - yIII, yII, yIII])
+    st = dict(N=np.full((1, C), N0), fr=np.zeros((1, 3, C)), nH=rng.uniform(0.5e-3, 2e-3, C), x5=x5,
+              T=np.full(C, T0), cells=np.zeros(0, np.int64), Q=np.zeros((0, 1)))
+    return mesh, cfg, st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_chemistry_closed_form_regimes(precision):
+    """The chemistry stage on the oracle's closed-form checks: photoionisation
+    alone in a thin field over Gamma t = 2 with the substep target 0.025
+    (~217 substeps per cell, the worklist pass), and cooling alone over one
+    short substep at 3e5 K.  FP64: every field at 1e-12 and the substep
+    counts equal to the oracle's; mixed: x and T within 1e-6 per cell."""
+    sigma, N0 = 3e-18, 1e-3
+    cases = []
+    mesh, cfg, st = _uniform_chem_case(1e4, 1, 0, N0, 0.01, f_s=0.025, y_he=0.0,
+                                       sigma=[[sigma, 0, 0], [0, 0, 0], [0, 0, 0]],
+                                       eps=[[0, 0, 0], [0, 0, 0], [0, 0, 0]])
+    st["nH"][:] = 1e-8
+    cases.append((mesh, cfg, st, 2.0 / (cfg["c_red"] * sigma * N0)))
+    mesh, cfg, st = _uniform_chem_case(3e5, 2, 4, 0.0, np.linspace(0.2, 0.8, 8), seed=3)
+    cases.append((mesh, cfg, st, None))
+    for mesh, cfg, st, dt in cases:
+        o = make_oracle(mesh, cfg, st)
+        if dt is None:
+            # one substep of ~1e-3 of the thermal energy
+            o_probe = make_oracle(mesh, cfg, st)
+            dt = 1e10
+            while True:
+                assert o_probe.thermochemistry(dt) == 0
+                if np.all(o_probe.substeps() == 1):
+                    break
+                dt *= 0.1
+                o_probe = make_oracle(mesh, cfg, st)
+        rt = make_gpu(mesh, cfg, st, precision=precision, gather_sum=1)
+        assert o.thermochemistry(dt) == 0
+        rt.thermochemistry(dt)
+        assert rt.sync() == 0
+        if precision == "fp64":
+            compare_state(rt, o, TOL64, fields=("x5", "T"), cell_tol={"x5": TOL64, "T": TOL64})
+            assert np.array_equal(rt.fields()["nsub"], o.substeps())
+        else:
+            compare_state(rt, o, 1e-6, fields=("x5", "T"), cell_tol={"xHI": 1e-6, "xHII": 1e-6, "T": 1e-6})
+
+
 @pytest.mark.parametrize("chem_mode", [0, 1])
 def test_mixed_step_chemistry_modes(chem_mode):
     """The mixed path without chemistry (transport and sources only) and
