@@ -177,3 +177,41 @@ def test_generators_seeded():
     m = synth.voronoi_mesh(8, 1.0, 0.3, seed=2)
     probe = m.gen + 0.01
     assert np.all(synth.locate_cells(m, probe) == np.arange(m.n_cells))
+
+
+def test_density_recipes():
+    """The synthetic densities as the input recipe states them: the GRF g
+    has zero mean, unit variance and a measured power-spectrum slope of -2
+    (shell-averaged |g_k|^2 fitted over 2 <= |k| <= 16 grid modes); exp(sigma
+    g) then has log-standard deviation sigma and the requested grid mean, and
+    the cells take the value of their nearest grid node; the i.i.d. lognormal
+    field has the requested median and log-width; the source peaks are strict
+    local maxima over the 26 periodic neighbours, highest first."""
+    ng = 64
+    g = synth.grf_field(ng, -2.0, 4)
+    assert abs(g.mean()) < 1e-12 and abs(g.std() - 1) < 1e-12
+    P = np.abs(np.fft.fftn(g)) ** 2
+    k = np.fft.fftfreq(ng) * ng
+    kk = np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    shells = np.arange(2, 17)
+    Pk = np.array([P[(kk >= s - 0.5) & (kk < s + 0.5)].mean() for s in shells])
+    slope = np.polyfit(np.log(shells), np.log(Pk), 1)[0]
+    assert abs(slope + 2.0) < 0.1, slope
+    pts = np.random.default_rng(1).uniform(0, 10.0, size=(500, 3))
+    nH, rho = synth.grf_density(pts, 10.0, ng, 1.5, 2e-4, 4)
+    assert rho.mean() == pytest.approx(2e-4, rel=1e-12)
+    assert np.log(rho).std() == pytest.approx(1.5, rel=1e-12)
+    ijk = np.floor(pts / 10.0 * ng).astype(int) % ng
+    np.testing.assert_array_equal(nH, rho[ijk[:, 0], ijk[:, 1], ijk[:, 2]])
+    ln = synth.lognormal_density(200000, 1e-3, 1.0, 2)
+    assert np.median(ln) == pytest.approx(1e-3, rel=0.01)
+    assert np.log(ln).std() == pytest.approx(1.0, rel=0.01)
+    peaks = synth.density_peaks(rho, 50)
+    vals = rho[peaks[:, 0], peaks[:, 1], peaks[:, 2]]
+    assert np.all(np.diff(vals) <= 0)
+    for p in peaks[:10]:
+        for d in np.ndindex(3, 3, 3):
+            off = np.array(d) - 1
+            if off.any():
+                q = (p + off) % ng
+                assert rho[tuple(p)] > rho[tuple(q)]
