@@ -657,6 +657,49 @@ def test_errors_are_status_codes():
     rt2.sync()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonfinite_photon_density_is_reported(precision):
+    """A NaN in one cell's photon density spreads through the face fluxes;
+    the flux application flags it and rt_sync reports RT_NONFINITE.  With a
+    finite state set again the same context steps cleanly."""
+    from paper_2404_17630_gb300 import RTError
+    from paper_2404_17630_gb300.rt import RT_NONFINITE
+    mesh, cfg, st = voronoi_case(n=8, n_src=2)
+    bad = dict(st)
+    bad["N"] = st["N"].copy()
+    bad["N"][1, 17] = np.nan
+    rt = make_gpu(mesh, cfg, bad, precision=precision, gather_sum=1)
+    dt = rt.max_dt()
+    rt.step(2 * dt, 2)
+    with pytest.raises(RTError) as e:
+        rt.sync()
+    assert e.value.status == RT_NONFINITE
+    rt.set_radiation(st["N"], st["fr"] * cfg["c_red"])
+    rt.set_gas(st["nH"], st["x5"], st["T"])
+    rt.step(2 * dt, 2)
+    assert rt.sync() == 0
+    assert all(np.isfinite(v).all() for k, v in rt.fields().items() if k != "nsub")
+
+
+def test_degenerate_cell_is_a_bad_mesh():
+    """A cell whose neighbours all lie on one line through its centroid has
+    a singular least-squares matrix (Sec. 2.3.2): rt_init_mesh refuses the
+    mesh with RT_BAD_MESH."""
+    from paper_2404_17630_gb300 import RT, RTError, make_config
+    from paper_2404_17630_gb300.rt import RT_BAD_MESH
+    n = 6
+    mesh = synth.cartesian_mesh(n, float(n))
+    # cell 0 at (0.5, 0.5, 0.5); its +-y and +-z neighbours moved onto its x axis
+    for j, (i, k) in {n: (1, 0), n * (n - 1): (n - 1, 0), n * n: (1, 0), n * n * (n - 1): (n - 1, 0)}.items():
+        mesh.cx[j] = mesh.cx[0] + (0.4 if i == 1 else -0.4)
+        mesh.cy[j], mesh.cz[j] = mesh.cy[0], mesh.cz[0]
+    cfg = base_config(box=float(n), n_bins=1)
+    with pytest.raises(RTError) as e:
+        RT(make_config(**cfg), mesh)
+    assert e.value.status == RT_BAD_MESH
+    assert "singular" in str(e.value)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """A device wait that nothing completes gives up after its poll bound and
     is reported as RT_TIMEOUT by rt_sync (the failure path of every bounded
